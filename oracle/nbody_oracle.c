@@ -1,0 +1,389 @@
+/*
+ * nbody_oracle.c -- plain FP64 CPU oracle of the direct N-body Hermite
+ * block-time-step method (Portegies Zwart, Belleman & Geldof, "High
+ * Performance Direct Gravitational N-body Simulations on Graphics Processing
+ * Units", Section 2 and Appendix A).
+ *
+ * TEST INFRASTRUCTURE, NOT THE PRODUCT.  This file is the slow, obviously
+ * correct reference that the CUDA path is checked against.  Only the tests,
+ * the smoke check and the benchmark's CPU-baseline leg may load it; the
+ * product library never does, and the two share no code.
+ *
+ * Every routine is the plain definition or the paper's steps in the paper's
+ * order: double loops, no blocking, no reordering.  Compile with
+ *   -O2 -ffp-contract=off -fno-fast-math
+ * so that every double operation is one IEEE round-to-nearest operation in
+ * source order (no fused multiply-add), which is what lets integer block
+ * levels be compared bit for bit with the GPU path.
+ *
+ * Readings of points the paper leaves open (all pinned by tests):
+ *  - Eq. 1 prints (r_i - r_j) with a plus sign, which is repulsive; the
+ *    Appendix A kernel uses dx = x_j - x_i, which is attractive.  The kernel's
+ *    sign is taken.
+ *  - Softening: r^2 = |dx|^2 + eps^2 (Plummer softening, Appendix A kernel).
+ *  - The self term j = i is excluded, as Eq. 1's sum states.
+ *  - The time-step criterion is not printed (the abstract only says "the same
+ *    time step criterion"); the standard Aarseth criterion with eta = 0.01 is
+ *    used, with the snap and crackle that the corrector's a2 and a3 define.
+ *  - Times are integer ticks of 2^-40; time steps are 2^-k with
+ *    k_min <= k <= 40 (k_min = 3 gives the paper's dt_max = 0.125).
+ *  - Initial step: eta_init * |a| / |k| quantised like every other step.
+ *  - A step may halve as often as needed, but double only once per step and
+ *    only when the new time is a multiple of the doubled step.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_TICK_BITS 40
+#define ORC_OK 0
+#define ORC_EINVAL (-1)
+#define ORC_ENOMEM (-2)
+#define ORC_ESTEP (-4)
+
+static void orc_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Ticks -> time units: exact, because tick counts stay below 2^53. */
+static double orc_ticks_to_time(int64_t ticks)
+{
+    return ldexp((double)ticks, -ORC_TICK_BITS);
+}
+
+/*
+ * Direct summation (Eq. 1; pair terms as in the Appendix A kernel):
+ *   acc_i  =  sum_{j != i} m_j dx / r^3
+ *   jerk_i =  sum_{j != i} m_j ( dv / r^3 - 3 (dx . dv) dx / r^5 )
+ *   pot_i  = -sum_{j != i} m_j / r
+ * with dx = x_j - x_i, dv = v_j - v_i, r = sqrt(|dx|^2 + eps^2), G = 1.
+ * x, v are [n][3]; idx lists the active i; outputs are [n_act][3] and [n_act].
+ */
+void orc_force(int64_t n, const double *m, const double *x, const double *v,
+               double eps, int64_t n_act, const int32_t *idx,
+               double *acc, double *jerk, double *pot, int nthreads)
+{
+    orc_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t a = 0; a < n_act; a++) {
+        int64_t i = idx[a];
+        double ai[3] = {0.0, 0.0, 0.0};
+        double ki[3] = {0.0, 0.0, 0.0};
+        double pi = 0.0;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            double dx[3], dv[3];
+            for (int c = 0; c < 3; c++) {
+                dx[c] = x[3 * j + c] - x[3 * i + c];
+                dv[c] = v[3 * j + c] - v[3 * i + c];
+            }
+            double r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2] + eps * eps;
+            double r = sqrt(r2);
+            double r3 = r2 * r;
+            double r5 = r3 * r2;
+            double xv = dx[0] * dv[0] + dx[1] * dv[1] + dx[2] * dv[2];
+            for (int c = 0; c < 3; c++) {
+                ai[c] += m[j] * dx[c] / r3;
+                ki[c] += m[j] * (dv[c] / r3 - 3.0 * xv * dx[c] / r5);
+            }
+            pi -= m[j] / r;
+        }
+        for (int c = 0; c < 3; c++) {
+            acc[3 * a + c] = ai[c];
+            jerk[3 * a + c] = ki[c];
+        }
+        pot[a] = pi;
+    }
+}
+
+/*
+ * Total energy E = T + W with T = 1/2 sum m v^2 and the softened potential
+ * energy W = -sum_{i<j} m_i m_j / sqrt(|x_i - x_j|^2 + eps^2), the energy whose
+ * conservation the paper reports (Section 6).
+ */
+void orc_energy(int64_t n, const double *m, const double *x, const double *v,
+                double eps, double *ekin, double *epot, int nthreads)
+{
+    double *wrow = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double t = 0.0, w = 0.0;
+    for (int64_t i = 0; i < n; i++)
+        t += 0.5 * m[i] * (v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] + v[3 * i + 2] * v[3 * i + 2]);
+    orc_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int64_t j = i + 1; j < n; j++) {
+            double d0 = x[3 * i] - x[3 * j];
+            double d1 = x[3 * i + 1] - x[3 * j + 1];
+            double d2 = x[3 * i + 2] - x[3 * j + 2];
+            s -= m[i] * m[j] / sqrt(d0 * d0 + d1 * d1 + d2 * d2 + eps * eps);
+        }
+        wrow[i] = s;
+    }
+    for (int64_t i = 0; i < n; i++) w += wrow[i];
+    free(wrow);
+    *ekin = t;
+    *epot = w;
+}
+
+/*
+ * Hermite predictor (Section 2):
+ *   x_p = x + (v + (dt/2) (a + (dt/3) k)) dt
+ *   v_p = v + (a + (dt/2) k) dt
+ */
+void orc_predict_one(const double *x, const double *v, const double *a, const double *k,
+                     double dt, double *xp, double *vp)
+{
+    for (int c = 0; c < 3; c++) {
+        xp[c] = x[c] + (v[c] + (dt / 2.0) * (a[c] + (dt / 3.0) * k[c])) * dt;
+        vp[c] = v[c] + (a[c] + (dt / 2.0) * k[c]) * dt;
+    }
+}
+
+/*
+ * Hermite corrector (Section 2).  In the paper's notation a, k are the values
+ * at the start of the step and a_p, k_p those recomputed at the predicted point:
+ *   a3 = 2 (a - a_p) + (k + k_p) dt
+ *   a2 = -3 (a - a_p) - (2 k + k_p) dt
+ *   x  = x_p + (a2/12 + a3/20) dt^2
+ *   v  = v_p + (a2/3 + a3/4) dt
+ */
+void orc_correct_one(const double *xp, const double *vp, const double *a, const double *k,
+                     const double *ap, const double *kp, double dt,
+                     double *x, double *v, double *a2, double *a3)
+{
+    for (int c = 0; c < 3; c++) {
+        a3[c] = 2.0 * (a[c] - ap[c]) + (k[c] + kp[c]) * dt;
+        a2[c] = -3.0 * (a[c] - ap[c]) - (2.0 * k[c] + kp[c]) * dt;
+        x[c] = xp[c] + (a2[c] / 12.0 + a3[c] / 20.0) * (dt * dt);
+        v[c] = vp[c] + (a2[c] / 3.0 + a3[c] / 4.0) * dt;
+    }
+}
+
+static double orc_norm3(const double *u)
+{
+    return sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+}
+
+/*
+ * Aarseth time-step criterion at the end of a step of length dt.  The
+ * corrector's a2 = (dk/dt) dt^2 / 2 and a3 = (d2k/dt2) dt^3 / 6 (Section 2)
+ * give the snap at the start, s0 = 2 a2 / dt^2, the crackle c = 6 a3 / dt^3,
+ * and the snap at the end, s1 = s0 + c dt.  With a1, k1 the new acceleration
+ * and jerk:
+ *   dt_new = sqrt( eta (|a1| |s1| + |k1|^2) / (|k1| |c| + |s1|^2) ).
+ * A zero denominator gives +infinity (no constraint).
+ */
+double orc_aarseth_dt(const double *a1, const double *k1, const double *a2, const double *a3,
+                      double dt, double eta)
+{
+    double dt2 = dt * dt;
+    double dt3 = dt2 * dt;
+    double s0[3], cr[3], s1[3];
+    for (int c = 0; c < 3; c++) {
+        s0[c] = 2.0 * a2[c] / dt2;
+        cr[c] = 6.0 * a3[c] / dt3;
+        s1[c] = s0[c] + cr[c] * dt;
+    }
+    double na = orc_norm3(a1), nk = orc_norm3(k1), ns = orc_norm3(s1), nc = orc_norm3(cr);
+    double num = na * ns + nk * nk;
+    double den = nk * nc + ns * ns;
+    if (den == 0.0) return INFINITY;
+    return sqrt(eta * num / den);
+}
+
+/* Initial step eta_init |a| / |k|; +infinity when the jerk vanishes. */
+double orc_initial_dt(const double *a, const double *k, double eta_init)
+{
+    double nk = orc_norm3(k);
+    if (nk == 0.0) return INFINITY;
+    return eta_init * orc_norm3(a) / nk;
+}
+
+/*
+ * Block level of a raw step: the k of the largest 2^-k <= dt_raw, clamped to
+ * k >= kmin.  frexp gives dt_raw = f 2^e with 1/2 <= f < 1, so that power of
+ * two is 2^(e-1) and k = 1 - e, exactly.  Returns ORC_ESTEP when dt_raw is
+ * not a number or below 2^-40.
+ */
+int orc_level_of(double dt_raw, int kmin, int *level)
+{
+    if (isnan(dt_raw) || dt_raw < ldexp(1.0, -ORC_TICK_BITS)) return ORC_ESTEP;
+    int k;
+    if (isinf(dt_raw)) {
+        k = kmin;
+    } else {
+        int e;
+        (void)frexp(dt_raw, &e);
+        k = 1 - e;
+        if (k < kmin) k = kmin;
+    }
+    *level = k;
+    return ORC_OK;
+}
+
+/*
+ * New block level after a step that ends at t_new (ticks), from the old level
+ * and the quantised criterion (see the readings in the header).
+ */
+int orc_next_level(int k_old, int k_q, int64_t t_new, int kmin)
+{
+    if (k_q > k_old) return k_q;
+    if (k_q < k_old && k_old > kmin) {
+        int64_t twice_old = (int64_t)1 << (ORC_TICK_BITS - k_old + 1);
+        if (t_new % twice_old == 0) return k_old - 1;
+    }
+    return k_old;
+}
+
+/*
+ * Start-up: full force at t = 0 on every particle, then the initial step.
+ * With kfix > 0 every particle gets the shared level kfix instead.
+ * Arrays are [n][3] (x, v, a, k), [n] ticks t and levels lev.
+ */
+int orc_init(int64_t n, const double *m, const double *x, const double *v, double eps,
+             double eta_init, int kmin, int kfix, double *a, double *k, double *pot,
+             int64_t *t, int32_t *lev, int nthreads)
+{
+    if (n < 1 || eps < 0.0 || kmin < 0 || kmin > ORC_TICK_BITS) return ORC_EINVAL;
+    int32_t *all = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!all) return ORC_ENOMEM;
+    for (int64_t i = 0; i < n; i++) all[i] = (int32_t)i;
+    orc_force(n, m, x, v, eps, n, all, a, k, pot, nthreads);
+    free(all);
+    int rc = ORC_OK;
+    for (int64_t i = 0; i < n; i++) {
+        t[i] = 0;
+        if (kfix > 0) {
+            lev[i] = kfix;
+            continue;
+        }
+        int level;
+        if (orc_level_of(orc_initial_dt(a + 3 * i, k + 3 * i, eta_init), kmin, &level) != ORC_OK) {
+            rc = ORC_ESTEP;
+            level = ORC_TICK_BITS;
+        }
+        lev[i] = level;
+    }
+    return rc;
+}
+
+/* Earliest end time t_i + 2^-k_i over all particles, in ticks. */
+int64_t orc_next_time(int64_t n, const int64_t *t, const int32_t *lev)
+{
+    int64_t best = INT64_MAX;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t e = t[i] + ((int64_t)1 << (ORC_TICK_BITS - lev[i]));
+        if (e < best) best = e;
+    }
+    return best;
+}
+
+/*
+ * One block step (Section 2's step loop): select the block (the particles
+ * with the smallest t_i + dt_i), predict all particles to that time, recompute
+ * acceleration and jerk on the block from the predicted state, correct the
+ * block and give it new steps.  No step is taken when the block time would
+ * exceed t_end (ticks); the return value is then 0.  Otherwise it is the block
+ * size (active indices in act[], ascending, and the block time in *t_next),
+ * or ORC_ESTEP if some new step fell below 2^-40.  pot_out[] (length n) gets
+ * the block's potentials at the predicted state, indexed by particle.
+ */
+int64_t orc_step(int64_t n, const double *m, double eps, double eta, int kmin, int kfix,
+                 int64_t t_end, double *x, double *v, double *a, double *k,
+                 int64_t *t, int32_t *lev, int32_t *act, int64_t *t_next_out,
+                 double *pot_out, int nthreads)
+{
+    int64_t tn = orc_next_time(n, t, lev);
+    *t_next_out = tn;
+    if (tn > t_end) return 0;
+
+    int64_t na = 0;
+    for (int64_t i = 0; i < n; i++)
+        if (t[i] + ((int64_t)1 << (ORC_TICK_BITS - lev[i])) == tn) act[na++] = (int32_t)i;
+
+    double *xp = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *vp = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *anew = (double *)malloc(sizeof(double) * 3 * (size_t)na);
+    double *knew = (double *)malloc(sizeof(double) * 3 * (size_t)na);
+    double *pnew = (double *)malloc(sizeof(double) * (size_t)na);
+    if (!xp || !vp || !anew || !knew || !pnew) {
+        free(xp); free(vp); free(anew); free(knew); free(pnew);
+        return ORC_ENOMEM;
+    }
+    for (int64_t j = 0; j < n; j++)
+        orc_predict_one(x + 3 * j, v + 3 * j, a + 3 * j, k + 3 * j,
+                        orc_ticks_to_time(tn - t[j]), xp + 3 * j, vp + 3 * j);
+
+    orc_force(n, m, xp, vp, eps, na, act, anew, knew, pnew, nthreads);
+
+    int64_t rc = na;
+    for (int64_t s = 0; s < na; s++) {
+        int64_t i = act[s];
+        double dt = orc_ticks_to_time(tn - t[i]);
+        double a2[3], a3[3];
+        orc_correct_one(xp + 3 * i, vp + 3 * i, a + 3 * i, k + 3 * i, anew + 3 * s, knew + 3 * s,
+                        dt, x + 3 * i, v + 3 * i, a2, a3);
+        for (int c = 0; c < 3; c++) {
+            a[3 * i + c] = anew[3 * s + c];
+            k[3 * i + c] = knew[3 * s + c];
+        }
+        if (pot_out) pot_out[i] = pnew[s];
+        t[i] = tn;
+        if (kfix > 0) continue;
+        int kq;
+        if (orc_level_of(orc_aarseth_dt(a + 3 * i, k + 3 * i, a2, a3, dt, eta), kmin, &kq) != ORC_OK) {
+            rc = ORC_ESTEP;
+            kq = ORC_TICK_BITS;
+        }
+        lev[i] = orc_next_level(lev[i], kq, tn, kmin);
+    }
+    free(xp); free(vp); free(anew); free(knew); free(pnew);
+    return rc;
+}
+
+/*
+ * Runs block steps until every particle has reached t_end (ticks) or
+ * max_steps steps were taken.  Optional outputs: hist_nact[s] = block size of
+ * step s (up to max_steps entries), *interactions = sum of n_active (n - 1).
+ * Returns the number of steps, or a negative error.
+ */
+int64_t orc_run(int64_t n, const double *m, double eps, double eta, int kmin, int kfix,
+                int64_t t_end, int64_t max_steps, double *x, double *v, double *a, double *k,
+                int64_t *t, int32_t *lev, int32_t *hist_nact, int64_t *interactions, int nthreads)
+{
+    int32_t *act = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!act) return ORC_ENOMEM;
+    int64_t steps = 0, inter = 0;
+    while (steps < max_steps) {
+        int64_t tn;
+        int64_t na = orc_step(n, m, eps, eta, kmin, kfix, t_end, x, v, a, k, t, lev, act, &tn,
+                              NULL, nthreads);
+        if (na < 0) { free(act); return na; }
+        if (na == 0) break;
+        if (hist_nact) hist_nact[steps] = (int32_t)na;
+        inter += na * (n - 1);
+        steps++;
+    }
+    free(act);
+    if (interactions) *interactions = inter;
+    return steps;
+}

@@ -1,0 +1,69 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake (a dropped term, a flipped sign, a wrong index or
+coefficient) in a copy of the oracle's C source, builds it, and runs the pin
+tests against that copy in a subprocess: every run must fail.  The mistakes
+are planted in the oracle, on the CPU; nothing here touches a GPU.
+"""
+import os
+import subprocess
+import sys
+import tempfile
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "nbody_oracle.c")
+PINS = ["tests/test_oracle_force.py", "tests/test_oracle_hermite.py"]
+
+MUTATIONS = {
+    "force_sign_repulsive": ("dx[c] = x[3 * j + c] - x[3 * i + c];", "dx[c] = x[3 * i + c] - x[3 * j + c];"),
+    "jerk_drop_factor_3": ("3.0 * xv * dx[c] / r5", "xv * dx[c] / r5"),
+    "jerk_wrong_sign": ("dv[c] / r3 - 3.0", "dv[c] / r3 + 3.0"),
+    "jerk_dv_transposed": ("dv[c] = v[3 * j + c] - v[3 * i + c];", "dv[c] = v[3 * i + c] - v[3 * j + c];"),
+    "force_no_softening": ("dx[2] * dx[2] + eps * eps;", "dx[2] * dx[2];"),
+    "force_mass_index": ("ai[c] += m[j] * dx[c] / r3;", "ai[c] += m[i] * dx[c] / r3;"),
+    "force_self_term_kept": ("if (j == i) continue;\n            double dx[3], dv[3];", "double dx[3], dv[3];"),
+    "pot_wrong_power": ("pi -= m[j] / r;", "pi -= m[j] / r2;"),
+    "predict_dt_over_2": ("(a[c] + (dt / 3.0) * k[c])", "(a[c] + (dt / 2.0) * k[c])"),
+    "predict_v_drop_jerk": ("vp[c] = v[c] + (a[c] + (dt / 2.0) * k[c]) * dt;", "vp[c] = v[c] + a[c] * dt;"),
+    "corrector_a2_swapped": ("- (2.0 * k[c] + kp[c]) * dt", "- (k[c] + 2.0 * kp[c]) * dt"),
+    "corrector_a3_coeff": ("a3[c] / 20.0", "a3[c] / 24.0"),
+    "corrector_v_coeff": ("a3[c] / 4.0", "a3[c] / 6.0"),
+    "aarseth_swapped_term": ("double num = na * ns + nk * nk;", "double num = na * ns + na * na;"),
+    "aarseth_crackle_power": ("cr[c] = 6.0 * a3[c] / dt3;", "cr[c] = 6.0 * a3[c] / dt2;"),
+    "level_off_by_one": ("k = 1 - e;", "k = -e;"),
+    "doubling_not_commensurate": ("if (t_new % twice_old == 0) return k_old - 1;", "return k_old - 1;"),
+    "block_only_first_particle": ("== tn) act[na++] = (int32_t)i;", "== tn) { act[na++] = (int32_t)i; break; }"),
+    "block_end_time_off_by_one": ("int64_t e = t[i] + ((int64_t)1 << (ORC_TICK_BITS - lev[i]));",
+                                  "int64_t e = t[i] + ((int64_t)1 << (ORC_TICK_BITS - lev[i] - 1));"),
+    "energy_kinetic_no_half": ("t += 0.5 * m[i] *", "t += m[i] *"),
+    "energy_no_softening": ("d2 * d2 + eps * eps);", "d2 * d2);"),
+}
+
+
+def _run(name, tmpdir):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, name
+    path = os.path.join(tmpdir, name + ".c")
+    lib = os.path.join(tmpdir, name + ".so")
+    open(path, "w").write(src.replace(old, new))
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+                    "-shared", "-o", lib, path, "-lm"], check=True)
+    env = dict(os.environ, NBODY_ORACLE_LIB=lib, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode
+
+
+@pytest.mark.slow
+def test_every_planted_mistake_is_caught():
+    names = sorted(MUTATIONS)
+    with tempfile.TemporaryDirectory() as d:
+        with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+            codes = dict(zip(names, ex.map(lambda n: _run(n, d), names)))
+    survived = [n for n, c in codes.items() if c == 0]
+    assert not survived, "mutations not caught by the pins: %s" % survived
+    assert all(c == 1 for c in codes.values()), codes  # failed tests, not crashes
