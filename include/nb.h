@@ -1,0 +1,194 @@
+/*
+ * nb.h -- C ABI of the GB300 direct N-body library.
+ *
+ * The library integrates a self-gravitating N-body system with the
+ * fourth-order Hermite predictor-corrector and power-of-two block time steps
+ * described in Portegies Zwart, Belleman & Geldof, "High Performance Direct
+ * Gravitational N-body Simulations on Graphics Processing Units" (Section 2),
+ * with the force evaluation of its Appendix A kernel done by direct summation
+ * on the GPU.  Units are N-body units with G = 1.
+ *
+ * Conventions for every entry point:
+ *  - Return value: NB_OK (0) on success, otherwise one of the negative codes
+ *    below; nb_last_error() then describes the failure.
+ *  - Host arrays are owned by the caller and only read or written during the
+ *    call.  Position-like arrays are [n][3] row-major doubles (x0 y0 z0 x1 ...).
+ *  - *_dev entry points take device pointers (for instance from
+ *    torch.Tensor.data_ptr()) with the same layouts; they are asynchronous on
+ *    the context's stream and return before the GPU work completes.
+ *  - Device memory of the context is allocated in nb_init and released in
+ *    nb_free.  Calls on one context are not thread-safe.
+ *  - Time is kept as integer ticks of 2^-40 N-body time units; a time step is
+ *    2^-level ticks-scaled, i.e. dt = 2^-level, level_min <= level <= 40.
+ */
+#ifndef NB_H
+#define NB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NB_OK 0
+#define NB_EINVAL (-1)   /* bad argument: n, n_active, index, eps, NaN input, time off the grid */
+#define NB_ENOMEM (-2)   /* device or pinned host allocation failed */
+#define NB_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
+#define NB_ESTEP (-4)    /* a new time step fell below 2^-40 (or was not a number) */
+#define NB_ETIMEOUT (-5) /* a bounded device-side wait ran out */
+#define NB_ESTATE (-6)   /* call out of order (e.g. nb_correct without a matching nb_force) */
+
+#define NB_DS 0   /* FP32 pair arithmetic on double-single (hi + lo FP32) positions */
+#define NB_FP64 1 /* all pair arithmetic in FP64 */
+
+#define NB_FORCE_AUTO 0  /* pick the force kernel from n_active */
+#define NB_FORCE_IPAR 1  /* i across threads, j tiles broadcast from shared memory */
+#define NB_FORCE_JPAR 2  /* j across threads, warp-shuffle tree reduction (small n_active) */
+
+#define NB_TICK_BITS 40
+
+typedef struct nb_ctx nb_ctx;
+
+typedef struct nb_opts {
+    double eta;        /* Aarseth accuracy parameter; default 0.01 */
+    double eta_init;   /* initial step eta_init |a| / |k|; default 0.01 */
+    int level_min;     /* largest step 2^-level_min; default 3 (dt_max = 0.125, Section 4) */
+    int level_fixed;   /* > 0: every particle keeps the shared step 2^-level_fixed; default 0 */
+    int precision;     /* NB_DS (default) or NB_FP64 */
+    int force_mode;    /* NB_FORCE_AUTO (default), NB_FORCE_IPAR or NB_FORCE_JPAR */
+    int split_j;       /* i-parallel kernel: number of j slices, 0 = automatic */
+    int reserved;      /* must be 0 */
+    void *stream;      /* cudaStream_t to run on; NULL = the legacy default stream */
+} nb_opts;
+
+/* Fills *opts with the defaults listed above. */
+void nb_default_opts(nb_opts *opts);
+
+/*
+ * Creates a context on the current CUDA device and copies in the system:
+ * masses m[n] (> 0 or == 0), positions x[n][3], velocities v[n][3] (host
+ * arrays, FP64), Plummer softening eps >= 0.  Computes the full force at t = 0
+ * and the initial steps (Section 2 step loop, start-up).  opts may be NULL.
+ * Errors: NB_EINVAL (n < 1 or n > 2^31 - 1, eps < 0, non-finite input, bad
+ * opts), NB_ENOMEM, NB_ECUDA, NB_ESTEP.  On error *ctx is NULL.
+ */
+int nb_init(nb_ctx **ctx, int64_t n, const double *m, const double *x, const double *v,
+            double eps, const nb_opts *opts);
+
+/*
+ * Predicts every particle to time t (Section 2 predictor, FP64):
+ *   x_p = x + (v + (dt/2)(a + (dt/3) k)) dt,  v_p = v + (a + (dt/2) k) dt,
+ * with each particle's own dt = t - t_i, and stores the result in the force
+ * kernel's j layout.  t must lie on the 2^-40 tick grid and satisfy t >= t_i
+ * for all i.  Errors: NB_EINVAL, NB_ECUDA.
+ */
+int nb_predict(nb_ctx *ctx, double t);
+
+/*
+ * Direct-summation force on the n_active particles listed in active_idx
+ * (ascending or not, distinct, each in [0, n)) from all n predicted particles
+ * (Eq. 1, pair terms of the Appendix A kernel, dx = x_j - x_i attractive,
+ * r^2 = |dx|^2 + eps^2, j != i):
+ *   acc  =  sum m_j dx / r^3
+ *   jerk =  sum m_j (dv / r^3 - 3 (dx . dv) dx / r^5)
+ *   pot  = -sum m_j / r
+ * evaluated at the state of the last nb_predict (or nb_init).  Outputs are
+ * host arrays acc[n_active][3], jerk[n_active][3], pot[n_active] (any may be
+ * NULL), in the order of active_idx.  The results are also kept for
+ * nb_correct.  Errors: NB_EINVAL (n_active out of [0, n], index out of range
+ * or repeated), NB_ECUDA.
+ */
+int nb_force(nb_ctx *ctx, const int32_t *active_idx, int32_t n_active, double *acc,
+             double *jerk, double *pot);
+
+/*
+ * As nb_force with device pointers: d_active_idx[n_active] int32, outputs
+ * d_acc[n_active][3], d_jerk[n_active][3], d_pot[n_active] (any may be NULL).
+ * Indices are validated on the device; a bad index makes this call return
+ * NB_EINVAL after a synchronisation of the context's stream.
+ */
+int nb_force_dev(nb_ctx *ctx, const int32_t *d_active_idx, int32_t n_active, double *d_acc,
+                 double *d_jerk, double *d_pot);
+
+/*
+ * Hermite corrector plus new block step for the listed particles (Section 2):
+ *   a3 = 2 (a - a_p) + (k + k_p) dt,  a2 = -3 (a - a_p) - (2 k + k_p) dt,
+ *   x = x_p + (a2/12 + a3/20) dt^2,   v = v_p + (a2/3 + a3/4) dt,
+ * then the Aarseth step from the snap and crackle that a2 and a3 define,
+ * quantised to a power of two (halving at once, doubling by one level when t
+ * is a multiple of the doubled step), and t_i = t.  The new acceleration and
+ * jerk a_p, k_p are acc[n_active][3], jerk[n_active][3] (host) when given,
+ * else the results of the last nb_force, which must have used the same
+ * n_active and the prediction time t.  Errors: NB_EINVAL, NB_ESTATE,
+ * NB_ESTEP, NB_ECUDA.
+ */
+int nb_correct(nb_ctx *ctx, const int32_t *active_idx, int32_t n_active, double t,
+               const double *acc, const double *jerk);
+
+/*
+ * One block step entirely on the device (Section 2 step loop): select the
+ * particles with the smallest t_i + dt_i, predict all, force on the block,
+ * correct the block.  If t_out or n_active_out is non-NULL the call waits for
+ * the step and reports the block time and size; otherwise it only enqueues.
+ * Errors: NB_ESTEP (reported when the step is waited for), NB_ECUDA.
+ */
+int nb_step(nb_ctx *ctx, double *t_out, int32_t *n_active_out);
+
+/*
+ * Block steps until every particle has reached t_end (which must be a multiple
+ * of the largest step so that all particles meet there), or max_steps steps.
+ * Steps are replayed from a captured CUDA graph with no host synchronisation
+ * between them.  Outputs (may be NULL): steps taken, interactions
+ * (sum of n_active (n - 1)).  Errors: NB_EINVAL, NB_ESTEP, NB_ECUDA.
+ */
+int nb_run(nb_ctx *ctx, double t_end, int64_t max_steps, int64_t *steps_out,
+           int64_t *interactions_out);
+
+/*
+ * Total energy of the system predicted to the current system time (exact when
+ * all particles are synchronised): *ekin = 1/2 sum m v^2 (FP64) and
+ * *epot = 1/2 sum m_i pot_i from a full force sweep (the softened potential
+ * energy, Section 6).  Errors: NB_ECUDA.
+ */
+int nb_energy(nb_ctx *ctx, double *ekin, double *epot);
+
+/*
+ * Checkpoint: copies the FP64 state out to host arrays x, v, a (acceleration),
+ * k (jerk) [n][3], t_ticks[n] (int64 ticks of 2^-40) and level[n]; any may be
+ * NULL.  Errors: NB_ECUDA.
+ */
+int nb_get_state(nb_ctx *ctx, double *x, double *v, double *a, double *k, int64_t *t_ticks,
+                 int32_t *level);
+
+/*
+ * Restore: replaces the state with host arrays of the layouts above (all
+ * required).  Levels must lie in [level_min, 40] and every t_ticks[i] must be
+ * a non-negative multiple of 2^(40 - level[i]).  Resuming from a state saved
+ * by nb_get_state reproduces the original run bit for bit.
+ * Errors: NB_EINVAL, NB_ECUDA.
+ */
+int nb_set_state(nb_ctx *ctx, const double *x, const double *v, const double *a,
+                 const double *k, const int64_t *t_ticks, const int32_t *level);
+
+/*
+ * The block of the last nb_step / nb_run step: writes up to cap indices
+ * (ascending) to idx and the block size and time (ticks) to *n_active and
+ * *t_ticks (each pointer may be NULL).  Errors: NB_ECUDA.
+ */
+int nb_get_active(nb_ctx *ctx, int32_t *idx, int32_t cap, int32_t *n_active, int64_t *t_ticks);
+
+/* Number of particles, or -1 for a NULL context. */
+int64_t nb_num_particles(const nb_ctx *ctx);
+
+/* Description of the last failure on this context ("" if none); with a NULL
+ * context, that of the last failed nb_init on the calling thread.  Never NULL. */
+const char *nb_last_error(const nb_ctx *ctx);
+
+/* Releases the context and its device memory; NULL is ignored. */
+void nb_free(nb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NB_H */

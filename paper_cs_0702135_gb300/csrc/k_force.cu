@@ -1,0 +1,565 @@
+// k_force.cu -- direct-summation force kernels on the CUDA cores.
+//
+// For every active i and every j != i (Eq. 1 with the attractive sign and the
+// pair terms of the Appendix A kernel), with dx = x_j - x_i, dv = v_j - v_i,
+// r^2 = |dx|^2 + eps^2:
+//   acc  +=  m_j dx / r^3
+//   jerk +=  m_j (dv / r^3 - 3 (dx . dv) dx / r^5)
+//   pot  -=  m_j / r
+//
+// DS kernels: positions are double-single (hi + lo FP32), the difference
+// x_j - x_i is formed as (x_j,hi - x_i,hi) + (x_j,lo - x_i,lo), the pair terms
+// run in FP32 with rsqrtf on the SFU, and each thread's per-tile FP32 partials
+// are folded into hi + lo FP32 accumulators with TwoSum, so that the error of
+// the sum over all N does not grow with N.  FP64 kernels do everything in FP64.
+//
+// i-parallel kernels: a CTA owns a block of active i (R per thread, in
+// registers) and one j slice, streamed through shared memory in tiles that
+// every thread reads by broadcast.  j-parallel kernels (small blocks): a CTA
+// owns up to four active i and one j slice, each thread takes every NT-th j,
+// and the CTA reduces with a warp-shuffle tree.  With several j slices the
+// slice partials go to a buffer and a combine kernel sums them in fixed slice
+// order, so results are deterministic and no atomics are used.
+//
+// The self term j = i is dropped inside the loop: a warp whose own i fall in
+// the current j tile runs a guarded copy of the inner loop that zeroes the
+// pair with j = i; every other tile runs the unguarded loop.  (Leaving the
+// self pair in and subtracting -m_i / eps at the end would inflate the FP32
+// tile partial of the potential by m_i / eps, which at small N or large mass
+// ratios is larger than the potential itself.)  With eps = 0 a pair at r = 0
+// between distinct particles is dropped as well.
+#include "nb_internal.cuh"
+
+namespace nbk {
+namespace {
+
+__device__ __forceinline__ int read_na(const ForceArgs &fa)
+{
+    return fa.na_dev ? *fa.na_dev : fa.na_host;
+}
+
+// Knuth's TwoSum: hi + lo absorbs x, with the rounding error of hi + x in lo.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
+{
+    float s = hi + x;
+    float bb = s - hi;
+    float e = (hi - (s - bb)) + (x - bb);
+    hi = s;
+    lo += e;
+}
+
+// Sum of two double-single values (h, l) += (h2, l2).
+__device__ __forceinline__ void ds_add(float &h, float &l, float h2, float l2)
+{
+    float s = h + h2;
+    float bb = s - h;
+    float e = (h - (s - bb)) + (h2 - bb);
+    h = s;
+    l = (l + l2) + e;
+}
+
+__device__ __forceinline__ void store_result(const ForceOut &o, int a, const double r[kComp])
+{
+    if (o.acc) {
+        o.acc[3 * (long long)a + 0] = r[0];
+        o.acc[3 * (long long)a + 1] = r[1];
+        o.acc[3 * (long long)a + 2] = r[2];
+    }
+    if (o.jerk) {
+        o.jerk[3 * (long long)a + 0] = r[3];
+        o.jerk[3 * (long long)a + 1] = r[4];
+        o.jerk[3 * (long long)a + 2] = r[5];
+    }
+    if (o.pot) o.pot[a] = r[6];
+}
+
+// One FP32 pair interaction on double-single positions.
+template <bool SOFT, bool GUARD>
+__device__ __forceinline__ void pair_ds(const float4 &p, const float4 &l, const float4 &w,
+                                        const float xh[3], const float xl[3], const float vi[3],
+                                        float eps2, float acc[3], float jk[3], float &pot,
+                                        int j = 0, int i = 1)
+{
+    const float dx = (p.x - xh[0]) + (l.x - xl[0]);
+    const float dy = (p.y - xh[1]) + (l.y - xl[1]);
+    const float dz = (p.z - xh[2]) + (l.z - xl[2]);
+    const float ux = w.x - vi[0];
+    const float uy = w.y - vi[1];
+    const float uz = w.z - vi[2];
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+    const float rv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+    float rinv = rsqrtf(r2);
+    if (!SOFT) rinv = (r2 > 0.0f) ? rinv : 0.0f;
+    if (GUARD) rinv = (j == i) ? 0.0f : rinv;
+    const float rinv2 = rinv * rinv;
+    const float mr = p.w * rinv;           // m_j / r
+    const float mr3 = mr * rinv2;          // m_j / r^3
+    const float b = -3.0f * rv * rinv2;    // -3 (dx . dv) / r^2
+    acc[0] = fmaf(mr3, dx, acc[0]);
+    acc[1] = fmaf(mr3, dy, acc[1]);
+    acc[2] = fmaf(mr3, dz, acc[2]);
+    const float qx = fmaf(b, dx, ux);
+    const float qy = fmaf(b, dy, uy);
+    const float qz = fmaf(b, dz, uz);
+    jk[0] = fmaf(mr3, qx, jk[0]);
+    jk[1] = fmaf(mr3, qy, jk[1]);
+    jk[2] = fmaf(mr3, qz, jk[2]);
+    pot -= mr;
+}
+
+// One FP64 pair interaction.
+template <bool SOFT>
+__device__ __forceinline__ void pair_f64(const double4_32a &p, const double4_32a &w, const double xi[3],
+                                         const double vi[3], double eps2, double acc[3],
+                                         double jk[3], double &pot, int j, int i)
+{
+    const double dx = p.x - xi[0];
+    const double dy = p.y - xi[1];
+    const double dz = p.z - xi[2];
+    const double ux = w.x - vi[0];
+    const double uy = w.y - vi[1];
+    const double uz = w.z - vi[2];
+    const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+    const double rv = fma(dx, ux, fma(dy, uy, dz * uz));
+    double rinv = rsqrt(r2);
+    if (!SOFT) rinv = (r2 > 0.0) ? rinv : 0.0;
+    rinv = (j == i) ? 0.0 : rinv;
+    const double rinv2 = rinv * rinv;
+    const double mr = p.w * rinv;
+    const double mr3 = mr * rinv2;
+    const double b = -3.0 * rv * rinv2;
+    acc[0] = fma(mr3, dx, acc[0]);
+    acc[1] = fma(mr3, dy, acc[1]);
+    acc[2] = fma(mr3, dz, acc[2]);
+    jk[0] = fma(mr3, fma(b, dx, ux), jk[0]);
+    jk[1] = fma(mr3, fma(b, dy, uy), jk[1]);
+    jk[2] = fma(mr3, fma(b, dz, uz), jk[2]);
+    pot -= mr;
+}
+
+__device__ __forceinline__ int clamp_index(int i, int n) { return min(max(i, 0), n - 1); }
+
+// ----------------------------------------------------------------------------
+// DS, i-parallel.
+
+template <int NT, int R, bool SOFT>
+__global__ void __launch_bounds__(NT) k_force_ipar_ds(ForceArgs fa, JDS J)
+{
+    const int na = read_na(fa);
+    if (na <= 0 || use_jpar(na, fa.jpar_max)) return;
+    const Plan P = plan_ipar(na, fa.n, NT * R, NT, fa.slots_ipar, fa.split, fa.part_cap);
+    __shared__ float4 s_p[NT], s_l[NT], s_v[NT];
+    const float eps2 = (float)fa.eps2;
+    const int tid = threadIdx.x;
+
+    for (int w = blockIdx.x; w < P.items; w += gridDim.x) {
+        const int ib = w % P.n_iblk;
+        const int sl = w / P.n_iblk;
+        const int j0 = sl * P.jslice;
+        const int j1 = min(fa.n, j0 + P.jslice);
+
+        float xh[R][3], xl[R][3], vi[R][3];
+        int ia[R], ii[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int a = ib * NT * R + r * NT + tid;
+            ia[r] = a < na ? a : -1;
+            const int i = clamp_index(fa.act[a < na ? a : 0], fa.n);
+            ii[r] = i;
+            const float4 p = J.pos_hi[i], l = J.pos_lo[i], v = J.vel[i];
+            xh[r][0] = p.x; xh[r][1] = p.y; xh[r][2] = p.z;
+            xl[r][0] = l.x; xl[r][1] = l.y; xl[r][2] = l.z;
+            vi[r][0] = v.x; vi[r][1] = v.y; vi[r][2] = v.z;
+        }
+        float hi[R][kComp], lo[R][kComp];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < kComp; ++c) hi[r][c] = lo[r][c] = 0.0f;
+
+        for (int jt = j0; jt < j1; jt += NT) {
+            __syncthreads();
+            const int j = jt + tid;
+            if (j < j1) {
+                s_p[tid] = J.pos_hi[j];
+                s_l[tid] = J.pos_lo[j];
+                s_v[tid] = J.vel[j];
+            } else {
+                s_p[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+                s_l[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+                s_v[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncthreads();
+            float ta[R][3], tk[R][3], tp[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                ta[r][0] = ta[r][1] = ta[r][2] = 0.0f;
+                tk[r][0] = tk[r][1] = tk[r][2] = 0.0f;
+                tp[r] = 0.0f;
+            }
+            bool mine = false;
+#pragma unroll
+            for (int r = 0; r < R; ++r) mine |= (unsigned)(ii[r] - jt) < (unsigned)NT;
+            if (__any_sync(0xffffffffu, mine)) {
+                for (int jj = 0; jj < NT; ++jj) {
+                    const float4 p = s_p[jj], l = s_l[jj], v = s_v[jj];
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        pair_ds<SOFT, true>(p, l, v, xh[r], xl[r], vi[r], eps2, ta[r], tk[r], tp[r],
+                                            jt + jj, ii[r]);
+                }
+            } else {
+#pragma unroll 8
+                for (int jj = 0; jj < NT; ++jj) {
+                    const float4 p = s_p[jj], l = s_l[jj], v = s_v[jj];
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        pair_ds<SOFT, false>(p, l, v, xh[r], xl[r], vi[r], eps2, ta[r], tk[r], tp[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                two_sum_acc(hi[r][0], lo[r][0], ta[r][0]);
+                two_sum_acc(hi[r][1], lo[r][1], ta[r][1]);
+                two_sum_acc(hi[r][2], lo[r][2], ta[r][2]);
+                two_sum_acc(hi[r][3], lo[r][3], tk[r][0]);
+                two_sum_acc(hi[r][4], lo[r][4], tk[r][1]);
+                two_sum_acc(hi[r][5], lo[r][5], tk[r][2]);
+                two_sum_acc(hi[r][6], lo[r][6], tp[r]);
+            }
+        }
+
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (ia[r] < 0) continue;
+            double res[kComp];
+#pragma unroll
+            for (int c = 0; c < kComp; ++c) res[c] = (double)hi[r][c] + (double)lo[r][c];
+            if (P.S == 1) {
+                store_result(fa.out, ia[r], res);
+            } else {
+#pragma unroll
+                for (int c = 0; c < kComp; ++c)
+                    fa.part[((long long)sl * kComp + c) * na + ia[r]] = res[c];
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// DS, j-parallel (small blocks).
+
+template <int NT, int IC, bool SOFT>
+__global__ void __launch_bounds__(NT) k_force_jpar_ds(ForceArgs fa, JDS J)
+{
+    const int na = read_na(fa);
+    if (na <= 0 || !use_jpar(na, fa.jpar_max)) return;
+    const Plan P = plan_jpar(na, fa.n, NT, IC, fa.slots_jpar, fa.part_cap);
+    constexpr int NW = NT / 32;
+    constexpr int NV = IC * kComp;
+    __shared__ float s_h[NW][NV], s_l[NW][NV];
+    const float eps2 = (float)fa.eps2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (int w = blockIdx.x; w < P.items; w += gridDim.x) {
+        const int ch = w % P.n_iblk;
+        const int sl = w / P.n_iblk;
+        const int j0 = sl * P.jslice;
+        const int j1 = min(fa.n, j0 + P.jslice);
+
+        float xh[IC][3], xl[IC][3], vi[IC][3];
+        int ii[IC];
+#pragma unroll
+        for (int q = 0; q < IC; ++q) {
+            const int a = ch * IC + q;
+            const int i = clamp_index(fa.act[a < na ? a : 0], fa.n);
+            ii[q] = i;
+            const float4 p = J.pos_hi[i], l = J.pos_lo[i], v = J.vel[i];
+            xh[q][0] = p.x; xh[q][1] = p.y; xh[q][2] = p.z;
+            xl[q][0] = l.x; xl[q][1] = l.y; xl[q][2] = l.z;
+            vi[q][0] = v.x; vi[q][1] = v.y; vi[q][2] = v.z;
+        }
+        float va[IC][3], vk[IC][3], vp[IC];
+#pragma unroll
+        for (int q = 0; q < IC; ++q) {
+            va[q][0] = va[q][1] = va[q][2] = 0.0f;
+            vk[q][0] = vk[q][1] = vk[q][2] = 0.0f;
+            vp[q] = 0.0f;
+        }
+        for (int j = j0 + tid; j < j1; j += NT) {
+            const float4 p = __ldg(&J.pos_hi[j]), l = __ldg(&J.pos_lo[j]), v = __ldg(&J.vel[j]);
+#pragma unroll
+            for (int q = 0; q < IC; ++q)
+                pair_ds<SOFT, true>(p, l, v, xh[q], xl[q], vi[q], eps2, va[q], vk[q], vp[q], j, ii[q]);
+        }
+        // Warp tree in double-single.  The xor butterfly leaves every lane with
+        // the same value, since TwoSum is exact in either operand order.
+        float h[NV], lo[NV];
+#pragma unroll
+        for (int q = 0; q < IC; ++q) {
+            h[q * kComp + 0] = va[q][0]; h[q * kComp + 1] = va[q][1]; h[q * kComp + 2] = va[q][2];
+            h[q * kComp + 3] = vk[q][0]; h[q * kComp + 4] = vk[q][1]; h[q * kComp + 5] = vk[q][2];
+            h[q * kComp + 6] = vp[q];
+        }
+#pragma unroll
+        for (int e = 0; e < NV; ++e) lo[e] = 0.0f;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+#pragma unroll
+            for (int e = 0; e < NV; ++e) {
+                const float h2 = __shfl_xor_sync(0xffffffffu, h[e], off);
+                const float l2 = __shfl_xor_sync(0xffffffffu, lo[e], off);
+                ds_add(h[e], lo[e], h2, l2);
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int e = 0; e < NV; ++e) {
+                s_h[warp][e] = h[e];
+                s_l[warp][e] = lo[e];
+            }
+        }
+        __syncthreads();
+        if (tid < NV) {
+            float th = s_h[0][tid], tl = s_l[0][tid];
+            for (int ww = 1; ww < NW; ++ww) ds_add(th, tl, s_h[ww][tid], s_l[ww][tid]);
+            const int q = tid / kComp, c = tid % kComp;
+            const int a = ch * IC + q;
+            if (a < na) {
+                const double r = (double)th + (double)tl;
+                fa.part[((long long)sl * kComp + c) * na + a] = r;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// FP64, i-parallel.
+
+template <int NT, int R, bool SOFT>
+__global__ void __launch_bounds__(NT) k_force_ipar_f64(ForceArgs fa, JF64 J)
+{
+    const int na = read_na(fa);
+    if (na <= 0 || use_jpar(na, fa.jpar_max)) return;
+    const Plan P = plan_ipar(na, fa.n, NT * R, NT, fa.slots_ipar, fa.split, fa.part_cap);
+    __shared__ double4_32a s_p[NT], s_v[NT];
+    const double eps2 = fa.eps2;
+    const int tid = threadIdx.x;
+
+    for (int w = blockIdx.x; w < P.items; w += gridDim.x) {
+        const int ib = w % P.n_iblk;
+        const int sl = w / P.n_iblk;
+        const int j0 = sl * P.jslice;
+        const int j1 = min(fa.n, j0 + P.jslice);
+
+        double xi[R][3], vi[R][3];
+        int ia[R], ii[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int a = ib * NT * R + r * NT + tid;
+            ia[r] = a < na ? a : -1;
+            const int i = clamp_index(fa.act[a < na ? a : 0], fa.n);
+            ii[r] = i;
+            const double4_32a p = J.pos[i], v = J.vel[i];
+            xi[r][0] = p.x; xi[r][1] = p.y; xi[r][2] = p.z;
+            vi[r][0] = v.x; vi[r][1] = v.y; vi[r][2] = v.z;
+        }
+        double acc[R][3], jk[R][3], pot[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            acc[r][0] = acc[r][1] = acc[r][2] = 0.0;
+            jk[r][0] = jk[r][1] = jk[r][2] = 0.0;
+            pot[r] = 0.0;
+        }
+        for (int jt = j0; jt < j1; jt += NT) {
+            __syncthreads();
+            const int j = jt + tid;
+            if (j < j1) {
+                s_p[tid] = J.pos[j];
+                s_v[tid] = J.vel[j];
+            } else {
+                s_p[tid] = make_double4_32a(0., 0., 0., 0.);
+                s_v[tid] = make_double4_32a(0., 0., 0., 0.);
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int jj = 0; jj < NT; ++jj) {
+                const double4_32a p = s_p[jj], v = s_v[jj];
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    pair_f64<SOFT>(p, v, xi[r], vi[r], eps2, acc[r], jk[r], pot[r], jt + jj, ii[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (ia[r] < 0) continue;
+            double res[kComp] = {acc[r][0], acc[r][1], acc[r][2], jk[r][0], jk[r][1], jk[r][2],
+                                 pot[r]};
+            if (P.S == 1) {
+                store_result(fa.out, ia[r], res);
+            } else {
+#pragma unroll
+                for (int c = 0; c < kComp; ++c)
+                    fa.part[((long long)sl * kComp + c) * na + ia[r]] = res[c];
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// FP64, j-parallel (small blocks).
+
+template <int NT, int IC, bool SOFT>
+__global__ void __launch_bounds__(NT) k_force_jpar_f64(ForceArgs fa, JF64 J)
+{
+    const int na = read_na(fa);
+    if (na <= 0 || !use_jpar(na, fa.jpar_max)) return;
+    const Plan P = plan_jpar(na, fa.n, NT, IC, fa.slots_jpar, fa.part_cap);
+    constexpr int NW = NT / 32;
+    constexpr int NV = IC * kComp;
+    __shared__ double s_r[NW][NV];
+    const double eps2 = fa.eps2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (int w = blockIdx.x; w < P.items; w += gridDim.x) {
+        const int ch = w % P.n_iblk;
+        const int sl = w / P.n_iblk;
+        const int j0 = sl * P.jslice;
+        const int j1 = min(fa.n, j0 + P.jslice);
+        double xi[IC][3], vi[IC][3];
+        int ii[IC];
+#pragma unroll
+        for (int q = 0; q < IC; ++q) {
+            const int a = ch * IC + q;
+            const int i = clamp_index(fa.act[a < na ? a : 0], fa.n);
+            ii[q] = i;
+            const double4_32a p = J.pos[i], v = J.vel[i];
+            xi[q][0] = p.x; xi[q][1] = p.y; xi[q][2] = p.z;
+            vi[q][0] = v.x; vi[q][1] = v.y; vi[q][2] = v.z;
+        }
+        double val[NV];
+#pragma unroll
+        for (int e = 0; e < NV; ++e) val[e] = 0.0;
+        for (int j = j0 + tid; j < j1; j += NT) {
+            const double4_32a p = J.pos[j], v = J.vel[j];
+#pragma unroll
+            for (int q = 0; q < IC; ++q) {
+                double a3[3] = {val[q * kComp], val[q * kComp + 1], val[q * kComp + 2]};
+                double k3[3] = {val[q * kComp + 3], val[q * kComp + 4], val[q * kComp + 5]};
+                double pp = val[q * kComp + 6];
+                pair_f64<SOFT>(p, v, xi[q], vi[q], eps2, a3, k3, pp, j, ii[q]);
+                val[q * kComp] = a3[0]; val[q * kComp + 1] = a3[1]; val[q * kComp + 2] = a3[2];
+                val[q * kComp + 3] = k3[0]; val[q * kComp + 4] = k3[1]; val[q * kComp + 5] = k3[2];
+                val[q * kComp + 6] = pp;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1)
+#pragma unroll
+            for (int e = 0; e < NV; ++e) val[e] += __shfl_xor_sync(0xffffffffu, val[e], off);
+        if (lane == 0)
+#pragma unroll
+            for (int e = 0; e < NV; ++e) s_r[warp][e] = val[e];
+        __syncthreads();
+        if (tid < NV) {
+            double r = s_r[0][tid];
+            for (int ww = 1; ww < NW; ++ww) r += s_r[ww][tid];
+            const int q = tid / kComp, c = tid % kComp;
+            const int a = ch * IC + q;
+            if (a < na) {
+                fa.part[((long long)sl * kComp + c) * na + a] = r;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Slice combine: out = sum over slices in slice order (FP64).
+
+template <int IR, int IR64>
+__global__ void k_force_combine(ForceArgs fa, int precision)
+{
+    const int na = read_na(fa);
+    if (na <= 0) return;
+    int S;
+    if (use_jpar(na, fa.jpar_max)) {
+        S = plan_jpar(na, fa.n, kJparNT, kJparIC, fa.slots_jpar, fa.part_cap).S;
+    } else {
+        const int iblk = kIparNT * (precision == NB_FP64 ? IR64 : IR);
+        const Plan p = plan_ipar(na, fa.n, iblk, kIparNT, fa.slots_ipar, fa.split, fa.part_cap);
+        if (p.S == 1) return;
+        S = p.S;
+    }
+    const long long total = (long long)na * kComp;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e / na), a = (int)(e % na);
+        double s = 0.0;
+        for (int q = 0; q < S; ++q) s += fa.part[((long long)q * kComp + c) * na + a];
+        if (c < 3) {
+            if (fa.out.acc) fa.out.acc[3 * (long long)a + c] = s;
+        } else if (c < 6) {
+            if (fa.out.jerk) fa.out.jerk[3 * (long long)a + (c - 3)] = s;
+        } else if (fa.out.pot) {
+            fa.out.pot[a] = s;
+        }
+    }
+}
+
+int combine_grid(const ForceArgs &fa)
+{
+    if (!fa.na_dev) {
+        long long total = (long long)fa.na_host * kComp;
+        long long g = (total + 255) / 256;
+        return (int)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
+    }
+    return 1024;
+}
+
+}  // namespace
+
+void launch_force_ds(const ForceArgs &fa, const JDS &j, bool softened, int grid_ipar,
+                     int grid_jpar, cudaStream_t st)
+{
+    if (softened) {
+        if (grid_ipar > 0) k_force_ipar_ds<kIparNT, kIparR, true><<<grid_ipar, kIparNT, 0, st>>>(fa, j);
+        if (grid_jpar > 0) k_force_jpar_ds<kJparNT, kJparIC, true><<<grid_jpar, kJparNT, 0, st>>>(fa, j);
+    } else {
+        if (grid_ipar > 0) k_force_ipar_ds<kIparNT, kIparR, false><<<grid_ipar, kIparNT, 0, st>>>(fa, j);
+        if (grid_jpar > 0) k_force_jpar_ds<kJparNT, kJparIC, false><<<grid_jpar, kJparNT, 0, st>>>(fa, j);
+    }
+    k_force_combine<kIparR, kIparR64><<<combine_grid(fa), 256, 0, st>>>(fa, NB_DS);
+}
+
+void launch_force_f64(const ForceArgs &fa, const JF64 &j, bool softened, int grid_ipar,
+                      int grid_jpar, cudaStream_t st)
+{
+    if (softened) {
+        if (grid_ipar > 0) k_force_ipar_f64<kIparNT, kIparR64, true><<<grid_ipar, kIparNT, 0, st>>>(fa, j);
+        if (grid_jpar > 0) k_force_jpar_f64<kJparNT, kJparIC, true><<<grid_jpar, kJparNT, 0, st>>>(fa, j);
+    } else {
+        if (grid_ipar > 0) k_force_ipar_f64<kIparNT, kIparR64, false><<<grid_ipar, kIparNT, 0, st>>>(fa, j);
+        if (grid_jpar > 0) k_force_jpar_f64<kJparNT, kJparIC, false><<<grid_jpar, kJparNT, 0, st>>>(fa, j);
+    }
+    k_force_combine<kIparR, kIparR64><<<combine_grid(fa), 256, 0, st>>>(fa, NB_FP64);
+}
+
+int occupancy_force(int precision, bool jpar, int *blocks_per_sm)
+{
+    cudaError_t e;
+    if (precision == NB_FP64)
+        e = jpar ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                       blocks_per_sm, k_force_jpar_f64<kJparNT, kJparIC, true>, kJparNT, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                       blocks_per_sm, k_force_ipar_f64<kIparNT, kIparR64, true>, kIparNT, 0);
+    else
+        e = jpar ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                       blocks_per_sm, k_force_jpar_ds<kJparNT, kJparIC, true>, kJparNT, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                       blocks_per_sm, k_force_ipar_ds<kIparNT, kIparR, true>, kIparNT, 0);
+    return e == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace nbk

@@ -1,0 +1,491 @@
+// k_step.cu -- the O(N) kernels around the force: Hermite predictor, Hermite
+// corrector with the block time step, block scheduler, energy reduction.
+//
+// All FP64 arithmetic of the predictor, corrector and time-step criterion uses
+// explicit round-to-nearest intrinsics (__dadd_rn, __dmul_rn, __ddiv_rn,
+// __dsqrt_rn) in the order the formulas are written, so that no multiply-add
+// is contracted and the same inputs give the same bits as any IEEE FP64
+// evaluation of those formulas in that order.  This is what lets integer block
+// levels be compared bit for bit with a CPU evaluation.
+#include <climits>
+
+#include "nb_internal.cuh"
+
+namespace nbk {
+namespace {
+
+constexpr double kTick = 0x1p-40;  // one tick in N-body time units
+
+__device__ __forceinline__ double ticks_to_time(long long d)
+{
+    return __dmul_rn(__ll2double_rn(d), kTick);
+}
+
+// Hermite predictor (Section 2):
+//   x_p = x + (v + (dt/2)(a + (dt/3) k)) dt,   v_p = v + (a + (dt/2) k) dt.
+__device__ __forceinline__ void predict1(double x, double v, double a, double k, double dt,
+                                         double &xp, double &vp)
+{
+    const double h = __ddiv_rn(dt, 2.0);
+    const double q = __ddiv_rn(dt, 3.0);
+    xp = __dadd_rn(x, __dmul_rn(__dadd_rn(v, __dmul_rn(h, __dadd_rn(a, __dmul_rn(q, k)))), dt));
+    vp = __dadd_rn(v, __dmul_rn(__dadd_rn(a, __dmul_rn(h, k)), dt));
+}
+
+__device__ __forceinline__ double norm3(double u0, double u1, double u2)
+{
+    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(u0, u0), __dmul_rn(u1, u1)), __dmul_rn(u2, u2)));
+}
+
+__device__ __forceinline__ void raise_err(int *err, int code)
+{
+    atomicCAS(err, 0, code);
+}
+
+// Block level of a raw step: k of the largest 2^-k <= dt_raw, from the FP64
+// exponent field (dt_raw >= 2^-40 is a normal number), clamped to k >= kmin.
+// Returns false when dt_raw is not a number or below 2^-40.
+__device__ __forceinline__ bool level_of(double dt_raw, int kmin, int &level)
+{
+    if (isnan(dt_raw) || dt_raw < 0x1p-40) return false;
+    int k;
+    if (isinf(dt_raw)) {
+        k = kmin;
+    } else {
+        const long long bits = __double_as_longlong(dt_raw);
+        k = 1023 - (int)((bits >> 52) & 0x7FF);
+        if (k < kmin) k = kmin;
+    }
+    level = k;
+    return true;
+}
+
+// Halve at once; double by one level only when the new time is a multiple of
+// the doubled step; never above the largest step.
+__device__ __forceinline__ int next_level(int k_old, int k_q, long long t_new, int kmin)
+{
+    if (k_q > k_old) return k_q;
+    if (k_q < k_old && k_old > kmin) {
+        const long long twice_old = 1LL << (kTickBits - k_old + 1);
+        if (t_new % twice_old == 0) return k_old - 1;
+    }
+    return k_old;
+}
+
+// ---------------------------------------------------------------------------
+
+__global__ void k_predict(State s, long long t_val, const long long *t_ptr, const int *gate,
+                          int precision, JDS jds, JF64 jf)
+{
+    if (gate && *gate <= 0) return;
+    const long long tn = t_ptr ? *t_ptr : t_val;
+    const int n = s.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double dt = ticks_to_time(tn - s.t[i]);
+        double xp[3], vp[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            predict1(s.x[c * n + i], s.v[c * n + i], s.a[c * n + i], s.k[c * n + i], dt, xp[c],
+                     vp[c]);
+        const double m = s.m[i];
+        if (precision == NB_FP64) {
+            jf.pos[i] = make_double4_32a(xp[0], xp[1], xp[2], m);
+            jf.vel[i] = make_double4_32a(vp[0], vp[1], vp[2], 0.0);
+        } else {
+            float hi[3], lo[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                hi[c] = __double2float_rn(xp[c]);
+                lo[c] = __double2float_rn(__dsub_rn(xp[c], (double)hi[c]));
+            }
+            jds.pos_hi[i] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(m));
+            jds.pos_lo[i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+            jds.vel[i] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
+                                     __double2float_rn(vp[2]), 0.0f);
+        }
+    }
+}
+
+// Hermite corrector and Aarseth step for the block (Section 2).  In the
+// paper's notation a, k are the old values and a_p, k_p the new ones:
+//   a3 = 2 (a - a_p) + (k + k_p) dt,   a2 = -3 (a - a_p) - (2 k + k_p) dt,
+//   x = x_p + (a2/12 + a3/20) dt^2,    v = v_p + (a2/3 + a3/4) dt.
+// Snap s0 = 2 a2 / dt^2, crackle c = 6 a3 / dt^3, s1 = s0 + c dt, and
+//   dt_new = sqrt(eta (|a_p| |s1| + |k_p|^2) / (|k_p| |c| + |s1|^2)).
+__global__ void k_correct(State s, const int *act, int na_host, const int *na_dev, long long t_val,
+                          const long long *t_ptr, const double *acc_new, const double *jerk_new,
+                          double eta, int level_min, int level_fixed, int *err)
+{
+    const int na = na_dev ? *na_dev : na_host;
+    if (na <= 0) return;
+    const long long tn = t_ptr ? *t_ptr : t_val;
+    const int n = s.n;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < na; b += gridDim.x * blockDim.x) {
+        const int i = act[b];
+        const double dt = ticks_to_time(tn - s.t[i]);
+        double ap[3], kp[3], a2[3], a3[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ap[c] = acc_new[3 * (long long)b + c];
+            kp[c] = jerk_new[3 * (long long)b + c];
+            const double x = s.x[c * n + i], v = s.v[c * n + i];
+            const double a = s.a[c * n + i], k = s.k[c * n + i];
+            double xp, vp;
+            predict1(x, v, a, k, dt, xp, vp);
+            const double d = __dsub_rn(a, ap[c]);
+            a3[c] = __dadd_rn(__dmul_rn(2.0, d), __dmul_rn(__dadd_rn(k, kp[c]), dt));
+            a2[c] = __dsub_rn(__dmul_rn(-3.0, d), __dmul_rn(__dadd_rn(__dmul_rn(2.0, k), kp[c]), dt));
+            s.x[c * n + i] = __dadd_rn(
+                xp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[c], 12.0), __ddiv_rn(a3[c], 20.0)),
+                              __dmul_rn(dt, dt)));
+            s.v[c * n + i] =
+                __dadd_rn(vp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[c], 3.0), __ddiv_rn(a3[c], 4.0)), dt));
+            s.a[c * n + i] = ap[c];
+            s.k[c * n + i] = kp[c];
+        }
+        s.t[i] = tn;
+        if (level_fixed > 0) {
+            s.lev[i] = level_fixed;
+            continue;
+        }
+        const double dt2 = __dmul_rn(dt, dt);
+        const double dt3 = __dmul_rn(dt2, dt);
+        double s1[3], cr[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double s0 = __ddiv_rn(__dmul_rn(2.0, a2[c]), dt2);
+            cr[c] = __ddiv_rn(__dmul_rn(6.0, a3[c]), dt3);
+            s1[c] = __dadd_rn(s0, __dmul_rn(cr[c], dt));
+        }
+        const double na_ = norm3(ap[0], ap[1], ap[2]);
+        const double nk = norm3(kp[0], kp[1], kp[2]);
+        const double ns = norm3(s1[0], s1[1], s1[2]);
+        const double nc = norm3(cr[0], cr[1], cr[2]);
+        const double num = __dadd_rn(__dmul_rn(na_, ns), __dmul_rn(nk, nk));
+        const double den = __dadd_rn(__dmul_rn(nk, nc), __dmul_rn(ns, ns));
+        const double dt_raw =
+            den == 0.0 ? (double)INFINITY : __dsqrt_rn(__ddiv_rn(__dmul_rn(eta, num), den));
+        int kq;
+        if (!level_of(dt_raw, level_min, kq)) {
+            raise_err(err, NB_ESTEP);
+            kq = kTickBits;
+        }
+        s.lev[i] = next_level(s.lev[i], kq, tn, level_min);
+    }
+}
+
+// Start-up: acc and jerk from the t = 0 sweep (public layout) into the SoA
+// state, t = 0, and the initial step eta_init |a| / |k|.
+__global__ void k_initial(State s, const double *acc, const double *jerk, double eta_init,
+                          int level_min, int level_fixed, int *err)
+{
+    const int n = s.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double a[3], k[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a[c] = acc[3 * (long long)i + c];
+            k[c] = jerk[3 * (long long)i + c];
+            s.a[c * n + i] = a[c];
+            s.k[c * n + i] = k[c];
+        }
+        s.t[i] = 0;
+        if (level_fixed > 0) {
+            s.lev[i] = level_fixed;
+            continue;
+        }
+        const double nk = norm3(k[0], k[1], k[2]);
+        const double dt0 =
+            nk == 0.0 ? (double)INFINITY : __ddiv_rn(__dmul_rn(eta_init, norm3(a[0], a[1], a[2])), nk);
+        int lv;
+        if (!level_of(dt0, level_min, lv)) {
+            raise_err(err, NB_ESTEP);
+            lv = kTickBits;
+        }
+        s.lev[i] = lv;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block scheduler: t_next = min_i (t_i + 2^-lev_i) in ticks, then the block
+// {i : t_i + 2^-lev_i = t_next} compacted in ascending order by warp ballot
+// and prefix sums.  Three launches: per-chunk minimum; global minimum and
+// per-chunk counts; per-chunk exclusive offsets and scatter.
+
+constexpr int kSchedNT = 256;
+constexpr int kSchedChunk = kSchedNT * 8;
+
+__device__ __forceinline__ long long end_time(const State &s, int i)
+{
+    return s.t[i] + (1LL << (kTickBits - s.lev[i]));
+}
+
+template <typename T, typename Op>
+__device__ __forceinline__ T block_reduce(T v, Op op, T *smem)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, off));
+    __syncthreads();
+    if (lane == 0) smem[warp] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    T r = smem[0];
+    for (int w = 1; w < nw; ++w) r = op(r, smem[w]);
+    return r;
+}
+
+struct MinOp {
+    __device__ long long operator()(long long a, long long b) const { return a < b ? a : b; }
+};
+struct SumOp {
+    template <typename T>
+    __device__ T operator()(T a, T b) const { return a + b; }
+};
+
+__global__ void k_sched_min(State s, long long *blockmin)
+{
+    __shared__ long long sm[kSchedNT / 32];
+    const int lo = blockIdx.x * kSchedChunk;
+    const int hi = min(s.n, lo + kSchedChunk);
+    long long m = LLONG_MAX;
+    for (int i = lo + threadIdx.x; i < hi; i += kSchedNT) m = min(m, end_time(s, i));
+    m = block_reduce(m, MinOp(), sm);
+    if (threadIdx.x == 0) blockmin[blockIdx.x] = m;
+}
+
+__global__ void k_sched_count(State s, Ctrl *ctrl, const long long *blockmin, int *blockcnt,
+                              int nblocks)
+{
+    __shared__ long long sm[kSchedNT / 32];
+    __shared__ int si[kSchedNT / 32];
+    long long tn = LLONG_MAX;
+    for (int b = threadIdx.x; b < nblocks; b += kSchedNT) tn = min(tn, blockmin[b]);
+    tn = block_reduce(tn, MinOp(), sm);
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->t_next = tn;
+    const bool done = tn > ctrl->t_end;
+    const int lo = blockIdx.x * kSchedChunk;
+    const int hi = min(s.n, lo + kSchedChunk);
+    int cnt = 0;
+    if (!done)
+        for (int i = lo + threadIdx.x; i < hi; i += kSchedNT) cnt += end_time(s, i) == tn;
+    cnt = block_reduce(cnt, SumOp(), si);
+    if (threadIdx.x == 0) blockcnt[blockIdx.x] = cnt;
+}
+
+__global__ void k_sched_scatter(State s, Ctrl *ctrl, const int *blockcnt, int *act, int nblocks)
+{
+    __shared__ int si[kSchedNT / 32];
+    __shared__ int wtot[kSchedNT / 32];
+    const long long tn = ctrl->t_next;
+    const bool done = tn > ctrl->t_end;
+    int pre = 0;
+    for (int b = threadIdx.x; b < blockIdx.x; b += kSchedNT) pre += blockcnt[b];
+    pre = block_reduce(pre, SumOp(), si);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lo = blockIdx.x * kSchedChunk;
+    const int hi = min(s.n, lo + kSchedChunk);
+    int running = 0;
+    if (!done) {
+        for (int base = lo; base < hi; base += kSchedNT) {
+            const int i = base + threadIdx.x;
+            const bool f = i < hi && end_time(s, i) == tn;
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            const int below = __popc(bal & ((1u << lane) - 1u));
+            __syncthreads();
+            if (lane == 0) wtot[warp] = __popc(bal);
+            __syncthreads();
+            int woff = 0, tot = 0;
+            for (int w = 0; w < kSchedNT / 32; ++w) {
+                if (w < warp) woff += wtot[w];
+                tot += wtot[w];
+            }
+            if (f) act[pre + running + woff + below] = i;
+            running += tot;
+        }
+    }
+    if (blockIdx.x == nblocks - 1 && threadIdx.x == 0) {
+        const int total = pre + running;
+        ctrl->n_active = total;
+        if (total > 0) {
+            ctrl->t_now = tn;
+            ctrl->steps += 1;
+            ctrl->interactions += (long long)total * (long long)(s.n - 1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Energy: T = 1/2 sum m v_p^2 with v predicted to the system time, and
+// W = 1/2 sum m_i pot_i; per-block FP64 partials, then one block sums them in
+// block order (deterministic).
+
+constexpr int kEnNT = 256;
+
+__global__ void k_energy_partial(State s, const long long *t_ptr, const double *pot, double *part)
+{
+    __shared__ double sm[kEnNT / 32];
+    const long long tn = *t_ptr;
+    const int n = s.n;
+    double ke = 0.0, pe = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double dt = ticks_to_time(tn - s.t[i]);
+        double v2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double xp, vp;
+            predict1(s.x[c * n + i], s.v[c * n + i], s.a[c * n + i], s.k[c * n + i], dt, xp, vp);
+            v2 += vp * vp;
+        }
+        ke += 0.5 * s.m[i] * v2;
+        pe += 0.5 * s.m[i] * pot[i];
+    }
+    ke = block_reduce(ke, SumOp(), sm);
+    pe = block_reduce(pe, SumOp(), sm);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = ke;
+        part[2 * blockIdx.x + 1] = pe;
+    }
+}
+
+__global__ void k_energy_final(const double *part, int nblocks, Ctrl *ctrl)
+{
+    __shared__ double sm[kEnNT / 32];
+    double ke = 0.0, pe = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += kEnNT) {
+        ke += part[2 * b];
+        pe += part[2 * b + 1];
+    }
+    ke = block_reduce(ke, SumOp(), sm);
+    pe = block_reduce(pe, SumOp(), sm);
+    if (threadIdx.x == 0) {
+        ctrl->ekin = ke;
+        ctrl->epot = pe;
+    }
+}
+
+// ---------------------------------------------------------------------------
+
+__global__ void k_validate(const int *idx, int na, int n, unsigned int *bitmap, int *err)
+{
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < na; a += gridDim.x * blockDim.x) {
+        const int i = idx[a];
+        if (i < 0 || i >= n) {
+            raise_err(err, NB_EINVAL);
+            continue;
+        }
+        const unsigned bit = 1u << (i & 31);
+        if (atomicOr(&bitmap[i >> 5], bit) & bit) raise_err(err, NB_EINVAL);
+    }
+}
+
+__global__ void k_gather_state(State s, double *x, double *v, double *a, double *k)
+{
+    const int n = s.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (x) x[3 * (long long)i + c] = s.x[c * n + i];
+            if (v) v[3 * (long long)i + c] = s.v[c * n + i];
+            if (a) a[3 * (long long)i + c] = s.a[c * n + i];
+            if (k) k[3 * (long long)i + c] = s.k[c * n + i];
+        }
+}
+
+__global__ void k_scatter_state(State s, const double *x, const double *v, const double *a,
+                                const double *k)
+{
+    const int n = s.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (x) s.x[c * n + i] = x[3 * (long long)i + c];
+            if (v) s.v[c * n + i] = v[3 * (long long)i + c];
+            if (a) s.a[c * n + i] = a[3 * (long long)i + c];
+            if (k) s.k[c * n + i] = k[3 * (long long)i + c];
+        }
+}
+
+__global__ void k_iota(int *p, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = i;
+}
+
+int grid_for(long long n, int nt)
+{
+    long long g = (n + nt - 1) / nt;
+    if (g < 1) g = 1;
+    if (g > 8192) g = 8192;
+    return (int)g;
+}
+
+}  // namespace
+
+void launch_predict(const State &s, long long t_val, const long long *t_ptr, const int *gate,
+                    int precision, JDS jds, JF64 jf, cudaStream_t st)
+{
+    k_predict<<<grid_for(s.n, 256), 256, 0, st>>>(s, t_val, t_ptr, gate, precision, jds, jf);
+}
+
+void launch_correct(const State &s, const int *act, int na_host, const int *na_dev, long long t_val,
+                    const long long *t_ptr, const double *acc_new, const double *jerk_new,
+                    double eta, int level_min, int level_fixed, int *err, cudaStream_t st)
+{
+    const int g = na_dev ? grid_for(s.n, 128) : grid_for(na_host, 128);
+    k_correct<<<g, 128, 0, st>>>(s, act, na_host, na_dev, t_val, t_ptr, acc_new, jerk_new, eta,
+                                 level_min, level_fixed, err);
+}
+
+void launch_initial_steps(const State &s, const double *acc, const double *jerk, double eta_init,
+                          int level_min, int level_fixed, int *err, cudaStream_t st)
+{
+    k_initial<<<grid_for(s.n, 256), 256, 0, st>>>(s, acc, jerk, eta_init, level_min, level_fixed, err);
+}
+
+int schedule_blocks(int n) { return cdiv(n, kSchedChunk); }
+
+void launch_schedule(const State &s, Ctrl *ctrl, long long *blockmin, int *blockcnt, int *act,
+                     int nblocks, cudaStream_t st)
+{
+    k_sched_min<<<nblocks, kSchedNT, 0, st>>>(s, blockmin);
+    k_sched_count<<<nblocks, kSchedNT, 0, st>>>(s, ctrl, blockmin, blockcnt, nblocks);
+    k_sched_scatter<<<nblocks, kSchedNT, 0, st>>>(s, ctrl, blockcnt, act, nblocks);
+}
+
+int energy_blocks(int n)
+{
+    int g = cdiv(n, kEnNT * 8);
+    return g < 1 ? 1 : (g > 1024 ? 1024 : g);
+}
+
+void launch_energy(const State &s, const long long *t_ptr, const double *pot, double *part,
+                   Ctrl *ctrl, cudaStream_t st)
+{
+    const int nb = energy_blocks(s.n);
+    k_energy_partial<<<nb, kEnNT, 0, st>>>(s, t_ptr, pot, part);
+    k_energy_final<<<1, kEnNT, 0, st>>>(part, nb, ctrl);
+}
+
+void launch_validate(const int *idx, int na, int n, unsigned int *bitmap, int *err, cudaStream_t st)
+{
+    if (na <= 0) return;
+    k_validate<<<grid_for(na, 256), 256, 0, st>>>(idx, na, n, bitmap, err);
+}
+
+void launch_gather_state(const State &s, double *x, double *v, double *a, double *k, cudaStream_t st)
+{
+    k_gather_state<<<grid_for(s.n, 256), 256, 0, st>>>(s, x, v, a, k);
+}
+
+void launch_scatter_state(const State &s, const double *x, const double *v, const double *a,
+                          const double *k, cudaStream_t st)
+{
+    k_scatter_state<<<grid_for(s.n, 256), 256, 0, st>>>(s, x, v, a, k);
+}
+
+void launch_iota(int *p, int n, cudaStream_t st)
+{
+    k_iota<<<grid_for(n, 256), 256, 0, st>>>(p, n);
+}
+
+}  // namespace nbk

@@ -1,0 +1,660 @@
+// nb_api.cu -- the C ABI declared in include/nb.h: context, argument checks,
+// host-driven calls (nb_predict / nb_force / nb_correct) and the device-driven
+// block step (nb_step / nb_run) replayed from a captured CUDA graph.
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nb_internal.cuh"
+
+using namespace nbk;
+
+struct nb_ctx {
+    int n = 0;
+    double eps = 0.0;
+    nb_opts o{};
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int sms = 0;
+
+    State S{};
+    double *d_x = nullptr, *d_v = nullptr, *d_a = nullptr, *d_k = nullptr, *d_m = nullptr;
+    long long *d_t = nullptr;
+    int *d_lev = nullptr;
+    JDS jds{};
+    JF64 jf{};
+    double *d_res = nullptr;        // force results: acc [n][3], jerk [n][3], pot [n]
+    double *d_part = nullptr;       // slice partials
+    long long part_cap = 0;
+    int *d_act = nullptr;           // block of the device-driven step
+    int *d_idx = nullptr;           // indices passed by the host-driven calls
+    int *d_all = nullptr;           // 0 .. n-1
+    unsigned *d_bitmap = nullptr;   // index validation
+    Ctrl *d_ctrl = nullptr;
+    Ctrl *h_ctrl = nullptr;         // pinned mirror
+    long long *d_blockmin = nullptr;
+    int *d_blockcnt = nullptr;
+    int nsched = 0;
+    double *d_epart = nullptr;
+    double *d_stage = nullptr;      // [7n] staging for host I/O
+
+    int slots_ipar = 0, slots_jpar = 0, jpar_max = 0;
+    long long t_pred = 0;           // ticks of the last host-driven prediction
+    bool force_valid = false;       // results in d_res usable by nb_correct
+    int force_na = 0;
+    long long force_t = 0;
+    long long t_end_dev = -1;       // value of ctrl->t_end on the device
+    cudaGraphExec_t step_exec = nullptr;
+    std::string err;
+};
+
+namespace {
+
+const char *const kNoCtx = "null context";
+thread_local std::string g_init_err;  // message of the last failed nb_init on this thread
+
+int fail(nb_ctx *c, int code, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? NB_ENOMEM : NB_ECUDA,        \
+                        "%s: %s", #call, cudaGetErrorString(e_));                         \
+    } while (0)
+
+bool finite_all(const double *p, long long cnt)
+{
+    for (long long i = 0; i < cnt; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+// Converts a time to ticks of 2^-40; false if off the grid or out of range.
+bool time_to_ticks(double t, long long *ticks)
+{
+    if (!std::isfinite(t) || t < 0.0 || t >= 0x1p22) return false;
+    const double s = t * 0x1p40;
+    if (s != std::floor(s)) return false;
+    *ticks = (long long)s;
+    return true;
+}
+
+int check_indices_host(nb_ctx *c, const int32_t *idx, int32_t na)
+{
+    if (na < 0 || na > c->n) return fail(c, NB_EINVAL, "n_active=%d outside [0, %d]", na, c->n);
+    if (na > 0 && !idx) return fail(c, NB_EINVAL, "active_idx is NULL");
+    std::vector<unsigned char> seen((size_t)c->n, 0);
+    for (int32_t a = 0; a < na; ++a) {
+        const int32_t i = idx[a];
+        if (i < 0 || i >= c->n) return fail(c, NB_EINVAL, "active_idx[%d]=%d out of range", a, i);
+        if (seen[(size_t)i]) return fail(c, NB_EINVAL, "active_idx[%d]=%d repeated", a, i);
+        seen[(size_t)i] = 1;
+    }
+    return NB_OK;
+}
+
+// Pulls the control block to the host and turns a kernel-raised error into a
+// return code (clearing it on the device).
+int sync_ctrl(nb_ctx *c)
+{
+    CK(cudaMemcpyAsync(c->h_ctrl, c->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    CK(cudaGetLastError());
+    const int e = c->h_ctrl->err;
+    if (e != 0) {
+        CK(cudaMemsetAsync(&c->d_ctrl->err, 0, sizeof(int), c->st));
+        CK(cudaStreamSynchronize(c->st));
+        if (e == NB_ESTEP) return fail(c, NB_ESTEP, "a new time step fell below 2^-40");
+        if (e == NB_EINVAL) return fail(c, NB_EINVAL, "invalid particle index (device check)");
+        return fail(c, e, "device error %d", e);
+    }
+    return NB_OK;
+}
+
+ForceArgs force_args(nb_ctx *c, const int *act, int na_host, const int *na_dev, ForceOut out)
+{
+    ForceArgs fa{};
+    fa.n = c->n;
+    fa.act = act;
+    fa.na_dev = na_dev;
+    fa.na_host = na_host;
+    fa.jpar_max = c->jpar_max;
+    fa.split = c->o.split_j;
+    fa.slots_ipar = c->slots_ipar;
+    fa.slots_jpar = c->slots_jpar;
+    fa.part_cap = c->part_cap;
+    fa.part = c->d_part;
+    fa.out = out;
+    fa.eps2 = c->eps * c->eps;
+    fa.err = &c->d_ctrl->err;
+    return fa;
+}
+
+ForceOut res_out(nb_ctx *c)
+{
+    ForceOut o;
+    o.acc = c->d_res;
+    o.jerk = c->d_res + 3LL * c->n;
+    o.pot = c->d_res + 6LL * c->n;
+    return o;
+}
+
+// Enqueues the force on `act`.  With na_dev the block size is read on the
+// device and both kernels are launched with persistent grids; otherwise only
+// the kernel that serves na_host is launched, sized to its work.
+void enqueue_force(nb_ctx *c, const int *act, int na_host, const int *na_dev, ForceOut out)
+{
+    const ForceArgs fa = force_args(c, act, na_host, na_dev, out);
+    const bool f64 = c->o.precision == NB_FP64;
+    const int iblk = kIparNT * (f64 ? kIparR64 : kIparR);
+    int gi = c->slots_ipar, gj = c->slots_jpar;
+    if (!na_dev) {
+        if (na_host <= 0) return;
+        if (use_jpar(na_host, c->jpar_max)) {
+            const Plan p = plan_jpar(na_host, c->n, kJparNT, kJparIC, c->slots_jpar, c->part_cap);
+            gi = 0;
+            gj = p.items < c->slots_jpar ? p.items : c->slots_jpar;
+        } else {
+            const Plan p = plan_ipar(na_host, c->n, iblk, kIparNT, c->slots_ipar, c->o.split_j,
+                                     c->part_cap);
+            gj = 0;
+            gi = p.items < c->slots_ipar ? p.items : c->slots_ipar;
+        }
+    }
+    if (f64)
+        launch_force_f64(fa, c->jf, c->eps > 0.0, gi, gj, c->st);
+    else
+        launch_force_ds(fa, c->jds, c->eps > 0.0, gi, gj, c->st);
+}
+
+// The device-driven block step: schedule, predict all, force, correct.
+void enqueue_step(nb_ctx *c)
+{
+    launch_schedule(c->S, c->d_ctrl, c->d_blockmin, c->d_blockcnt, c->d_act, c->nsched, c->st);
+    launch_predict(c->S, 0, &c->d_ctrl->t_next, &c->d_ctrl->n_active, c->o.precision, c->jds,
+                   c->jf, c->st);
+    enqueue_force(c, c->d_act, 0, &c->d_ctrl->n_active, res_out(c));
+    launch_correct(c->S, c->d_act, 0, &c->d_ctrl->n_active, 0, &c->d_ctrl->t_next, c->d_res,
+                   c->d_res + 3LL * c->n, c->o.eta, c->o.level_min, c->o.level_fixed,
+                   &c->d_ctrl->err, c->st);
+}
+
+int set_t_end(nb_ctx *c, long long t_end)
+{
+    if (c->t_end_dev == t_end) return NB_OK;
+    CK(cudaStreamSynchronize(c->st));
+    c->h_ctrl->t_end = t_end;
+    CK(cudaMemcpyAsync(&c->d_ctrl->t_end, &c->h_ctrl->t_end, sizeof(long long),
+                       cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->t_end_dev = t_end;
+    return NB_OK;
+}
+
+template <typename T>
+int dalloc(nb_ctx *c, T **p, long long count)
+{
+    if (count < 1) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (size_t)count);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(c, NB_ENOMEM, "cudaMalloc of %lld bytes failed: %s",
+                    (long long)(sizeof(T) * count), cudaGetErrorString(e));
+    }
+    return NB_OK;
+}
+
+void release(nb_ctx *c)
+{
+    if (c->st) cudaStreamSynchronize(c->st);
+    if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+    void *ptrs[] = {c->d_x, c->d_v, c->d_a, c->d_k, c->d_m, c->d_t, c->d_lev, c->jds.pos_hi,
+                    c->jds.pos_lo, c->jds.vel, c->jf.pos, c->jf.vel, c->d_res, c->d_part,
+                    c->d_act, c->d_idx, c->d_all, c->d_bitmap, c->d_ctrl, c->d_blockmin,
+                    c->d_blockcnt, c->d_epart, c->d_stage};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
+    if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+}
+
+// Full sweep on all particles into d_res (predicted state must be current).
+void enqueue_full_sweep(nb_ctx *c) { enqueue_force(c, c->d_all, c->n, nullptr, res_out(c)); }
+
+int copy_results_out(nb_ctx *c, int na, double *acc, double *jerk, double *pot, cudaMemcpyKind k)
+{
+    if (na <= 0) return NB_OK;
+    if (acc) CK(cudaMemcpyAsync(acc, c->d_res, sizeof(double) * 3 * (size_t)na, k, c->st));
+    if (jerk)
+        CK(cudaMemcpyAsync(jerk, c->d_res + 3LL * c->n, sizeof(double) * 3 * (size_t)na, k, c->st));
+    if (pot) CK(cudaMemcpyAsync(pot, c->d_res + 6LL * c->n, sizeof(double) * (size_t)na, k, c->st));
+    return NB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nb_default_opts(nb_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->eta = 0.01;
+    o->eta_init = 0.01;
+    o->level_min = 3;
+    o->level_fixed = 0;
+    o->precision = NB_DS;
+    o->force_mode = NB_FORCE_AUTO;
+    o->split_j = 0;
+    o->stream = nullptr;
+}
+
+int64_t nb_num_particles(const nb_ctx *c) { return c ? c->n : -1; }
+
+const char *nb_last_error(const nb_ctx *c)
+{
+    if (c) return c->err.c_str();
+    return g_init_err.empty() ? kNoCtx : g_init_err.c_str();
+}
+
+void nb_free(nb_ctx *c)
+{
+    if (!c) return;
+    release(c);
+    delete c;
+}
+
+static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, const double *v,
+                     double eps, const nb_opts *opts)
+{
+    nb_opts o;
+    nb_default_opts(&o);
+    if (opts) o = *opts;
+    if (n < 1 || n > INT_MAX / 8) return fail(c, NB_EINVAL, "n=%lld out of range", (long long)n);
+    if (!m || !x || !v) return fail(c, NB_EINVAL, "m, x and v are required");
+    if (!std::isfinite(eps) || eps < 0.0) return fail(c, NB_EINVAL, "eps must be finite and >= 0");
+    if (!(o.eta > 0.0) || !std::isfinite(o.eta) || !(o.eta_init > 0.0) || !std::isfinite(o.eta_init))
+        return fail(c, NB_EINVAL, "eta and eta_init must be positive");
+    if (o.level_min < 0 || o.level_min > kTickBits)
+        return fail(c, NB_EINVAL, "level_min must lie in [0, 40]");
+    if (o.level_fixed < 0 || o.level_fixed > kTickBits ||
+        (o.level_fixed > 0 && o.level_fixed < o.level_min))
+        return fail(c, NB_EINVAL, "level_fixed must be 0 or in [level_min, 40]");
+    if (o.precision != NB_DS && o.precision != NB_FP64)
+        return fail(c, NB_EINVAL, "precision must be NB_DS or NB_FP64");
+    if (o.force_mode < NB_FORCE_AUTO || o.force_mode > NB_FORCE_JPAR)
+        return fail(c, NB_EINVAL, "bad force_mode");
+    if (o.split_j < 0 || o.reserved != 0) return fail(c, NB_EINVAL, "bad split_j or reserved");
+    if (!finite_all(m, n) || !finite_all(x, 3 * n) || !finite_all(v, 3 * n))
+        return fail(c, NB_EINVAL, "non-finite input");
+    for (int64_t i = 0; i < n; ++i)
+        if (m[i] < 0.0) return fail(c, NB_EINVAL, "negative mass at %lld", (long long)i);
+
+    c->n = (int)n;
+    c->eps = eps;
+    c->o = o;
+    if (o.stream) {
+        c->st = (cudaStream_t)o.stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+    const bool f64 = o.precision == NB_FP64;
+    int bi = 0, bj = 0;
+    if (occupancy_force(o.precision, false, &bi) || occupancy_force(o.precision, true, &bj))
+        return fail(c, NB_ECUDA, "occupancy query failed");
+    c->slots_ipar = c->sms * (bi > 0 ? bi : 1);
+    c->slots_jpar = c->sms * (bj > 0 ? bj : 1);
+    c->jpar_max = o.force_mode == NB_FORCE_IPAR ? 0
+                  : o.force_mode == NB_FORCE_JPAR ? INT_MAX
+                                                  : kJparMaxActive;
+    const long long iblk = kIparNT * (f64 ? kIparR64 : kIparR);
+    long long cap_i = 4LL * c->slots_ipar * iblk;
+    long long cap_j = 8LL * c->slots_jpar * kJparIC;
+    c->part_cap = (long long)kComp * (cap_i > cap_j ? cap_i : cap_j);
+    c->nsched = schedule_blocks(c->n);
+
+    int rc;
+    const long long N = c->n;
+    if ((rc = dalloc(c, &c->d_x, 3 * N)) || (rc = dalloc(c, &c->d_v, 3 * N)) ||
+        (rc = dalloc(c, &c->d_a, 3 * N)) || (rc = dalloc(c, &c->d_k, 3 * N)) ||
+        (rc = dalloc(c, &c->d_m, N)) || (rc = dalloc(c, &c->d_t, N)) ||
+        (rc = dalloc(c, &c->d_lev, N)) || (rc = dalloc(c, &c->d_res, 7 * N)) ||
+        (rc = dalloc(c, &c->d_part, c->part_cap)) || (rc = dalloc(c, &c->d_act, N)) ||
+        (rc = dalloc(c, &c->d_idx, N)) || (rc = dalloc(c, &c->d_all, N)) ||
+        (rc = dalloc(c, &c->d_bitmap, (N + 31) / 32)) || (rc = dalloc(c, &c->d_ctrl, 1)) ||
+        (rc = dalloc(c, &c->d_blockmin, c->nsched)) || (rc = dalloc(c, &c->d_blockcnt, c->nsched)) ||
+        (rc = dalloc(c, &c->d_epart, 2LL * energy_blocks(c->n))) ||
+        (rc = dalloc(c, &c->d_stage, 7 * N)))
+        return rc;
+    if (f64) {
+        if ((rc = dalloc(c, &c->jf.pos, N)) || (rc = dalloc(c, &c->jf.vel, N))) return rc;
+    } else {
+        if ((rc = dalloc(c, &c->jds.pos_hi, N)) || (rc = dalloc(c, &c->jds.pos_lo, N)) ||
+            (rc = dalloc(c, &c->jds.vel, N)))
+            return rc;
+    }
+    cudaError_t he = cudaMallocHost((void **)&c->h_ctrl, sizeof(Ctrl));
+    if (he != cudaSuccess) {
+        c->h_ctrl = nullptr;
+        return fail(c, NB_ENOMEM, "cudaMallocHost failed: %s", cudaGetErrorString(he));
+    }
+    std::memset(c->h_ctrl, 0, sizeof(Ctrl));
+    c->h_ctrl->t_end = LLONG_MAX;
+    c->t_end_dev = LLONG_MAX;
+
+    c->S.x = c->d_x;
+    c->S.v = c->d_v;
+    c->S.a = c->d_a;
+    c->S.k = c->d_k;
+    c->S.m = c->d_m;
+    c->S.t = c->d_t;
+    c->S.lev = c->d_lev;
+    c->S.n = c->n;
+
+    CK(cudaMemcpyAsync(c->d_ctrl, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemsetAsync(c->d_a, 0, sizeof(double) * 3 * N, c->st));
+    CK(cudaMemsetAsync(c->d_k, 0, sizeof(double) * 3 * N, c->st));
+    CK(cudaMemsetAsync(c->d_t, 0, sizeof(long long) * N, c->st));
+    CK(cudaMemcpyAsync(c->d_m, m, sizeof(double) * N, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->d_stage, x, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->d_stage + 3 * N, v, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));
+    launch_scatter_state(c->S, c->d_stage, c->d_stage + 3 * N, nullptr, nullptr, c->st);
+    launch_iota(c->d_all, c->n, c->st);
+    launch_predict(c->S, 0, nullptr, nullptr, o.precision, c->jds, c->jf, c->st);
+    enqueue_full_sweep(c);
+    launch_initial_steps(c->S, c->d_res, c->d_res + 3 * N, o.eta_init, o.level_min, o.level_fixed,
+                         &c->d_ctrl->err, c->st);
+    CK(cudaGetLastError());
+    c->t_pred = 0;
+    c->force_valid = false;
+    return sync_ctrl(c);
+}
+
+int nb_init(nb_ctx **ctx, int64_t n, const double *m, const double *x, const double *v,
+            double eps, const nb_opts *opts)
+{
+    g_init_err.clear();
+    if (!ctx) {
+        g_init_err = "ctx is NULL";
+        return NB_EINVAL;
+    }
+    *ctx = nullptr;
+    nb_ctx *c = new (std::nothrow) nb_ctx();
+    if (!c) {
+        g_init_err = "out of host memory";
+        return NB_ENOMEM;
+    }
+    const int rc = init_impl(c, n, m, x, v, eps, opts);
+    if (rc != NB_OK) {
+        g_init_err = c->err;  // readable through nb_last_error(NULL)
+        nb_free(c);
+        return rc;
+    }
+    *ctx = c;
+    return NB_OK;
+}
+
+int nb_predict(nb_ctx *c, double t)
+{
+    if (!c) return NB_EINVAL;
+    long long ticks;
+    if (!time_to_ticks(t, &ticks)) return fail(c, NB_EINVAL, "t=%.17g is not on the 2^-40 grid", t);
+    launch_predict(c->S, ticks, nullptr, nullptr, c->o.precision, c->jds, c->jf, c->st);
+    CK(cudaGetLastError());
+    c->t_pred = ticks;
+    c->force_valid = false;
+    return NB_OK;
+}
+
+int nb_force(nb_ctx *c, const int32_t *idx, int32_t na, double *acc, double *jerk, double *pot)
+{
+    if (!c) return NB_EINVAL;
+    int rc = check_indices_host(c, idx, na);
+    if (rc) return rc;
+    if (na > 0) {
+        CK(cudaMemcpyAsync(c->d_idx, idx, sizeof(int) * (size_t)na, cudaMemcpyHostToDevice, c->st));
+        enqueue_force(c, c->d_idx, na, nullptr, res_out(c));
+        CK(cudaGetLastError());
+        if ((rc = copy_results_out(c, na, acc, jerk, pot, cudaMemcpyDeviceToHost))) return rc;
+    }
+    CK(cudaStreamSynchronize(c->st));
+    c->force_valid = true;
+    c->force_na = na;
+    c->force_t = c->t_pred;
+    return NB_OK;
+}
+
+int nb_force_dev(nb_ctx *c, const int32_t *d_idx, int32_t na, double *d_acc, double *d_jerk,
+                 double *d_pot)
+{
+    if (!c) return NB_EINVAL;
+    if (na < 0 || na > c->n) return fail(c, NB_EINVAL, "n_active=%d outside [0, %d]", na, c->n);
+    if (na > 0 && !d_idx) return fail(c, NB_EINVAL, "active_idx is NULL");
+    if (na > 0) {
+        CK(cudaMemsetAsync(c->d_bitmap, 0, sizeof(unsigned) * (size_t)((c->n + 31) / 32), c->st));
+        launch_validate(d_idx, na, c->n, c->d_bitmap, &c->d_ctrl->err, c->st);
+        int rc = sync_ctrl(c);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(c->d_idx, d_idx, sizeof(int) * (size_t)na, cudaMemcpyDeviceToDevice,
+                           c->st));
+        enqueue_force(c, c->d_idx, na, nullptr, res_out(c));
+        CK(cudaGetLastError());
+        if ((rc = copy_results_out(c, na, d_acc, d_jerk, d_pot, cudaMemcpyDeviceToDevice))) return rc;
+    }
+    c->force_valid = true;
+    c->force_na = na;
+    c->force_t = c->t_pred;
+    return NB_OK;
+}
+
+int nb_correct(nb_ctx *c, const int32_t *idx, int32_t na, double t, const double *acc,
+               const double *jerk)
+{
+    if (!c) return NB_EINVAL;
+    long long ticks;
+    if (!time_to_ticks(t, &ticks)) return fail(c, NB_EINVAL, "t=%.17g is not on the 2^-40 grid", t);
+    int rc = check_indices_host(c, idx, na);
+    if (rc) return rc;
+    if ((acc == nullptr) != (jerk == nullptr))
+        return fail(c, NB_EINVAL, "acc and jerk must be given together");
+    if (!acc && (!c->force_valid || c->force_na != na || c->force_t != ticks))
+        return fail(c, NB_ESTATE, "nb_correct needs a preceding nb_force on %d particles at t", na);
+    if (na == 0) return NB_OK;
+    const long long N = c->n;
+    const double *an = c->d_res, *kn = c->d_res + 3 * N;
+    if (acc) {
+        if (!finite_all(acc, 3LL * na) || !finite_all(jerk, 3LL * na))
+            return fail(c, NB_EINVAL, "non-finite acc or jerk");
+        CK(cudaMemcpyAsync(c->d_stage, acc, sizeof(double) * 3 * (size_t)na, cudaMemcpyHostToDevice,
+                           c->st));
+        CK(cudaMemcpyAsync(c->d_stage + 3 * N, jerk, sizeof(double) * 3 * (size_t)na,
+                           cudaMemcpyHostToDevice, c->st));
+        an = c->d_stage;
+        kn = c->d_stage + 3 * N;
+    }
+    CK(cudaMemcpyAsync(c->d_idx, idx, sizeof(int) * (size_t)na, cudaMemcpyHostToDevice, c->st));
+    launch_correct(c->S, c->d_idx, na, nullptr, ticks, nullptr, an, kn, c->o.eta, c->o.level_min,
+                   c->o.level_fixed, &c->d_ctrl->err, c->st);
+    CK(cudaGetLastError());
+    c->force_valid = false;
+    if ((rc = sync_ctrl(c))) return rc;
+    if (ticks > c->h_ctrl->t_now) {
+        // the system time follows the latest corrected block
+        c->h_ctrl->t_now = ticks;
+        CK(cudaMemcpyAsync(&c->d_ctrl->t_now, &c->h_ctrl->t_now, sizeof(long long),
+                           cudaMemcpyHostToDevice, c->st));
+        CK(cudaStreamSynchronize(c->st));
+    }
+    return NB_OK;
+}
+
+int nb_step(nb_ctx *c, double *t_out, int32_t *na_out)
+{
+    if (!c) return NB_EINVAL;
+    int rc = set_t_end(c, LLONG_MAX);
+    if (rc) return rc;
+    enqueue_step(c);
+    CK(cudaGetLastError());
+    c->force_valid = false;
+    if (t_out || na_out) {
+        if ((rc = sync_ctrl(c))) return rc;
+        if (t_out) *t_out = (double)c->h_ctrl->t_now * 0x1p-40;
+        if (na_out) *na_out = c->h_ctrl->n_active;
+    }
+    return NB_OK;
+}
+
+int nb_run(nb_ctx *c, double t_end, int64_t max_steps, int64_t *steps_out, int64_t *inter_out)
+{
+    if (!c) return NB_EINVAL;
+    long long te;
+    if (!time_to_ticks(t_end, &te)) return fail(c, NB_EINVAL, "t_end is not on the 2^-40 grid");
+    if (max_steps < 0) return fail(c, NB_EINVAL, "max_steps < 0");
+    int rc = set_t_end(c, te);
+    if (rc) return rc;
+    if ((rc = sync_ctrl(c))) return rc;
+    const long long steps0 = c->h_ctrl->steps, inter0 = c->h_ctrl->interactions;
+    if (!c->step_exec) {
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+        enqueue_step(c);
+        cudaError_t e = cudaStreamEndCapture(c->st, &g);
+        if (e != cudaSuccess) return fail(c, NB_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->step_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->step_exec = nullptr;
+            return fail(c, NB_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    c->force_valid = false;
+    long long done = 0;
+    const int batch = 32;
+    while (done < max_steps) {
+        const long long k = (max_steps - done) < batch ? (max_steps - done) : batch;
+        for (long long s = 0; s < k; ++s) CK(cudaGraphLaunch(c->step_exec, c->st));
+        if ((rc = sync_ctrl(c))) return rc;
+        done = c->h_ctrl->steps - steps0;
+        if (c->h_ctrl->n_active == 0) break;
+    }
+    if (steps_out) *steps_out = c->h_ctrl->steps - steps0;
+    if (inter_out) *inter_out = c->h_ctrl->interactions - inter0;
+    return set_t_end(c, LLONG_MAX);
+}
+
+int nb_energy(nb_ctx *c, double *ekin, double *epot)
+{
+    if (!c) return NB_EINVAL;
+    launch_predict(c->S, 0, &c->d_ctrl->t_now, nullptr, c->o.precision, c->jds, c->jf, c->st);
+    enqueue_full_sweep(c);
+    launch_energy(c->S, &c->d_ctrl->t_now, c->d_res + 6LL * c->n, c->d_epart, c->d_ctrl, c->st);
+    CK(cudaGetLastError());
+    c->force_valid = false;
+    const int rc = sync_ctrl(c);
+    if (rc) return rc;
+    if (ekin) *ekin = c->h_ctrl->ekin;
+    if (epot) *epot = c->h_ctrl->epot;
+    return NB_OK;
+}
+
+int nb_get_state(nb_ctx *c, double *x, double *v, double *a, double *k, int64_t *t, int32_t *lev)
+{
+    if (!c) return NB_EINVAL;
+    const long long N = c->n;
+    launch_gather_state(c->S, c->d_stage, c->d_stage + 3 * N, nullptr, nullptr, c->st);
+    CK(cudaGetLastError());
+    if (x) CK(cudaMemcpyAsync(x, c->d_stage, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->st));
+    if (v)
+        CK(cudaMemcpyAsync(v, c->d_stage + 3 * N, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (a || k) {
+        launch_gather_state(c->S, nullptr, nullptr, c->d_stage, c->d_stage + 3 * N, c->st);
+        CK(cudaGetLastError());
+        if (a) CK(cudaMemcpyAsync(a, c->d_stage, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->st));
+        if (k)
+            CK(cudaMemcpyAsync(k, c->d_stage + 3 * N, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost,
+                               c->st));
+    }
+    if (t) CK(cudaMemcpyAsync(t, c->d_t, sizeof(long long) * N, cudaMemcpyDeviceToHost, c->st));
+    if (lev) CK(cudaMemcpyAsync(lev, c->d_lev, sizeof(int) * N, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return NB_OK;
+}
+
+int nb_set_state(nb_ctx *c, const double *x, const double *v, const double *a, const double *k,
+                 const int64_t *t, const int32_t *lev)
+{
+    if (!c) return NB_EINVAL;
+    if (!x || !v || !a || !k || !t || !lev) return fail(c, NB_EINVAL, "all state arrays are required");
+    const long long N = c->n;
+    if (!finite_all(x, 3 * N) || !finite_all(v, 3 * N) || !finite_all(a, 3 * N) ||
+        !finite_all(k, 3 * N))
+        return fail(c, NB_EINVAL, "non-finite state");
+    long long t_max = 0;
+    for (long long i = 0; i < N; ++i) {
+        if (lev[i] < c->o.level_min || lev[i] > kTickBits)
+            return fail(c, NB_EINVAL, "level[%lld]=%d outside [%d, 40]", i, lev[i], c->o.level_min);
+        const long long dt = 1LL << (kTickBits - lev[i]);
+        if (t[i] < 0 || t[i] % dt != 0 || t[i] > (1LL << 62))
+            return fail(c, NB_EINVAL, "t_ticks[%lld] is not a multiple of its step", i);
+        if (t[i] > t_max) t_max = t[i];
+    }
+    CK(cudaStreamSynchronize(c->st));
+    CK(cudaMemcpyAsync(c->d_stage, x, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->d_stage + 3 * N, v, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));
+    launch_scatter_state(c->S, c->d_stage, c->d_stage + 3 * N, nullptr, nullptr, c->st);
+    CK(cudaStreamSynchronize(c->st));
+    CK(cudaMemcpyAsync(c->d_stage, a, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->d_stage + 3 * N, k, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));
+    launch_scatter_state(c->S, nullptr, nullptr, c->d_stage, c->d_stage + 3 * N, c->st);
+    CK(cudaMemcpyAsync(c->d_t, t, sizeof(long long) * N, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->d_lev, lev, sizeof(int) * N, cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->h_ctrl->t_now = t_max;
+    CK(cudaMemcpyAsync(&c->d_ctrl->t_now, &c->h_ctrl->t_now, sizeof(long long),
+                       cudaMemcpyHostToDevice, c->st));
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));
+    c->force_valid = false;
+    return NB_OK;
+}
+
+int nb_get_active(nb_ctx *c, int32_t *idx, int32_t cap, int32_t *na, int64_t *t_ticks)
+{
+    if (!c) return NB_EINVAL;
+    int rc = sync_ctrl(c);
+    if (rc) return rc;
+    const int n_act = c->h_ctrl->n_active;
+    if (na) *na = n_act;
+    if (t_ticks) *t_ticks = c->h_ctrl->t_now;
+    const int cnt = n_act < cap ? n_act : cap;
+    if (idx && cnt > 0) {
+        CK(cudaMemcpyAsync(idx, c->d_act, sizeof(int) * (size_t)cnt, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+    }
+    return NB_OK;
+}
+
+}  // extern "C"

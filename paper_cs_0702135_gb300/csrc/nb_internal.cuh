@@ -1,0 +1,168 @@
+// nb_internal.cuh -- device data layout, control block and launchers shared by
+// the CUDA translation units of the library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nb.h"
+
+namespace nbk {
+
+constexpr int kTickBits = 40;
+
+// Device-resident control block.  Every kernel of a block step reads its
+// block time and block size from here, so a whole step can be replayed from a
+// CUDA graph with no host round trip.
+struct Ctrl {
+    long long t_now;         // system time: block time of the last step (ticks)
+    long long t_next;        // block time chosen by the scheduler (ticks)
+    long long t_end;         // steps stop once the next block time would pass this
+    long long steps;         // block steps taken
+    long long interactions;  // sum over steps of n_active * (n - 1)
+    double ekin, epot;       // last energy reduction
+    int n_active;            // size of the current block; 0 = nothing to do
+    int err;                 // first NB_* error raised by a kernel (0 = none)
+    int err_where;           // which check raised it (for messages)
+    int pad;
+};
+
+// FP64 master state, structure of arrays: x[c * n + i] for component c.
+struct State {
+    double *x, *v, *a, *k;   // position, velocity, acceleration, jerk
+    const double *m;         // masses
+    long long *t;            // particle times in ticks
+    int *lev;                // block levels: dt_i = 2^-lev
+    int n;
+};
+
+// j-particle records written by the predictor.
+//  DS:   pos_hi = (x_hi, y_hi, z_hi, m), pos_lo = (x_lo, y_lo, z_lo, 0),
+//        vel = (vx, vy, vz, 0) with x = x_hi + x_lo to 2^-48 relative.
+//  FP64: pos = (x, y, z, m), vel = (vx, vy, vz, 0).
+struct JDS {
+    float4 *pos_hi, *pos_lo, *vel;
+};
+struct JF64 {
+    double4_32a *pos, *vel;
+};
+
+// Force results in the public layout: acc[a][3], jerk[a][3], pot[a].
+struct ForceOut {
+    double *acc, *jerk, *pot;
+};
+
+// ---------------------------------------------------------------------------
+// Work decomposition.  The same functions run on the host (to size buffers and
+// grids) and on the device (where n_active is only known there).
+
+constexpr int kIparNT = 128;   // threads per CTA, i-parallel kernels
+constexpr int kIparR = 2;      // i per thread, DS i-parallel kernel
+constexpr int kIparR64 = 1;    // i per thread, FP64 i-parallel kernel
+constexpr int kJparNT = 256;   // threads per CTA, j-parallel kernels
+constexpr int kJparIC = 4;     // i per pass, j-parallel kernels
+constexpr int kJparMaxActive = 16;  // automatic mode: j-parallel up to this block size
+constexpr int kComp = 7;       // acc xyz, jerk xyz, pot
+
+struct Plan {
+    int n_iblk;   // i-blocks (i-parallel) or i-chunks (j-parallel)
+    int S;        // j slices
+    int jslice;   // j per slice (multiple of the tile)
+    int items;    // n_iblk * S work items
+};
+
+__host__ __device__ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// i-parallel: CTAs own iblk consecutive active particles and one j slice.
+// Slices are added until there are about two work items per resident CTA,
+// keeping at least two tiles per slice and the partial buffer within
+// part_cap doubles.
+__host__ __device__ inline Plan plan_ipar(int na, int n, int iblk, int tile, int slots,
+                                          int split, long long part_cap)
+{
+    Plan p;
+    p.n_iblk = cdiv(na, iblk);
+    int S = split > 0 ? split : (p.n_iblk >= 2 * slots ? 1 : cdiv(2LL * slots, p.n_iblk));
+    int smax = cdiv(n, 2LL * tile);
+    if (S > smax) S = smax;
+    long long pmax = part_cap / ((long long)kComp * (na > 0 ? na : 1));
+    if (S > pmax) S = (int)pmax;
+    if (S < 1) S = 1;
+    p.jslice = cdiv(cdiv(n, S), tile) * tile;
+    p.S = cdiv(n, p.jslice);
+    p.items = p.n_iblk * p.S;
+    return p;
+}
+
+// j-parallel: CTAs own ic active particles and one j slice; each thread takes
+// every nt-th j of the slice, at least eight per thread.
+__host__ __device__ inline Plan plan_jpar(int na, int n, int nt, int ic, int slots,
+                                          long long part_cap)
+{
+    Plan p;
+    p.n_iblk = cdiv(na, ic);
+    int S = cdiv(2LL * slots, p.n_iblk);
+    int smax = cdiv(n, 8LL * nt);
+    if (S > smax) S = smax;
+    long long pmax = part_cap / ((long long)kComp * (na > 0 ? na : 1));
+    if (S > pmax) S = (int)pmax;
+    if (S < 1) S = 1;
+    p.jslice = cdiv(cdiv(n, S), nt) * nt;
+    p.S = cdiv(n, p.jslice);
+    p.items = p.n_iblk * p.S;
+    return p;
+}
+
+// Which kernel serves a block of na particles: jpar for na <= jpar_max.
+__host__ __device__ inline bool use_jpar(int na, int jpar_max) { return na <= jpar_max; }
+
+// Everything a force launch needs.
+struct ForceArgs {
+    int n;                    // j count
+    const int *act;           // active indices (device)
+    const int *na_dev;        // device block size, or nullptr to use na_host
+    int na_host;
+    int jpar_max;             // regime boundary (see use_jpar)
+    int split;                // forced slice count for i-parallel, 0 = auto
+    int slots_ipar, slots_jpar;
+    long long part_cap;       // capacity of part in doubles
+    double *part;             // slice partials: part[(s * 7 + c) * na + a]
+    ForceOut out;
+    double eps2;
+    int *err;                 // device error word
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (defined in the .cu files).
+
+// k_force.cu
+void launch_force_ds(const ForceArgs &fa, const JDS &j, bool softened, int grid_ipar, int grid_jpar,
+                     cudaStream_t st);
+void launch_force_f64(const ForceArgs &fa, const JF64 &j, bool softened, int grid_ipar,
+                      int grid_jpar, cudaStream_t st);
+int occupancy_force(int precision, bool jpar, int *blocks_per_sm);
+
+// k_step.cu
+void launch_predict(const State &s, long long t_val, const long long *t_ptr, const int *gate,
+                    int precision, JDS jds, JF64 jf, cudaStream_t st);
+void launch_correct(const State &s, const int *act, int na_host, const int *na_dev,
+                    long long t_val, const long long *t_ptr, const double *acc_new,
+                    const double *jerk_new, double eta, int level_min, int level_fixed,
+                    int *err, cudaStream_t st);
+void launch_initial_steps(const State &s, const double *acc, const double *jerk, double eta_init,
+                          int level_min, int level_fixed, int *err, cudaStream_t st);
+void launch_schedule(const State &s, Ctrl *ctrl, long long *blockmin, int *blockcnt, int *act,
+                     int nblocks, cudaStream_t st);
+int schedule_blocks(int n);
+void launch_energy(const State &s, const long long *t_ptr, const double *pot, double *part,
+                   Ctrl *ctrl, cudaStream_t st);
+int energy_blocks(int n);
+void launch_validate(const int *idx, int na, int n, unsigned int *bitmap, int *err,
+                     cudaStream_t st);
+void launch_gather_state(const State &s, double *x, double *v, double *a, double *k,
+                         cudaStream_t st);
+void launch_scatter_state(const State &s, const double *x, const double *v, const double *a,
+                          const double *k, cudaStream_t st);
+void launch_iota(int *p, int n, cudaStream_t st);
+
+}  // namespace nbk

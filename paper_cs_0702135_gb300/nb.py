@@ -1,0 +1,292 @@
+"""Python binding of the C ABI in ``include/nb.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does
+nothing but convert arguments: all work runs in ``libnb_gb300.so``.  The
+library must have been built (``__graft_entry__.build()`` or
+``python -m paper_cs_0702135_gb300.build``); loading fails loudly otherwise,
+and there is no fallback implementation.
+
+Device-pointer variants accept torch CUDA tensors; pass the tensor's stream as
+``stream`` in the options (``torch.cuda.current_stream().cuda_stream``) when
+mixing the library with torch work on the same data.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libnb_gb300.so")
+
+NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ESTEP, NB_ETIMEOUT, NB_ESTATE = 0, -1, -2, -3, -4, -5, -6
+NB_DS, NB_FP64 = 0, 1
+NB_FORCE_AUTO, NB_FORCE_IPAR, NB_FORCE_JPAR = 0, 1, 2
+NB_TICK_BITS = 40
+TICKS_PER_UNIT = 1 << NB_TICK_BITS
+
+_ERRNAMES = {NB_EINVAL: "NB_EINVAL", NB_ENOMEM: "NB_ENOMEM", NB_ECUDA: "NB_ECUDA",
+             NB_ESTEP: "NB_ESTEP", NB_ETIMEOUT: "NB_ETIMEOUT", NB_ESTATE: "NB_ESTATE"}
+
+
+class NbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_ERRNAMES.get(code, "error"), code, msg))
+        self.code = code
+
+
+class nb_opts(ctypes.Structure):
+    _fields_ = [("eta", ctypes.c_double), ("eta_init", ctypes.c_double),
+                ("level_min", ctypes.c_int), ("level_fixed", ctypes.c_int),
+                ("precision", ctypes.c_int), ("force_mode", ctypes.c_int),
+                ("split_j", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+_c_dp = ctypes.POINTER(ctypes.c_double)
+_c_ip = ctypes.POINTER(ctypes.c_int32)
+_c_lp = ctypes.POINTER(ctypes.c_int64)
+_vp = ctypes.c_void_p
+_lib = None
+
+# (name, restype, argtypes) of every entry point of include/nb.h
+SIGNATURES = [
+    ("nb_default_opts", None, [ctypes.POINTER(nb_opts)]),
+    ("nb_init", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int64, _vp, _vp, _vp, ctypes.c_double,
+                               ctypes.POINTER(nb_opts)]),
+    ("nb_predict", ctypes.c_int, [_vp, ctypes.c_double]),
+    ("nb_force", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, _vp]),
+    ("nb_force_dev", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, _vp]),
+    ("nb_correct", ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_double, _vp, _vp]),
+    ("nb_step", ctypes.c_int, [_vp, _c_dp, _c_ip]),
+    ("nb_run", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int64, _c_lp, _c_lp]),
+    ("nb_energy", ctypes.c_int, [_vp, _c_dp, _c_dp]),
+    ("nb_get_state", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("nb_set_state", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("nb_get_active", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _c_ip, _c_lp]),
+    ("nb_num_particles", ctypes.c_int64, [_vp]),
+    ("nb_last_error", ctypes.c_char_p, [_vp]),
+    ("nb_free", None, [_vp]),
+]
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("%s is missing: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _dptr(t):
+    """Device pointer of a torch tensor (or an int address, or None)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != shape:
+        raise ValueError("expected shape %s, got %s" % (shape, a.shape))
+    return a
+
+
+def _check(ctx, rc):
+    if rc != NB_OK:
+        raise NbError(rc, lib().nb_last_error(ctx).decode())
+
+
+def nb_default_opts(**overrides) -> nb_opts:
+    o = nb_opts()
+    lib().nb_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def nb_init(m, x, v, eps, opts=None):
+    """Returns a context handle (c_void_p)."""
+    m = _f64(m)
+    n = m.shape[0]
+    x = _f64(x, (n, 3))
+    v = _f64(v, (n, 3))
+    ctx = ctypes.c_void_p()
+    rc = lib().nb_init(ctypes.byref(ctx), n, _ptr(m), _ptr(x), _ptr(v), float(eps),
+                       None if opts is None else ctypes.byref(opts))
+    if rc != NB_OK:
+        raise NbError(rc, lib().nb_last_error(None).decode())
+    return ctx
+
+
+def nb_predict(ctx, t):
+    _check(ctx, lib().nb_predict(ctx, float(t)))
+
+
+def nb_force(ctx, active_idx):
+    """(acc[n,3], jerk[n,3], pot[n]) on host for the listed particles."""
+    idx = np.ascontiguousarray(active_idx, dtype=np.int32)
+    na = idx.shape[0]
+    acc = np.empty((na, 3))
+    jerk = np.empty((na, 3))
+    pot = np.empty(na)
+    _check(ctx, lib().nb_force(ctx, _ptr(idx), na, _ptr(acc), _ptr(jerk), _ptr(pot)))
+    return acc, jerk, pot
+
+
+def nb_force_into(ctx, active_idx, acc, jerk, pot):
+    """nb_force writing into caller-provided host arrays (any may be None)."""
+    idx = np.ascontiguousarray(active_idx, dtype=np.int32)
+    _check(ctx, lib().nb_force(ctx, _ptr(idx), idx.shape[0], _ptr(acc), _ptr(jerk), _ptr(pot)))
+
+
+def nb_force_dev(ctx, d_active_idx, n_active, d_acc=None, d_jerk=None, d_pot=None):
+    """Device-pointer variant: torch CUDA tensors (int32 indices, float64 outputs)."""
+    _check(ctx, lib().nb_force_dev(ctx, _dptr(d_active_idx), int(n_active), _dptr(d_acc),
+                                   _dptr(d_jerk), _dptr(d_pot)))
+
+
+def nb_correct(ctx, active_idx, t, acc=None, jerk=None):
+    idx = np.ascontiguousarray(active_idx, dtype=np.int32)
+    na = idx.shape[0]
+    a = None if acc is None else _f64(acc, (na, 3))
+    k = None if jerk is None else _f64(jerk, (na, 3))
+    _check(ctx, lib().nb_correct(ctx, _ptr(idx), na, float(t), _ptr(a), _ptr(k)))
+
+
+def nb_step(ctx, wait=True):
+    """One device-driven block step; returns (t, n_active) when wait, else None."""
+    if not wait:
+        _check(ctx, lib().nb_step(ctx, None, None))
+        return None
+    t = ctypes.c_double()
+    na = ctypes.c_int32()
+    _check(ctx, lib().nb_step(ctx, ctypes.byref(t), ctypes.byref(na)))
+    return t.value, na.value
+
+
+def nb_run(ctx, t_end, max_steps=1 << 62):
+    """Block steps to t_end; returns (steps, interactions)."""
+    s = ctypes.c_int64()
+    it = ctypes.c_int64()
+    _check(ctx, lib().nb_run(ctx, float(t_end), int(max_steps), ctypes.byref(s), ctypes.byref(it)))
+    return s.value, it.value
+
+
+def nb_energy(ctx):
+    """(kinetic, potential) energy."""
+    ek = ctypes.c_double()
+    ep = ctypes.c_double()
+    _check(ctx, lib().nb_energy(ctx, ctypes.byref(ek), ctypes.byref(ep)))
+    return ek.value, ep.value
+
+
+def nb_get_state(ctx):
+    """dict with x, v, a, k [n,3], t (int64 ticks) and level (int32)."""
+    n = int(lib().nb_num_particles(ctx))
+    st = {"x": np.empty((n, 3)), "v": np.empty((n, 3)), "a": np.empty((n, 3)),
+          "k": np.empty((n, 3)), "t": np.empty(n, dtype=np.int64), "level": np.empty(n, dtype=np.int32)}
+    _check(ctx, lib().nb_get_state(ctx, _ptr(st["x"]), _ptr(st["v"]), _ptr(st["a"]), _ptr(st["k"]),
+                                   _ptr(st["t"]), _ptr(st["level"])))
+    return st
+
+
+def nb_set_state(ctx, x, v, a, k, t, level):
+    n = int(lib().nb_num_particles(ctx))
+    arrs = [_f64(x, (n, 3)), _f64(v, (n, 3)), _f64(a, (n, 3)), _f64(k, (n, 3)),
+            np.ascontiguousarray(t, dtype=np.int64), np.ascontiguousarray(level, dtype=np.int32)]
+    _check(ctx, lib().nb_set_state(ctx, *[_ptr(q) for q in arrs]))
+
+
+def nb_get_active(ctx):
+    """(ascending indices of the last block, block time in ticks)."""
+    n = int(lib().nb_num_particles(ctx))
+    na = ctypes.c_int32()
+    tt = ctypes.c_int64()
+    _check(ctx, lib().nb_get_active(ctx, None, 0, ctypes.byref(na), ctypes.byref(tt)))
+    idx = np.empty(max(na.value, 1), dtype=np.int32)
+    _check(ctx, lib().nb_get_active(ctx, _ptr(idx), na.value, ctypes.byref(na), ctypes.byref(tt)))
+    return idx[:na.value].copy(), tt.value
+
+
+def nb_num_particles(ctx) -> int:
+    return int(lib().nb_num_particles(ctx))
+
+
+def nb_last_error(ctx) -> str:
+    return lib().nb_last_error(ctx).decode()
+
+
+def nb_free(ctx):
+    if ctx is not None and ctx.value:
+        lib().nb_free(ctx)
+        ctx.value = None
+
+
+class Context:
+    """Owns one nb_ctx; each method calls the entry point of the same name."""
+
+    def __init__(self, m, x, v, eps, **opts):
+        o = nb_default_opts(**opts) if opts else None
+        self.ctx = nb_init(m, x, v, eps, o)
+        self.n = nb_num_particles(self.ctx)
+
+    def nb_predict(self, t):
+        return nb_predict(self.ctx, t)
+
+    def nb_force(self, active_idx):
+        return nb_force(self.ctx, active_idx)
+
+    def nb_force_dev(self, d_active_idx, n_active, d_acc=None, d_jerk=None, d_pot=None):
+        return nb_force_dev(self.ctx, d_active_idx, n_active, d_acc, d_jerk, d_pot)
+
+    def nb_correct(self, active_idx, t, acc=None, jerk=None):
+        return nb_correct(self.ctx, active_idx, t, acc, jerk)
+
+    def nb_step(self, wait=True):
+        return nb_step(self.ctx, wait)
+
+    def nb_run(self, t_end, max_steps=1 << 62):
+        return nb_run(self.ctx, t_end, max_steps)
+
+    def nb_energy(self):
+        return nb_energy(self.ctx)
+
+    def nb_get_state(self):
+        return nb_get_state(self.ctx)
+
+    def nb_set_state(self, x, v, a, k, t, level):
+        return nb_set_state(self.ctx, x, v, a, k, t, level)
+
+    def nb_get_active(self):
+        return nb_get_active(self.ctx)
+
+    def nb_free(self):
+        nb_free(self.ctx)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.nb_free()
+
+    def __del__(self):
+        try:
+            self.nb_free()
+        except Exception:
+            pass
