@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark of the direct N-body hot path on GB300.
+
+Workload: Plummer sphere N = 2^20 (seed 3), eps = 1/1024, FP32 pair
+arithmetic on double-single positions.  One step = one full-active Hermite
+block step on the device (schedule, predict all N, force on all N from all N,
+correct + new steps; every particle shares the level 2^-10), i.e. the N^2
+sweep with every O(N) stage around it.  Metric: acc+jerk interactions per
+second, N (N - 1) per step, also as Gflop/s at 60 flop per interaction and as
+a fraction of the FP32 peak.  Energy is measured (full sweeps) before and
+after the run.
+
+Beside it, in the same JSON line: the force kernel's roofline (CUDA events
+around each force launch on the library's stream), isolated sweeps with
+n_active in {1, 256, 4096, 65536, N}, the all-FP64 kernel on the same sweep,
+an end-to-end figure through the host-buffer API, the CPU oracle on a bounded
+sample of the same workload, and SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N --steps K --warmup W]       # this library
+  python bench.py --impl reference [...]                # the CPU oracle
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "acc+jerk interactions/s & % FP32 peak, FP32-DS vs FP64 GPU, at |ΔE/E|≤1e-6"
+UNIT = "interactions/s"
+FLOP_PER_INTERACTION = 60          # eta_fe of the paper (Section 5)
+N_DEFAULT = 1 << 20
+EPS = 1.0 / 1024
+SEED = 3
+LEVEL = 10                         # shared step 2^-10
+SWEEP_LADDER = [1, 256, 4096, 65536]
+FP64_SAMPLE = 4096
+L2_FLUSH_BYTES = 256 << 20
+FP32_LANES_PER_SM = 128
+MAX_SM_MHZ_FALLBACK = 2070.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    p.add_argument("--n", type=int, default=N_DEFAULT)
+    p.add_argument("--no-extras", action="store_true", help="skip ladder, FP64 arm, e2e, CPU baseline")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu_index = gpu_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [q.strip() for q in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "power_w_max": float(max(power)), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def nvsmi_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [q.strip() for q in vis.split(",") if q.strip()]
+    if ids and all(q.isdigit() for q in ids) and local_rank < len(ids):
+        return int(ids[local_rank])
+    return local_rank
+
+
+# ---------------------------------------------------------------------------
+
+def fp32_peak_tflops(sms, mhz):
+    """FP32 FMA peak: 128 lanes per SM, 2 flop per FMA."""
+    return 2.0 * FP32_LANES_PER_SM * sms * mhz * 1e6 / 1e12
+
+
+def force_traffic_per_launch(n):
+    """DRAM bytes per full-N force launch from the committed ncu summary, or
+    None when the kernel source changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "k_force_ipar_ds.md")
+    src = os.path.join(ROOT, "paper_cs_0702135_gb300", "csrc", "k_force.cu")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    mh = re.search(r"k_force\.cu sha256:\s*([0-9a-f]{64})", text)
+    mb = re.search(r"dram bytes per launch at N=(\d+):\s*([0-9.eE+]+)", text)
+    if not mh or not mb:
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != mh.group(1):
+        return None
+    # With the j records resident in L2 the kernel's DRAM traffic is O(N)
+    # (records, block outputs), so a smaller capture scales linearly.
+    n_cap, b = int(mb.group(1)), float(mb.group(2))
+    return b * n / n_cap
+
+
+def cpu_oracle_rate(m, x, v, eps, budget_s=10.0, seed=SEED):
+    """Oracle direct-sum force (OpenMP over i) on a growing sample of active i
+    against all N j until one timing takes at least budget_s seconds."""
+    import oracle
+    from synth import sample_active
+    threads = os.cpu_count() or 1
+    oracle.lib()
+    n = m.shape[0]
+    na = 64
+    while True:
+        idx = sample_active(n, na, seed + na)
+        t0 = time.perf_counter()
+        oracle.force(m, x, v, eps, idx, nthreads=threads)
+        dt = time.perf_counter() - t0
+        if dt >= budget_s or na >= n:
+            break
+        na = min(n, max(na * 2, int(na * budget_s / max(dt, 1e-3) * 1.1)))
+    return na * (n - 1) / dt, threads, na, dt
+
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores, on this workload's metric."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from synth import plummer, sample_active
+    n = args.n
+    m, x, v = plummer(n, SEED)
+    threads = os.cpu_count() or 1
+    oracle.lib()
+    na = max(1, min(n, 256 * max(1, threads // 16)))
+    idx = [sample_active(n, na, SEED + s) for s in range(args.warmup + args.steps)]
+    for s in range(args.warmup):
+        oracle.force(m, x, v, EPS, idx[s], nthreads=threads)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle.force(m, x, v, EPS, idx[args.warmup + s], nthreads=threads)
+    el = time.perf_counter() - t0
+    rate = args.steps * na * (n - 1) / el
+    sample = ("oracle direct-sum force, %d of the %d active i per step against all N j "
+              "(the full-active step's N^2 sweep, sampled); O(N) predict/correct not timed" % (na, n))
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "plummer_N%d_eps1/1024_full_active_block_step" % n, "N": n,
+                       "eps": EPS, "seed": SEED},
+            "cpu_baseline": {"kind": "oracle", "cores": threads, "sample": sample, "value": rate,
+                             "unit": UNIT},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_mine(args):
+    import torch
+    import paper_cs_0702135_gb300 as nb
+    from synth import plummer, sample_active
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    # A stream of our own: the library runs on it, and the events and the L2
+    # flush below are recorded on it too.
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    n = args.n
+    inter_per_step = n * (n - 1)
+
+    m, x, v = plummer(n, SEED + rank)      # replicas: one independent sphere per rank
+    ctx = nb.Context(m, x, v, EPS, level_fixed=LEVEL, stream=stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    e0 = sum(ctx.nb_energy())
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        ctx.nb_step(wait=False)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(nvsmi_index(local))
+    ctx.nb_get_stats(reset=True)
+    ctx.nb_set_profiling(True)
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()                         # L2 flush between steps
+        ctx.nb_step(wait=False)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    stats = ctx.nb_get_stats(reset=True)
+    ctx.nb_set_profiling(False)
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        elapsed = float(t.item())
+    e1 = sum(ctx.nb_energy())
+    value = world * args.steps * inter_per_step / elapsed
+
+    force_s = stats["force_ms"] / 1e3 / max(1, stats["force_launches"])
+    peak = fp32_peak_tflops(sms, MAX_SM_MHZ_FALLBACK)
+    achieved = FLOP_PER_INTERACTION * inter_per_step / force_s / 1e12
+    traffic = force_traffic_per_launch(n)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_force_ipar_ds (full-N launch inside the step)",
+                "peak_note": "FP32 FMA peak 2 x 128 lanes x %d SMs x 2070 MHz (max SM clock)" % sms}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_measured_clock"] = achieved / fp32_peak_tflops(sms, clocks["sm_mhz"])
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = run_extras(args, nb, ctx, m, x, v, stream, dev, torch, sample_active)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "plummer_N%d_eps1/1024_full_active_block_step" % n, "N": n,
+                   "eps": EPS, "seed": SEED, "n_active": n, "shared_level": LEVEL,
+                   "precision": "FP32 pair terms on double-single positions, FP64 predictor/corrector",
+                   "l2": "inputs larger than L2 (~270 MB touched per step) and a 256 MiB memset "
+                         "between steps inside the timed region",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "gflops": value * FLOP_PER_INTERACTION / 1e9,
+        "pct_fp32_peak": 100.0 * value * FLOP_PER_INTERACTION / 1e12 / peak,
+        "energy": {"rel_err": abs(e1 - e0) / abs(e0), "steps": args.warmup + args.steps,
+                   "dt": 2.0 ** -LEVEL},
+        "roofline": roofline,
+        "gpu_launches": stats["kernel_launches"],
+        "clocks": clocks,
+        "device": {"name": props.name, "sms": sms},
+    }
+    line.update(extras)
+    ctx.nb_free()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_extras(args, nb, ctx, m, x, v, stream, dev, torch, sample_active):
+    n = args.n
+    out = {}
+    # Isolated sweeps: n_active i (uniform without replacement) against all N j.
+    ladder = {}
+    for na in SWEEP_LADDER + [n]:
+        if na > n:
+            continue
+        idx = torch.from_numpy(sample_active(n, na, SEED + na)).to(dev)
+        acc = torch.empty((na, 3), dtype=torch.float64, device=dev)
+        jerk = torch.empty_like(acc)
+        pot = torch.empty(na, dtype=torch.float64, device=dev)
+        reps = 3 if na == n else 20
+        for _ in range(3):
+            ctx.nb_force_dev(idx, na, acc, jerk, pot)
+        ctx.nb_get_stats(reset=True)
+        ctx.nb_set_profiling(True)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            ctx.nb_force_dev(idx, na, acc, jerk, pot)
+        torch.cuda.synchronize(dev)
+        call_s = (time.perf_counter() - t0) / reps
+        st = ctx.nb_get_stats(reset=True)
+        ctx.nb_set_profiling(False)
+        fs = st["force_ms"] / 1e3 / max(1, st["force_launches"])
+        ladder[str(na)] = {"force_us": fs * 1e6, "call_us": call_s * 1e6,
+                           "interactions_per_s": na * (n - 1) / fs,
+                           "gflops": FLOP_PER_INTERACTION * na * (n - 1) / fs / 1e9}
+    out["sweeps"] = ladder
+
+    # The all-FP64 kernel on the same sweep (FP64_SAMPLE active i against all N).
+    na = min(FP64_SAMPLE, n)
+    c64 = nb.Context(m, x, v, EPS, precision=nb.NB_FP64, flags=nb.NB_INIT_NO_FORCE,
+                     stream=stream.cuda_stream)
+    idx = torch.from_numpy(sample_active(n, na, SEED + na)).to(dev)
+    acc = torch.empty((na, 3), dtype=torch.float64, device=dev)
+    c64.nb_force_dev(idx, na, acc, None, None)
+    c64.nb_get_stats(reset=True)
+    c64.nb_set_profiling(True)
+    for _ in range(3):
+        c64.nb_force_dev(idx, na, acc, None, None)
+    st = c64.nb_get_stats(reset=True)
+    c64.nb_free()
+    fs64 = st["force_ms"] / 1e3 / max(1, st["force_launches"])
+    r64 = na * (n - 1) / fs64
+    rds = ladder[str(na)]["interactions_per_s"] if str(na) in ladder else None
+    out["fp64_gpu"] = {"value": r64, "unit": UNIT, "sample": "%d active i against all %d j" % (na, n),
+                       "ds_over_fp64": (rds / r64) if rds else None}
+
+    # End to end through the host-buffer API: per step nb_predict, nb_force with
+    # pinned host index/output arrays, nb_correct; copies inside the timed region.
+    st0 = ctx.nb_get_state()
+    t_cur = int(st0["t"].max())
+    dt = 1 << (40 - LEVEL)
+    idx_h = torch.arange(n, dtype=torch.int32).pin_memory().numpy()
+    acc_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+    jerk_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+    pot_h = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    k_e2e = max(2, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for s in range(k_e2e):
+        t_cur += dt
+        ctx.nb_predict(t_cur / nb.TICKS_PER_UNIT)
+        nb.nb_force_into(ctx.ctx, idx_h, acc_h, jerk_h, pot_h)
+        ctx.nb_correct(idx_h, t_cur / nb.TICKS_PER_UNIT)
+    torch.cuda.synchronize(dev)
+    el = time.perf_counter() - t0
+    out["e2e"] = {"value": k_e2e * n * (n - 1) / el, "unit": UNIT,
+                  "h2d_bytes_per_step": 2 * 4 * n, "d2h_bytes_per_step": (3 + 3 + 1) * 8 * n,
+                  "steps": k_e2e, "api": "nb_predict + nb_force (host arrays) + nb_correct"}
+
+    # The CPU oracle on a bounded sample of the same workload.
+    if int(os.environ.get("WORLD_SIZE", "1")) == 1:
+        rate, threads, na_s, secs = cpu_oracle_rate(m, x, v, EPS)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": "oracle direct-sum force (FP64, OpenMP) on %d of the %d "
+                                         "active i against all j, %.1f s" % (na_s, n, secs)}
+    return out
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mine(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -47,6 +47,8 @@ extern "C" {
 
 #define NB_TICK_BITS 40
 
+#define NB_INIT_NO_FORCE 1  /* nb_opts.flags: skip the t = 0 force sweep and initial steps */
+
 typedef struct nb_ctx nb_ctx;
 
 typedef struct nb_opts {
@@ -57,8 +59,8 @@ typedef struct nb_opts {
     int precision;     /* NB_DS (default) or NB_FP64 */
     int force_mode;    /* NB_FORCE_AUTO (default), NB_FORCE_IPAR or NB_FORCE_JPAR */
     int split_j;       /* i-parallel kernel: number of j slices, 0 = automatic */
-    int reserved;      /* must be 0 */
-    void *stream;      /* cudaStream_t to run on; NULL = the legacy default stream */
+    int flags;         /* NB_INIT_NO_FORCE or 0 (default): see nb_init */
+    void *stream;      /* cudaStream_t to run on; NULL = a non-blocking stream the context creates */
 } nb_opts;
 
 /* Fills *opts with the defaults listed above. */
@@ -69,6 +71,9 @@ void nb_default_opts(nb_opts *opts);
  * masses m[n] (> 0 or == 0), positions x[n][3], velocities v[n][3] (host
  * arrays, FP64), Plummer softening eps >= 0.  Computes the full force at t = 0
  * and the initial steps (Section 2 step loop, start-up).  opts may be NULL.
+ * With opts->flags & NB_INIT_NO_FORCE the start-up sweep is skipped:
+ * acceleration and jerk start at zero and every level at level_min, for
+ * callers that only use nb_force or that load a state with nb_set_state.
  * Errors: NB_EINVAL (n < 1 or n > 2^31 - 1, eps < 0, non-finite input, bad
  * opts), NB_ENOMEM, NB_ECUDA, NB_ESTEP.  On error *ctx is NULL.
  */
@@ -176,6 +181,29 @@ int nb_set_state(nb_ctx *ctx, const double *x, const double *v, const double *a,
  * *t_ticks (each pointer may be NULL).  Errors: NB_ECUDA.
  */
 int nb_get_active(nb_ctx *ctx, int32_t *idx, int32_t cap, int32_t *n_active, int64_t *t_ticks);
+
+/* Counters of a context (measurement aid; the paper has no counterpart). */
+typedef struct nb_stats {
+    int64_t steps;            /* device-driven block steps taken */
+    int64_t interactions;     /* sum of n_active (n - 1) over those steps */
+    int64_t kernel_launches;  /* kernels this library enqueued (graph replays count each node) */
+    int64_t force_launches;   /* force evaluations timed while profiling was on */
+    double force_ms;          /* their summed GPU time from CUDA events on the context's stream */
+} nb_stats;
+
+/*
+ * Turns per-force-evaluation timing on (enable != 0) or off.  While on, every
+ * force evaluation enqueued by nb_step, nb_force and nb_force_dev is bracketed
+ * by CUDA events on the context's stream.  Errors: NB_ECUDA.
+ */
+int nb_set_profiling(nb_ctx *ctx, int enable);
+
+/*
+ * Reads the counters (waiting for the timed force evaluations to finish) and,
+ * with reset != 0, zeroes the launch and timing counters afterwards.
+ * Errors: NB_ECUDA.
+ */
+int nb_get_stats(nb_ctx *ctx, nb_stats *stats, int reset);
 
 /* Number of particles, or -1 for a NULL context. */
 int64_t nb_num_particles(const nb_ctx *ctx);

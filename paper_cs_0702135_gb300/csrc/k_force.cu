@@ -9,7 +9,7 @@
 //
 // DS kernels: positions are double-single (hi + lo FP32), the difference
 // x_j - x_i is formed as (x_j,hi - x_i,hi) + (x_j,lo - x_i,lo), the pair terms
-// run in FP32 with rsqrtf on the SFU, and each thread's per-tile FP32 partials
+// run in FP32 with rsqrt.approx on the SFU, and each thread's per-tile FP32 partials
 // are folded into hi + lo FP32 accumulators with TwoSum, so that the error of
 // the sum over all N does not grow with N.  FP64 kernels do everything in FP64.
 //
@@ -73,6 +73,17 @@ __device__ __forceinline__ void store_result(const ForceOut &o, int a, const dou
     if (o.pot) o.pot[a] = r[6];
 }
 
+// 1/sqrt(x) on the SFU: the PTX approximate reciprocal square root with
+// flush-to-zero (one MUFU instruction; relative error about 2^-23).  r^2 >=
+// eps^2 is never subnormal, so the denormal handling of rsqrtf() would only
+// cost issue slots here.
+__device__ __forceinline__ float rsqrt_sfu(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // One FP32 pair interaction on double-single positions.
 template <bool SOFT, bool GUARD>
 __device__ __forceinline__ void pair_ds(const float4 &p, const float4 &l, const float4 &w,
@@ -88,7 +99,7 @@ __device__ __forceinline__ void pair_ds(const float4 &p, const float4 &l, const 
     const float uz = w.z - vi[2];
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
     const float rv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
-    float rinv = rsqrtf(r2);
+    float rinv = rsqrt_sfu(r2);
     if (!SOFT) rinv = (r2 > 0.0f) ? rinv : 0.0f;
     if (GUARD) rinv = (j == i) ? 0.0f : rinv;
     const float rinv2 = rinv * rinv;
@@ -209,7 +220,7 @@ __global__ void __launch_bounds__(NT) k_force_ipar_ds(ForceArgs fa, JDS J)
                                             jt + jj, ii[r]);
                 }
             } else {
-#pragma unroll 8
+#pragma unroll (kIparUnroll)
                 for (int jj = 0; jj < NT; ++jj) {
                     const float4 p = s_p[jj], l = s_l[jj], v = s_v[jj];
 #pragma unroll
@@ -286,6 +297,7 @@ __global__ void __launch_bounds__(NT) k_force_jpar_ds(ForceArgs fa, JDS J)
             vk[q][0] = vk[q][1] = vk[q][2] = 0.0f;
             vp[q] = 0.0f;
         }
+#pragma unroll 4
         for (int j = j0 + tid; j < j1; j += NT) {
             const float4 p = __ldg(&J.pos_hi[j]), l = __ldg(&J.pos_lo[j]), v = __ldg(&J.vel[j]);
 #pragma unroll

@@ -50,6 +50,15 @@ struct nb_ctx {
     long long force_t = 0;
     long long t_end_dev = -1;       // value of ctrl->t_end on the device
     cudaGraphExec_t step_exec = nullptr;
+    long long step_nodes = 0;       // kernels in one captured step
+    bool capturing = false;
+
+    // measurement counters (nb_get_stats)
+    long long launches = 0;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_free, ev_pending;  // pending: start, stop, start, stop, ...
+    long long force_launches = 0;
+    double force_ms = 0.0;
     std::string err;
 };
 
@@ -178,10 +187,34 @@ void enqueue_force(nb_ctx *c, const int *act, int na_host, const int *na_dev, Fo
             gi = p.items < c->slots_ipar ? p.items : c->slots_ipar;
         }
     }
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    const bool timed = c->profiling && !c->capturing;
+    if (timed) {
+        for (int q = 0; q < 2; ++q) {
+            if (!c->ev_free.empty()) {
+                ev[q] = c->ev_free.back();
+                c->ev_free.pop_back();
+            } else if (cudaEventCreate(&ev[q]) != cudaSuccess) {
+                ev[q] = nullptr;
+            }
+        }
+        if (ev[0] && ev[1]) cudaEventRecord(ev[0], c->st);
+    }
     if (f64)
         launch_force_f64(fa, c->jf, c->eps > 0.0, gi, gj, c->st);
     else
         launch_force_ds(fa, c->jds, c->eps > 0.0, gi, gj, c->st);
+    c->launches += (gi > 0) + (gj > 0) + 1;
+    if (timed) {
+        if (ev[0] && ev[1]) {
+            cudaEventRecord(ev[1], c->st);
+            c->ev_pending.push_back(ev[0]);
+            c->ev_pending.push_back(ev[1]);
+        } else {
+            for (cudaEvent_t e : ev)
+                if (e) c->ev_free.push_back(e);
+        }
+    }
 }
 
 // The device-driven block step: schedule, predict all, force, correct.
@@ -194,6 +227,7 @@ void enqueue_step(nb_ctx *c)
     launch_correct(c->S, c->d_act, 0, &c->d_ctrl->n_active, 0, &c->d_ctrl->t_next, c->d_res,
                    c->d_res + 3LL * c->n, c->o.eta, c->o.level_min, c->o.level_fixed,
                    &c->d_ctrl->err, c->st);
+    c->launches += 3 + 1 + 1;  // scheduler, predictor, corrector (force counted above)
 }
 
 int set_t_end(nb_ctx *c, long long t_end)
@@ -232,6 +266,8 @@ void release(nb_ctx *c)
                     c->d_blockcnt, c->d_epart, c->d_stage};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_pending) cudaEventDestroy(e);
     if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
 }
@@ -264,6 +300,7 @@ void nb_default_opts(nb_opts *o)
     o->precision = NB_DS;
     o->force_mode = NB_FORCE_AUTO;
     o->split_j = 0;
+    o->flags = 0;
     o->stream = nullptr;
 }
 
@@ -302,7 +339,8 @@ static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, con
         return fail(c, NB_EINVAL, "precision must be NB_DS or NB_FP64");
     if (o.force_mode < NB_FORCE_AUTO || o.force_mode > NB_FORCE_JPAR)
         return fail(c, NB_EINVAL, "bad force_mode");
-    if (o.split_j < 0 || o.reserved != 0) return fail(c, NB_EINVAL, "bad split_j or reserved");
+    if (o.split_j < 0 || (o.flags & ~NB_INIT_NO_FORCE) != 0)
+        return fail(c, NB_EINVAL, "bad split_j or flags");
     if (!finite_all(m, n) || !finite_all(x, 3 * n) || !finite_all(v, 3 * n))
         return fail(c, NB_EINVAL, "non-finite input");
     for (int64_t i = 0; i < n; ++i)
@@ -330,9 +368,11 @@ static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, con
                   : o.force_mode == NB_FORCE_JPAR ? INT_MAX
                                                   : kJparMaxActive;
     const long long iblk = kIparNT * (f64 ? kIparR64 : kIparR);
-    long long cap_i = 4LL * c->slots_ipar * iblk;
-    long long cap_j = 8LL * c->slots_jpar * kJparIC;
-    c->part_cap = (long long)kComp * (cap_i > cap_j ? cap_i : cap_j);
+    // Partials: up to 16 slots' worth of i-blocks, and four slices of all n.
+    long long cap = 16LL * c->slots_ipar * iblk;
+    if (cap < 4LL * n) cap = 4LL * n;
+    const long long cap_j = 8LL * c->slots_jpar * kJparIC;
+    c->part_cap = (long long)kComp * (cap > cap_j ? cap : cap_j);
     c->nsched = schedule_blocks(c->n);
 
     int rc;
@@ -383,9 +423,13 @@ static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, con
     launch_scatter_state(c->S, c->d_stage, c->d_stage + 3 * N, nullptr, nullptr, c->st);
     launch_iota(c->d_all, c->n, c->st);
     launch_predict(c->S, 0, nullptr, nullptr, o.precision, c->jds, c->jf, c->st);
-    enqueue_full_sweep(c);
+    if (o.flags & NB_INIT_NO_FORCE)
+        CK(cudaMemsetAsync(c->d_res, 0, sizeof(double) * 6 * N, c->st));  // a = k = 0
+    else
+        enqueue_full_sweep(c);
     launch_initial_steps(c->S, c->d_res, c->d_res + 3 * N, o.eta_init, o.level_min, o.level_fixed,
                          &c->d_ctrl->err, c->st);
+    c->launches += 4;
     CK(cudaGetLastError());
     c->t_pred = 0;
     c->force_valid = false;
@@ -423,6 +467,7 @@ int nb_predict(nb_ctx *c, double t)
     if (!time_to_ticks(t, &ticks)) return fail(c, NB_EINVAL, "t=%.17g is not on the 2^-40 grid", t);
     launch_predict(c->S, ticks, nullptr, nullptr, c->o.precision, c->jds, c->jf, c->st);
     CK(cudaGetLastError());
+    c->launches += 1;
     c->t_pred = ticks;
     c->force_valid = false;
     return NB_OK;
@@ -455,6 +500,7 @@ int nb_force_dev(nb_ctx *c, const int32_t *d_idx, int32_t na, double *d_acc, dou
     if (na > 0) {
         CK(cudaMemsetAsync(c->d_bitmap, 0, sizeof(unsigned) * (size_t)((c->n + 31) / 32), c->st));
         launch_validate(d_idx, na, c->n, c->d_bitmap, &c->d_ctrl->err, c->st);
+        c->launches += 1;
         int rc = sync_ctrl(c);
         if (rc) return rc;
         CK(cudaMemcpyAsync(c->d_idx, d_idx, sizeof(int) * (size_t)na, cudaMemcpyDeviceToDevice,
@@ -498,6 +544,7 @@ int nb_correct(nb_ctx *c, const int32_t *idx, int32_t na, double t, const double
     launch_correct(c->S, c->d_idx, na, nullptr, ticks, nullptr, an, kn, c->o.eta, c->o.level_min,
                    c->o.level_fixed, &c->d_ctrl->err, c->st);
     CK(cudaGetLastError());
+    c->launches += 1;
     c->force_valid = false;
     if ((rc = sync_ctrl(c))) return rc;
     if (ticks > c->h_ctrl->t_now) {
@@ -539,7 +586,12 @@ int nb_run(nb_ctx *c, double t_end, int64_t max_steps, int64_t *steps_out, int64
     if (!c->step_exec) {
         cudaGraph_t g;
         CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+        const long long l0 = c->launches;
+        c->capturing = true;
         enqueue_step(c);
+        c->capturing = false;
+        c->step_nodes = c->launches - l0;
+        c->launches = l0;
         cudaError_t e = cudaStreamEndCapture(c->st, &g);
         if (e != cudaSuccess) return fail(c, NB_ECUDA, "graph capture: %s", cudaGetErrorString(e));
         e = cudaGraphInstantiate(&c->step_exec, g, 0);
@@ -554,7 +606,10 @@ int nb_run(nb_ctx *c, double t_end, int64_t max_steps, int64_t *steps_out, int64
     const int batch = 32;
     while (done < max_steps) {
         const long long k = (max_steps - done) < batch ? (max_steps - done) : batch;
-        for (long long s = 0; s < k; ++s) CK(cudaGraphLaunch(c->step_exec, c->st));
+        for (long long s = 0; s < k; ++s) {
+            CK(cudaGraphLaunch(c->step_exec, c->st));
+            c->launches += c->step_nodes;
+        }
         if ((rc = sync_ctrl(c))) return rc;
         done = c->h_ctrl->steps - steps0;
         if (c->h_ctrl->n_active == 0) break;
@@ -571,6 +626,7 @@ int nb_energy(nb_ctx *c, double *ekin, double *epot)
     enqueue_full_sweep(c);
     launch_energy(c->S, &c->d_ctrl->t_now, c->d_res + 6LL * c->n, c->d_epart, c->d_ctrl, c->st);
     CK(cudaGetLastError());
+    c->launches += 1 + 2;
     c->force_valid = false;
     const int rc = sync_ctrl(c);
     if (rc) return rc;
@@ -653,6 +709,41 @@ int nb_get_active(nb_ctx *c, int32_t *idx, int32_t cap, int32_t *na, int64_t *t_
     if (idx && cnt > 0) {
         CK(cudaMemcpyAsync(idx, c->d_act, sizeof(int) * (size_t)cnt, cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
+    }
+    return NB_OK;
+}
+
+int nb_set_profiling(nb_ctx *c, int enable)
+{
+    if (!c) return NB_EINVAL;
+    c->profiling = enable != 0;
+    return NB_OK;
+}
+
+int nb_get_stats(nb_ctx *c, nb_stats *out, int reset)
+{
+    if (!c) return NB_EINVAL;
+    int rc = sync_ctrl(c);
+    if (rc) return rc;
+    for (size_t q = 0; q + 1 < c->ev_pending.size(); q += 2) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, c->ev_pending[q], c->ev_pending[q + 1]));
+        c->force_ms += ms;
+        c->force_launches += 1;
+    }
+    for (cudaEvent_t e : c->ev_pending) c->ev_free.push_back(e);
+    c->ev_pending.clear();
+    if (out) {
+        out->steps = c->h_ctrl->steps;
+        out->interactions = c->h_ctrl->interactions;
+        out->kernel_launches = c->launches;
+        out->force_launches = c->force_launches;
+        out->force_ms = c->force_ms;
+    }
+    if (reset) {
+        c->launches = 0;
+        c->force_launches = 0;
+        c->force_ms = 0.0;
     }
     return NB_OK;
 }

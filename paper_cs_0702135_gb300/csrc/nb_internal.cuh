@@ -56,8 +56,19 @@ struct ForceOut {
 // Work decomposition.  The same functions run on the host (to size buffers and
 // grids) and on the device (where n_active is only known there).
 
-constexpr int kIparNT = 128;   // threads per CTA, i-parallel kernels
-constexpr int kIparR = 2;      // i per thread, DS i-parallel kernel
+#ifndef NB_IPAR_NT
+#define NB_IPAR_NT 64
+#endif
+#ifndef NB_IPAR_R
+#define NB_IPAR_R 4
+#endif
+#ifndef NB_IPAR_UNROLL
+#define NB_IPAR_UNROLL 8
+#endif
+
+constexpr int kIparNT = NB_IPAR_NT;  // threads per CTA (= j per tile), i-parallel kernels
+constexpr int kIparR = NB_IPAR_R;    // i per thread, DS i-parallel kernel
+constexpr int kIparUnroll = NB_IPAR_UNROLL;  // j unrolling of the DS inner loop
 constexpr int kIparR64 = 1;    // i per thread, FP64 i-parallel kernel
 constexpr int kJparNT = 256;   // threads per CTA, j-parallel kernels
 constexpr int kJparIC = 4;     // i per pass, j-parallel kernels
@@ -77,17 +88,45 @@ __host__ __device__ inline int cdiv(long long a, long long b) { return (int)((a 
 // Slices are added until there are about two work items per resident CTA,
 // keeping at least two tiles per slice and the partial buffer within
 // part_cap doubles.
+// Fraction of the last wave that does work when items run on slots resident
+// CTAs, as a measure of the tail: waves / ceil(waves).
+__host__ __device__ inline double wave_fill(long long items, int slots)
+{
+    const long long w = (items + slots - 1) / slots;
+    return (double)items / ((double)w * slots);
+}
+
+// i-parallel: CTAs own iblk consecutive active particles and one j slice.
+// With fewer than two i-blocks per resident CTA, slices are added until there
+// are two; then (in both cases) the slice count is raised, within a factor of
+// four, until the last wave of work items is at least 95% full.  Slices keep
+// at least two tiles each and the partials fit in part_cap doubles.
 __host__ __device__ inline Plan plan_ipar(int na, int n, int iblk, int tile, int slots,
                                           int split, long long part_cap)
 {
     Plan p;
     p.n_iblk = cdiv(na, iblk);
-    int S = split > 0 ? split : (p.n_iblk >= 2 * slots ? 1 : cdiv(2LL * slots, p.n_iblk));
-    int smax = cdiv(n, 2LL * tile);
-    if (S > smax) S = smax;
-    long long pmax = part_cap / ((long long)kComp * (na > 0 ? na : 1));
-    if (S > pmax) S = (int)pmax;
-    if (S < 1) S = 1;
+    const int smax_tiles = cdiv(n, 2LL * tile);
+    const long long pmax = part_cap / ((long long)kComp * (na > 0 ? na : 1));
+    int smax = smax_tiles < pmax ? smax_tiles : (int)pmax;
+    if (smax < 1) smax = 1;
+    int S;
+    if (split > 0) {
+        S = split < smax ? split : smax;
+    } else {
+        const int s0 = p.n_iblk >= 2 * slots ? 1 : cdiv(2LL * slots, p.n_iblk);
+        S = s0 < smax ? s0 : smax;
+        int best = S;
+        double best_fill = wave_fill((long long)p.n_iblk * S, slots);
+        for (int s = S + 1; s <= 4 * S && s <= smax && best_fill < 0.95; ++s) {
+            const double f = wave_fill((long long)p.n_iblk * s, slots);
+            if (f > best_fill + 1e-9) {
+                best = s;
+                best_fill = f;
+            }
+        }
+        S = best;
+    }
     p.jslice = cdiv(cdiv(n, S), tile) * tile;
     p.S = cdiv(n, p.jslice);
     p.items = p.n_iblk * p.S;

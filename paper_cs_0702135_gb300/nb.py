@@ -24,6 +24,7 @@ NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ESTEP, NB_ETIMEOUT, NB_ESTATE = 0, -1,
 NB_DS, NB_FP64 = 0, 1
 NB_FORCE_AUTO, NB_FORCE_IPAR, NB_FORCE_JPAR = 0, 1, 2
 NB_TICK_BITS = 40
+NB_INIT_NO_FORCE = 1
 TICKS_PER_UNIT = 1 << NB_TICK_BITS
 
 _ERRNAMES = {NB_EINVAL: "NB_EINVAL", NB_ENOMEM: "NB_ENOMEM", NB_ECUDA: "NB_ECUDA",
@@ -40,8 +41,14 @@ class nb_opts(ctypes.Structure):
     _fields_ = [("eta", ctypes.c_double), ("eta_init", ctypes.c_double),
                 ("level_min", ctypes.c_int), ("level_fixed", ctypes.c_int),
                 ("precision", ctypes.c_int), ("force_mode", ctypes.c_int),
-                ("split_j", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("split_j", ctypes.c_int), ("flags", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
+
+
+class nb_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("interactions", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("force_launches", ctypes.c_int64),
+                ("force_ms", ctypes.c_double)]
 
 
 _c_dp = ctypes.POINTER(ctypes.c_double)
@@ -65,6 +72,8 @@ SIGNATURES = [
     ("nb_get_state", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("nb_set_state", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("nb_get_active", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _c_ip, _c_lp]),
+    ("nb_set_profiling", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("nb_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(nb_stats), ctypes.c_int]),
     ("nb_num_particles", ctypes.c_int64, [_vp]),
     ("nb_last_error", ctypes.c_char_p, [_vp]),
     ("nb_free", None, [_vp]),
@@ -224,6 +233,17 @@ def nb_get_active(ctx):
     return idx[:na.value].copy(), tt.value
 
 
+def nb_set_profiling(ctx, enable=True):
+    _check(ctx, lib().nb_set_profiling(ctx, 1 if enable else 0))
+
+
+def nb_get_stats(ctx, reset=False):
+    """dict of the context counters (see nb_stats in include/nb.h)."""
+    st = nb_stats()
+    _check(ctx, lib().nb_get_stats(ctx, ctypes.byref(st), 1 if reset else 0))
+    return {name: getattr(st, name) for name, _ in nb_stats._fields_}
+
+
 def nb_num_particles(ctx) -> int:
     return int(lib().nb_num_particles(ctx))
 
@@ -275,6 +295,12 @@ class Context:
 
     def nb_get_active(self):
         return nb_get_active(self.ctx)
+
+    def nb_set_profiling(self, enable=True):
+        return nb_set_profiling(self.ctx, enable)
+
+    def nb_get_stats(self, reset=False):
+        return nb_get_stats(self.ctx, reset)
 
     def nb_free(self):
         nb_free(self.ctx)
