@@ -205,6 +205,44 @@ int nb_set_profiling(nb_ctx *ctx, int enable);
  */
 int nb_get_stats(nb_ctx *ctx, nb_stats *stats, int reset);
 
+/* Largest n_active that nb_force_few_noalloc accepts. */
+#define NB_NOALLOC_MAX_ACTIVE 64
+
+/*
+ * Force on a few particles for callers that may not allocate device memory:
+ * for example a host application that gives this library a fixed share of the
+ * GPU and forbids later cudaMalloc calls, a real-time loop where an
+ * allocation could stall or fail, or a plug-in whose host owns the allocator.
+ * The paper has no counterpart of this entry point; it computes the same sums
+ * as nb_force in the NB_DS precision, in a different summation order.
+ *
+ * Needs no context.  Inputs are device arrays owned by the caller: masses
+ * d_m[n], positions d_x[n][3] and velocities d_v[n][3] (FP64, the state at
+ * which the force is wanted), the indices d_active_idx[n_active] (each in
+ * [0, n): an index outside is clamped, not reported), softening eps >= 0.
+ * Outputs are device arrays d_acc[n_active][3], d_jerk[n_active][3],
+ * d_pot[n_active] (any may be NULL).  The work is enqueued on `stream`
+ * (cudaStream_t, NULL = the legacy default stream) and the call returns
+ * without waiting for it.
+ *
+ * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine.  Its working memory is one fixed array of 7 MiB in the library's
+ * device code, which every GPU that loads the library holds until the process
+ * exits.  The first call on each device looks up that array's device address,
+ * so make that first call before capturing any stream on that device into a
+ * CUDA graph.  All calls share the array and each call writes every part of it
+ * that it reads, so nothing carries over from one call to the next; but calls
+ * whose GPU work overlaps (on two streams at once, or from two host threads)
+ * race on it and must be serialised by the caller.
+ *
+ * Errors: NB_EINVAL (n < 1 or n > 2^31 - 1, n_active outside
+ * [0, NB_NOALLOC_MAX_ACTIVE], eps negative or not finite, a NULL input),
+ * NB_ECUDA (the address lookup or a launch failed).
+ */
+int nb_force_few_noalloc(int64_t n, const double *d_m, const double *d_x, const double *d_v,
+                         double eps, const int32_t *d_active_idx, int32_t n_active, double *d_acc,
+                         double *d_jerk, double *d_pot, void *stream);
+
 /* Number of particles, or -1 for a NULL context. */
 int64_t nb_num_particles(const nb_ctx *ctx);
 

@@ -25,6 +25,7 @@ NB_DS, NB_FP64 = 0, 1
 NB_FORCE_AUTO, NB_FORCE_IPAR, NB_FORCE_JPAR = 0, 1, 2
 NB_TICK_BITS = 40
 NB_INIT_NO_FORCE = 1
+NB_NOALLOC_MAX_ACTIVE = 64
 TICKS_PER_UNIT = 1 << NB_TICK_BITS
 
 _ERRNAMES = {NB_EINVAL: "NB_EINVAL", NB_ENOMEM: "NB_ENOMEM", NB_ECUDA: "NB_ECUDA",
@@ -74,6 +75,8 @@ SIGNATURES = [
     ("nb_get_active", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _c_ip, _c_lp]),
     ("nb_set_profiling", ctypes.c_int, [_vp, ctypes.c_int]),
     ("nb_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(nb_stats), ctypes.c_int]),
+    ("nb_force_few_noalloc", ctypes.c_int, [ctypes.c_int64, _vp, _vp, _vp, ctypes.c_double, _vp,
+                                            ctypes.c_int32, _vp, _vp, _vp, _vp]),
     ("nb_num_particles", ctypes.c_int64, [_vp]),
     ("nb_last_error", ctypes.c_char_p, [_vp]),
     ("nb_free", None, [_vp]),
@@ -242,6 +245,19 @@ def nb_get_stats(ctx, reset=False):
     st = nb_stats()
     _check(ctx, lib().nb_get_stats(ctx, ctypes.byref(st), 1 if reset else 0))
     return {name: getattr(st, name) for name, _ in nb_stats._fields_}
+
+
+def nb_force_few_noalloc(n, d_m, d_x, d_v, eps, d_active_idx, n_active, d_acc=None, d_jerk=None,
+                         d_pot=None, stream=None):
+    """Context-free force on at most NB_NOALLOC_MAX_ACTIVE particles from device
+    arrays (torch CUDA tensors or addresses), for callers that may not allocate
+    device memory; enqueued on `stream` (an int cudaStream_t, None = default)."""
+    rc = lib().nb_force_few_noalloc(int(n), _dptr(d_m), _dptr(d_x), _dptr(d_v), float(eps),
+                                    _dptr(d_active_idx), int(n_active), _dptr(d_acc), _dptr(d_jerk),
+                                    _dptr(d_pot), None if not stream else ctypes.c_void_p(stream))
+    if rc != NB_OK:
+        raise NbError(rc, "nb_force_few_noalloc rejected n=%d n_active=%d eps=%r (limit %d)"
+                      % (n, n_active, eps, NB_NOALLOC_MAX_ACTIVE))
 
 
 def nb_num_particles(ctx) -> int:
