@@ -132,6 +132,22 @@ def nvsmi_index(local_rank):
 
 # ---------------------------------------------------------------------------
 
+def max_over_ranks(x, device):
+    """Maximum of a per-rank float over the process group (x itself alone)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, units_per_step, elapsed_max):
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return world * steps * units_per_step / elapsed_max
+
+
 def fp32_peak_tflops(sms, mhz):
     """FP32 FMA peak: 128 lanes per SM, 2 flop per FMA."""
     return 2.0 * FP32_LANES_PER_SM * sms * mhz * 1e6 / 1e12
@@ -261,12 +277,10 @@ def run_mine(args):
     stats = ctx.nb_get_stats(reset=True)
     ctx.nb_set_profiling(False)
     if world > 1:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = max_over_ranks(elapsed, dev)
         torch.distributed.barrier()
-        elapsed = float(t.item())
     e1 = sum(ctx.nb_energy())
-    value = world * args.steps * inter_per_step / elapsed
+    value = whole_job_rate(world, args.steps, inter_per_step, elapsed)
 
     force_s = stats["force_ms"] / 1e3 / max(1, stats["force_launches"])
     peak = fp32_peak_tflops(sms, MAX_SM_MHZ_FALLBACK)
