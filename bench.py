@@ -59,6 +59,14 @@ def parse_args():
     p.add_argument("--impl", default="mine", choices=["mine", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT)
     p.add_argument("--no-extras", action="store_true", help="skip ladder, FP64 arm, e2e, CPU baseline")
+    p.add_argument("--workload", default="full_active_step", choices=["full_active_step", "blockstep"],
+                   help="blockstep: individual block steps of a Plummer run (Section 2 step loop)")
+    p.add_argument("--t-end", type=float, default=0.25, help="blockstep: end time (multiple of dt_max)")
+    p.add_argument("--eps", type=float, default=None, help="blockstep: softening (default 1/256)")
+    p.add_argument("--seed", type=int, default=None)
+    p.add_argument("--precision", default="ds", choices=["ds", "fp64", "both"])
+    p.add_argument("--sample-errors", type=int, default=0,
+                   help="blockstep: check this many sampled i against the oracle at each of 16 checkpoints")
     return p.parse_args()
 
 
@@ -405,10 +413,115 @@ def run_extras(args, nb, ctx, m, x, v, stream, dev, torch, sample_active):
     return out
 
 
+def run_blockstep(args):
+    """A Plummer run with individual block steps on the device (nb_run, graph
+    replay): interactions/s over the whole run, |dE/E|, the block-size
+    distribution (from a step-by-step replay of the same run), DS and FP64."""
+    import torch
+    import paper_cs_0702135_gb300 as nb
+    from synth import plummer, sample_active
+    n = args.n
+    eps = args.eps if args.eps is not None else 1.0 / 256
+    seed = args.seed if args.seed is not None else 2
+    level_min = 3
+    while (2.0 ** -level_min) > args.t_end or (args.t_end / 2.0 ** -level_min) % 1:
+        level_min += 1
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    m, x, v = plummer(n, seed)
+    precs = {"ds": [nb.NB_DS], "fp64": [nb.NB_FP64], "both": [nb.NB_DS, nb.NB_FP64]}[args.precision]
+    out = {"workload": "blockstep_plummer_N%d_eps%g_t%g" % (n, eps, args.t_end), "N": n, "eps": eps,
+           "seed": seed, "t_end": args.t_end, "level_min": level_min, "eta": 0.01}
+    for prec in precs:
+        name = "ds" if prec == nb.NB_DS else "fp64"
+        ctx = nb.Context(m, x, v, eps, precision=prec, level_min=level_min, stream=stream.cuda_stream)
+        e0 = sum(ctx.nb_energy())
+        st0 = ctx.nb_get_state()
+        ctx.nb_get_stats(reset=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps, inter = ctx.nb_run(args.t_end)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        launches = ctx.nb_get_stats(reset=True)["kernel_launches"]
+        e1 = sum(ctx.nb_energy())
+        res = {"steps": steps, "interactions": inter, "seconds": el, "interactions_per_s": inter / el,
+               "gflops": 60 * inter / el / 1e9, "us_per_step": 1e6 * el / max(1, steps),
+               "energy_rel_err": abs(e1 - e0) / abs(e0), "kernel_launches": launches}
+        if prec == nb.NB_DS:
+            # replay the same run step by step for the block sizes (and sampled errors)
+            ctx.nb_set_state(st0["x"], st0["v"], st0["a"], st0["k"], st0["t"], st0["level"])
+            sizes = []
+            checks = set(np.linspace(0, steps - 1, 16).astype(int).tolist()) if args.sample_errors else set()
+            errs = []
+            for s_ in range(steps):
+                if s_ in checks:
+                    errs.append(sampled_force_errors(ctx, nb, m, eps, args.sample_errors, seed + s_))
+                tb, na = ctx.nb_step()
+                sizes.append(na)
+            sizes = np.array(sizes)
+            edges = [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192, 16384, 32768,
+                     65536, 131072, 262144, 524288, 1048576, 2097152]
+            hist, _ = np.histogram(sizes, bins=edges + [10 ** 12])
+            res["n_active"] = {"mean": float(sizes.mean()), "median": float(np.median(sizes)),
+                               "max": int(sizes.max()), "min": int(sizes.min()),
+                               "hist_log2_bins": {str(e): int(h) for e, h in zip(edges, hist) if h},
+                               "paper_fit_n_block": 0.20 * n ** 0.81,
+                               "paper_fit_steps": 247 * n ** 0.35 * args.t_end}
+            if errs:
+                res["sampled_errors"] = {"checkpoints": len(errs), "per_checkpoint_i": args.sample_errors,
+                                         "max_err_acc": max(e[0] for e in errs),
+                                         "max_err_jerk": max(e[1] for e in errs),
+                                         "max_err_pot": max(e[2] for e in errs),
+                                         "p99_raw_rel_acc": max(e[3] for e in errs)}
+        out[name] = res
+        ctx.nb_free()
+    if "ds" in out and "fp64" in out:
+        out["ds_over_fp64"] = out["ds"]["interactions_per_s"] / out["fp64"]["interactions_per_s"]
+    print(json.dumps(out), flush=True)
+
+
+def sampled_force_errors(ctx, nb, m, eps, k, seed):
+    """Force on k sampled particles at the current (synchronised-or-not) state,
+    DS GPU vs the FP64 oracle on the same predicted positions."""
+    import oracle
+    from synth import sample_active
+    st = ctx.nb_get_state()
+    t_now = int(st["t"].max())
+    n = m.shape[0]
+    # predict everything to the latest particle time with the oracle's predictor
+    xp = np.empty_like(st["x"])
+    vp = np.empty_like(st["v"])
+    dt = (t_now - st["t"]) / float(1 << 40)
+    h = dt / 2.0
+    q = dt / 3.0
+    xp = st["x"] + (st["v"] + h[:, None] * (st["a"] + q[:, None] * st["k"])) * dt[:, None]
+    vp = st["v"] + (st["a"] + h[:, None] * st["k"]) * dt[:, None]
+    idx = sample_active(n, k, seed)
+    ctx.nb_predict(t_now / float(1 << 40))
+    got = ctx.nb_force(idx)
+    ref = oracle.force(m, xp, vp, eps, idx, nthreads=os.cpu_count() or 1)
+    d = xp[None, :, :] - xp[idx, None, :]
+    r2 = np.einsum("ijk,ijk->ij", d, d) + eps * eps
+    sa = np.sum(m[None, :] * np.sqrt(r2 - eps * eps) / r2 ** 1.5, axis=1)
+    w = vp[None, :, :] - vp[idx, None, :]
+    rv = np.einsum("ijk,ijk->ij", d, w)
+    kk = m[None, :, None] * (w / r2[..., None] ** 1.5 - 3 * rv[..., None] * d / r2[..., None] ** 2.5)
+    sk = np.sum(np.linalg.norm(kk, axis=2), axis=1)
+    ea = np.linalg.norm(got[0] - ref[0], axis=1) / np.maximum(np.linalg.norm(ref[0], axis=1), sa / 10)
+    ek = np.linalg.norm(got[1] - ref[1], axis=1) / np.maximum(np.linalg.norm(ref[1], axis=1), sk / 10)
+    ep = np.abs(got[2] - ref[2]) / np.abs(ref[2])
+    raw = np.linalg.norm(got[0] - ref[0], axis=1) / np.linalg.norm(ref[0], axis=1)
+    return float(ea.max()), float(ek.max()), float(ep.max()), float(np.percentile(raw, 99))
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "blockstep":
+        run_blockstep(args)
     else:
         run_mine(args)
 

@@ -42,7 +42,8 @@ extern "C" {
 #define NB_FP64 1 /* all pair arithmetic in FP64 */
 
 #define NB_FORCE_AUTO 0  /* pick the force kernel from n_active */
-#define NB_FORCE_IPAR 1  /* i across threads, j tiles broadcast from shared memory */
+#define NB_FORCE_IPAR 1  /* i across threads, j tiles broadcast from shared memory (the
+                          * small-block variant, one i per thread, serves n_active <= 192) */
 #define NB_FORCE_JPAR 2  /* j across threads, warp-shuffle tree reduction (small n_active) */
 
 #define NB_TICK_BITS 40

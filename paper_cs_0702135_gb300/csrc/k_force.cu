@@ -153,12 +153,13 @@ __device__ __forceinline__ int clamp_index(int i, int n) { return min(max(i, 0),
 // ----------------------------------------------------------------------------
 // DS, i-parallel.
 
-template <int NT, int R, bool SOFT>
+template <int NT, int R, int REG, bool SOFT>
 __global__ void __launch_bounds__(NT) k_force_ipar_ds(ForceArgs fa, JDS J)
 {
     const int na = read_na(fa);
-    if (na <= 0 || use_jpar(na, fa.jpar_max)) return;
-    const Plan P = plan_ipar(na, fa.n, NT * R, NT, fa.slots_ipar, fa.split, fa.part_cap);
+    if (na <= 0 || regime_of(na, fa.jpar_max, fa.small_max) != REG) return;
+    const int slots = REG == kRegSmall ? fa.slots_small : fa.slots_ipar;
+    const Plan P = plan_ipar(na, fa.n, NT * R, NT, slots, fa.split, fa.part_cap);
     __shared__ float4 s_p[NT], s_l[NT], s_v[NT];
     const float eps2 = (float)fa.eps2;
     const int tid = threadIdx.x;
@@ -488,7 +489,19 @@ __global__ void __launch_bounds__(NT) k_force_jpar_f64(ForceArgs fa, JF64 J)
 }
 
 // ----------------------------------------------------------------------------
-// Slice combine: out = sum over slices in slice order (FP64).
+// Slice combine: out = sum over slices in a fixed order (FP64).
+
+__device__ __forceinline__ void write_combined(const ForceOut &o, int c, int a, double s)
+{
+    if (c < 3) {
+        if (o.acc) o.acc[3 * (long long)a + c] = s;
+    } else if (c < 6) {
+        if (o.jerk) o.jerk[3 * (long long)a + (c - 3)] = s;
+    } else if (o.pot) {
+        o.pot[a] = s;
+    }
+}
+
 
 template <int IR, int IR64>
 __global__ void k_force_combine(ForceArgs fa, int precision)
@@ -496,34 +509,48 @@ __global__ void k_force_combine(ForceArgs fa, int precision)
     const int na = read_na(fa);
     if (na <= 0) return;
     int S;
-    if (use_jpar(na, fa.jpar_max)) {
+    const int reg = precision == NB_FP64 ? (use_jpar(na, fa.jpar_max) ? kRegJpar : kRegIpar)
+                                         : regime_of(na, fa.jpar_max, fa.small_max);
+    if (reg == kRegJpar) {
         S = plan_jpar(na, fa.n, kJparNT, kJparIC, fa.slots_jpar, fa.part_cap).S;
     } else {
-        const int iblk = kIparNT * (precision == NB_FP64 ? IR64 : IR);
-        const Plan p = plan_ipar(na, fa.n, iblk, kIparNT, fa.slots_ipar, fa.split, fa.part_cap);
+        const int r = precision == NB_FP64 ? IR64 : (reg == kRegSmall ? kIparSmallR : IR);
+        const int slots = reg == kRegSmall ? fa.slots_small : fa.slots_ipar;
+        const Plan p = plan_ipar(na, fa.n, kIparNT * r, kIparNT, slots, fa.split, fa.part_cap);
         if (p.S == 1) return;
         S = p.S;
     }
     const long long total = (long long)na * kComp;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
+    if (S <= 8) {
+        // one thread per output, slices in order
+        for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+             e += (long long)gridDim.x * blockDim.x) {
+            const int c = (int)(e / na), a = (int)(e % na);
+            double s = 0.0;
+            for (int q = 0; q < S; ++q) s += fa.part[((long long)q * kComp + c) * na + a];
+            write_combined(fa.out, c, a, s);
+        }
+        return;
+    }
+    // one warp per output: lane l sums slices l, l + 32, ... in order, then a
+    // fixed xor tree; the order depends only on S, so results are reproducible
+    const int lane = threadIdx.x & 31;
+    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long e = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; e < total; e += warps) {
         const int c = (int)(e / na), a = (int)(e % na);
         double s = 0.0;
-        for (int q = 0; q < S; ++q) s += fa.part[((long long)q * kComp + c) * na + a];
-        if (c < 3) {
-            if (fa.out.acc) fa.out.acc[3 * (long long)a + c] = s;
-        } else if (c < 6) {
-            if (fa.out.jerk) fa.out.jerk[3 * (long long)a + (c - 3)] = s;
-        } else if (fa.out.pot) {
-            fa.out.pot[a] = s;
-        }
+        for (int q = lane; q < S; q += 32) s += fa.part[((long long)q * kComp + c) * na + a];
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) write_combined(fa.out, c, a, s);
     }
 }
 
 int combine_grid(const ForceArgs &fa)
 {
     if (!fa.na_dev) {
-        long long total = (long long)fa.na_host * kComp;
+        // enough threads for a warp per output when there are many slices
+        long long total = (long long)fa.na_host * kComp * 32;
         long long g = (total + 255) / 256;
         return (int)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
     }
@@ -533,13 +560,19 @@ int combine_grid(const ForceArgs &fa)
 }  // namespace
 
 void launch_force_ds(const ForceArgs &fa, const JDS &j, bool softened, int grid_ipar,
-                     int grid_jpar, cudaStream_t st)
+                     int grid_jpar, int grid_small, cudaStream_t st)
 {
     if (softened) {
-        if (grid_ipar > 0) k_force_ipar_ds<kIparNT, kIparR, true><<<grid_ipar, kIparNT, 0, st>>>(fa, j);
+        if (grid_ipar > 0)
+            k_force_ipar_ds<kIparNT, kIparR, kRegIpar, true><<<grid_ipar, kIparNT, 0, st>>>(fa, j);
+        if (grid_small > 0)
+            k_force_ipar_ds<kIparNT, kIparSmallR, kRegSmall, true><<<grid_small, kIparNT, 0, st>>>(fa, j);
         if (grid_jpar > 0) k_force_jpar_ds<kJparNT, kJparIC, true><<<grid_jpar, kJparNT, 0, st>>>(fa, j);
     } else {
-        if (grid_ipar > 0) k_force_ipar_ds<kIparNT, kIparR, false><<<grid_ipar, kIparNT, 0, st>>>(fa, j);
+        if (grid_ipar > 0)
+            k_force_ipar_ds<kIparNT, kIparR, kRegIpar, false><<<grid_ipar, kIparNT, 0, st>>>(fa, j);
+        if (grid_small > 0)
+            k_force_ipar_ds<kIparNT, kIparSmallR, kRegSmall, false><<<grid_small, kIparNT, 0, st>>>(fa, j);
         if (grid_jpar > 0) k_force_jpar_ds<kJparNT, kJparIC, false><<<grid_jpar, kJparNT, 0, st>>>(fa, j);
     }
     k_force_combine<kIparR, kIparR64><<<combine_grid(fa), 256, 0, st>>>(fa, NB_DS);
@@ -558,19 +591,24 @@ void launch_force_f64(const ForceArgs &fa, const JF64 &j, bool softened, int gri
     k_force_combine<kIparR, kIparR64><<<combine_grid(fa), 256, 0, st>>>(fa, NB_FP64);
 }
 
-int occupancy_force(int precision, bool jpar, int *blocks_per_sm)
+int occupancy_force(int precision, int regime, int *blocks_per_sm)
 {
     cudaError_t e;
     if (precision == NB_FP64)
-        e = jpar ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                       blocks_per_sm, k_force_jpar_f64<kJparNT, kJparIC, true>, kJparNT, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                       blocks_per_sm, k_force_ipar_f64<kIparNT, kIparR64, true>, kIparNT, 0);
+        e = regime == kRegJpar
+                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                      blocks_per_sm, k_force_jpar_f64<kJparNT, kJparIC, true>, kJparNT, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                      blocks_per_sm, k_force_ipar_f64<kIparNT, kIparR64, true>, kIparNT, 0);
+    else if (regime == kRegJpar)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            blocks_per_sm, k_force_jpar_ds<kJparNT, kJparIC, true>, kJparNT, 0);
+    else if (regime == kRegSmall)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            blocks_per_sm, k_force_ipar_ds<kIparNT, kIparSmallR, kRegSmall, true>, kIparNT, 0);
     else
-        e = jpar ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                       blocks_per_sm, k_force_jpar_ds<kJparNT, kJparIC, true>, kJparNT, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                       blocks_per_sm, k_force_ipar_ds<kIparNT, kIparR, true>, kIparNT, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            blocks_per_sm, k_force_ipar_ds<kIparNT, kIparR, kRegIpar, true>, kIparNT, 0);
     return e == cudaSuccess ? 0 : -1;
 }
 

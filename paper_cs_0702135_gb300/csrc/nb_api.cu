@@ -43,7 +43,7 @@ struct nb_ctx {
     double *d_epart = nullptr;
     double *d_stage = nullptr;      // [7n] staging for host I/O
 
-    int slots_ipar = 0, slots_jpar = 0, jpar_max = 0;
+    int slots_ipar = 0, slots_jpar = 0, slots_small = 0, jpar_max = 0, small_max = 0;
     long long t_pred = 0;           // ticks of the last host-driven prediction
     bool force_valid = false;       // results in d_res usable by nb_correct
     int force_na = 0;
@@ -145,9 +145,11 @@ ForceArgs force_args(nb_ctx *c, const int *act, int na_host, const int *na_dev, 
     fa.na_dev = na_dev;
     fa.na_host = na_host;
     fa.jpar_max = c->jpar_max;
+    fa.small_max = c->small_max;
     fa.split = c->o.split_j;
     fa.slots_ipar = c->slots_ipar;
     fa.slots_jpar = c->slots_jpar;
+    fa.slots_small = c->slots_small;
     fa.part_cap = c->part_cap;
     fa.part = c->d_part;
     fa.out = out;
@@ -172,18 +174,22 @@ void enqueue_force(nb_ctx *c, const int *act, int na_host, const int *na_dev, Fo
 {
     const ForceArgs fa = force_args(c, act, na_host, na_dev, out);
     const bool f64 = c->o.precision == NB_FP64;
-    const int iblk = kIparNT * (f64 ? kIparR64 : kIparR);
-    int gi = c->slots_ipar, gj = c->slots_jpar;
+    int gi = c->slots_ipar, gj = c->slots_jpar, gs = f64 ? 0 : c->slots_small;
     if (!na_dev) {
         if (na_host <= 0) return;
-        if (use_jpar(na_host, c->jpar_max)) {
+        const int reg = f64 ? (use_jpar(na_host, c->jpar_max) ? kRegJpar : kRegIpar)
+                            : regime_of(na_host, c->jpar_max, c->small_max);
+        gi = gj = gs = 0;
+        if (reg == kRegJpar) {
             const Plan p = plan_jpar(na_host, c->n, kJparNT, kJparIC, c->slots_jpar, c->part_cap);
-            gi = 0;
             gj = p.items < c->slots_jpar ? p.items : c->slots_jpar;
+        } else if (reg == kRegSmall) {
+            const Plan p = plan_ipar(na_host, c->n, kIparNT * kIparSmallR, kIparNT, c->slots_small,
+                                     c->o.split_j, c->part_cap);
+            gs = p.items < c->slots_small ? p.items : c->slots_small;
         } else {
-            const Plan p = plan_ipar(na_host, c->n, iblk, kIparNT, c->slots_ipar, c->o.split_j,
-                                     c->part_cap);
-            gj = 0;
+            const Plan p = plan_ipar(na_host, c->n, kIparNT * (f64 ? kIparR64 : kIparR), kIparNT,
+                                     c->slots_ipar, c->o.split_j, c->part_cap);
             gi = p.items < c->slots_ipar ? p.items : c->slots_ipar;
         }
     }
@@ -203,8 +209,8 @@ void enqueue_force(nb_ctx *c, const int *act, int na_host, const int *na_dev, Fo
     if (f64)
         launch_force_f64(fa, c->jf, c->eps > 0.0, gi, gj, c->st);
     else
-        launch_force_ds(fa, c->jds, c->eps > 0.0, gi, gj, c->st);
-    c->launches += (gi > 0) + (gj > 0) + 1;
+        launch_force_ds(fa, c->jds, c->eps > 0.0, gi, gj, gs, c->st);
+    c->launches += (gi > 0) + (gj > 0) + (gs > 0) + 1;
     if (timed) {
         if (ev[0] && ev[1]) {
             cudaEventRecord(ev[1], c->st);
@@ -359,14 +365,17 @@ static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, con
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
     const bool f64 = o.precision == NB_FP64;
-    int bi = 0, bj = 0;
-    if (occupancy_force(o.precision, false, &bi) || occupancy_force(o.precision, true, &bj))
+    int bi = 0, bj = 0, bs = 0;
+    if (occupancy_force(o.precision, kRegIpar, &bi) || occupancy_force(o.precision, kRegJpar, &bj) ||
+        occupancy_force(o.precision, kRegSmall, &bs))
         return fail(c, NB_ECUDA, "occupancy query failed");
     c->slots_ipar = c->sms * (bi > 0 ? bi : 1);
     c->slots_jpar = c->sms * (bj > 0 ? bj : 1);
+    c->slots_small = c->sms * (bs > 0 ? bs : 1);
     c->jpar_max = o.force_mode == NB_FORCE_IPAR ? 0
                   : o.force_mode == NB_FORCE_JPAR ? INT_MAX
                                                   : kJparMaxActive;
+    c->small_max = f64 || o.force_mode == NB_FORCE_JPAR ? 0 : kSmallMaxActive;
     const long long iblk = kIparNT * (f64 ? kIparR64 : kIparR);
     // Partials: up to 16 slots' worth of i-blocks, and four slices of all n.
     long long cap = 16LL * c->slots_ipar * iblk;

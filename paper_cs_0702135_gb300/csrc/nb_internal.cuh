@@ -72,7 +72,9 @@ constexpr int kIparUnroll = NB_IPAR_UNROLL;  // j unrolling of the DS inner loop
 constexpr int kIparR64 = 1;    // i per thread, FP64 i-parallel kernel
 constexpr int kJparNT = 256;   // threads per CTA, j-parallel kernels
 constexpr int kJparIC = 4;     // i per pass, j-parallel kernels
-constexpr int kJparMaxActive = 16;  // automatic mode: j-parallel up to this block size
+constexpr int kJparMaxActive = 32;  // automatic mode: j-parallel up to this block size
+constexpr int kIparSmallR = 1;      // i per thread of the small-block DS i-parallel kernel
+constexpr int kSmallMaxActive = 192;  // automatic mode: small-block kernel up to this size
 constexpr int kComp = 7;       // acc xyz, jerk xyz, pot
 
 struct Plan {
@@ -88,19 +90,27 @@ __host__ __device__ inline int cdiv(long long a, long long b) { return (int)((a 
 // Slices are added until there are about two work items per resident CTA,
 // keeping at least two tiles per slice and the partial buffer within
 // part_cap doubles.
-// Fraction of the last wave that does work when items run on slots resident
-// CTAs, as a measure of the tail: waves / ceil(waves).
-__host__ __device__ inline double wave_fill(long long items, int slots)
+// i-parallel: CTAs own iblk consecutive active particles and one j slice.
+// The slice count S starts at s0 = 1, or, with fewer than two i-blocks per
+// resident CTA, at the count that makes two; then among a few candidates
+// (s0 .. s0 + 7 and the counts that fill 1 .. 8 waves of the slots resident
+// CTAs exactly) the smallest whose last wave is at least 95% full is taken,
+// else the one with the fullest last wave.  Slices keep at least two tiles and
+// the partials fit in part_cap doubles.  Integer arithmetic only: this runs at
+// the start of every CTA.
+__host__ __device__ inline bool better_fill(long long items_a, int slots, long long items_b)
 {
-    const long long w = (items + slots - 1) / slots;
-    return (double)items / ((double)w * slots);
+    // fill(x) = x / (ceil(x / slots) * slots); compare fill(a) > fill(b)
+    const long long wa = (items_a + slots - 1) / slots, wb = (items_b + slots - 1) / slots;
+    return items_a * wb > items_b * wa;
 }
 
-// i-parallel: CTAs own iblk consecutive active particles and one j slice.
-// With fewer than two i-blocks per resident CTA, slices are added until there
-// are two; then (in both cases) the slice count is raised, within a factor of
-// four, until the last wave of work items is at least 95% full.  Slices keep
-// at least two tiles each and the partials fit in part_cap doubles.
+__host__ __device__ inline bool fill_ok(long long items, int slots)
+{
+    const long long w = (items + slots - 1) / slots;
+    return 20 * items >= 19 * w * slots;
+}
+
 __host__ __device__ inline Plan plan_ipar(int na, int n, int iblk, int tile, int slots,
                                           int split, long long part_cap)
 {
@@ -114,18 +124,20 @@ __host__ __device__ inline Plan plan_ipar(int na, int n, int iblk, int tile, int
     if (split > 0) {
         S = split < smax ? split : smax;
     } else {
-        const int s0 = p.n_iblk >= 2 * slots ? 1 : cdiv(2LL * slots, p.n_iblk);
-        S = s0 < smax ? s0 : smax;
-        int best = S;
-        double best_fill = wave_fill((long long)p.n_iblk * S, slots);
-        for (int s = S + 1; s <= 4 * S && s <= smax && best_fill < 0.95; ++s) {
-            const double f = wave_fill((long long)p.n_iblk * s, slots);
-            if (f > best_fill + 1e-9) {
-                best = s;
-                best_fill = f;
-            }
+        int s0 = p.n_iblk >= 2 * slots ? 1 : cdiv(2LL * slots, p.n_iblk);
+        if (s0 > smax) s0 = smax;
+        int best = s0, first_ok = fill_ok((long long)p.n_iblk * s0, slots) ? s0 : 0;
+        for (int q = 0; q < 24; ++q) {
+            int s;
+            if (q < 8) s = s0 + q;
+            else if (q < 16) s = (int)(((long long)(q - 7) * slots) / p.n_iblk);
+            else s = cdiv((long long)(q - 15) * slots, p.n_iblk);
+            if (s < s0 || s > smax) continue;
+            const long long it = (long long)p.n_iblk * s;
+            if (fill_ok(it, slots) && (first_ok == 0 || s < first_ok)) first_ok = s;
+            if (better_fill(it, slots, (long long)p.n_iblk * best)) best = s;
         }
-        S = best;
+        S = first_ok ? first_ok : best;
     }
     p.jslice = cdiv(cdiv(n, S), tile) * tile;
     p.S = cdiv(n, p.jslice);
@@ -155,15 +167,27 @@ __host__ __device__ inline Plan plan_jpar(int na, int n, int nt, int ic, int slo
 // Which kernel serves a block of na particles: jpar for na <= jpar_max.
 __host__ __device__ inline bool use_jpar(int na, int jpar_max) { return na <= jpar_max; }
 
+// Force kernels by block size: j-parallel, small-block i-parallel (one i per
+// thread), i-parallel (kIparR i per thread).  small_max <= jpar_max disables
+// the middle one.
+enum Regime { kRegJpar = 0, kRegSmall = 1, kRegIpar = 2 };
+__host__ __device__ inline int regime_of(int na, int jpar_max, int small_max)
+{
+    if (na <= jpar_max) return kRegJpar;
+    if (na <= small_max) return kRegSmall;
+    return kRegIpar;
+}
+
 // Everything a force launch needs.
 struct ForceArgs {
     int n;                    // j count
     const int *act;           // active indices (device)
     const int *na_dev;        // device block size, or nullptr to use na_host
     int na_host;
-    int jpar_max;             // regime boundary (see use_jpar)
+    int jpar_max;             // regime boundaries (see regime_of)
+    int small_max;
     int split;                // forced slice count for i-parallel, 0 = auto
-    int slots_ipar, slots_jpar;
+    int slots_ipar, slots_jpar, slots_small;
     long long part_cap;       // capacity of part in doubles
     double *part;             // slice partials: part[(s * 7 + c) * na + a]
     ForceOut out;
@@ -176,10 +200,10 @@ struct ForceArgs {
 
 // k_force.cu
 void launch_force_ds(const ForceArgs &fa, const JDS &j, bool softened, int grid_ipar, int grid_jpar,
-                     cudaStream_t st);
+                     int grid_small, cudaStream_t st);
 void launch_force_f64(const ForceArgs &fa, const JF64 &j, bool softened, int grid_ipar,
                       int grid_jpar, cudaStream_t st);
-int occupancy_force(int precision, bool jpar, int *blocks_per_sm);
+int occupancy_force(int precision, int regime, int *blocks_per_sm);
 
 // k_step.cu
 void launch_predict(const State &s, long long t_val, const long long *t_ptr, const int *gate,

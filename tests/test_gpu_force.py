@@ -39,7 +39,7 @@ def test_full_sweep(nb, n, precision):
 
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1, 2])
-@pytest.mark.parametrize("na", [1, 7, 16, 17, 31, 32, 33, 255, 256, 257, 1000])
+@pytest.mark.parametrize("na", [1, 7, 16, 17, 31, 32, 33, 64, 65, 191, 192, 193, 255, 256, 257, 1000])
 def test_block_sizes_and_kernels(nb, na, mode, precision):
     n = 3001
     m, x, v = plummer(n, 7)

@@ -1,0 +1,94 @@
+"""Host-side work decomposition of the force kernels (plan_ipar / plan_jpar in
+csrc/nb_internal.cuh), compiled from the same header as the library and
+checked over a grid of sizes on the CPU.
+
+Invariants: the slices cover [0, n) exactly once, slices are whole tiles,
+partial sums fit the buffer whenever there is more than one slice, the item
+count is i-blocks x slices, and the regime boundaries are consistent.
+"""
+import itertools
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = r'''
+#include <cstdio>
+#include "nb_internal.cuh"
+using namespace nbk;
+int main() {
+    int na, n, iblk, tile, slots, split; long long cap; char kind;
+    while (std::scanf(" %c %d %d %d %d %d %d %lld", &kind, &na, &n, &iblk, &tile, &slots, &split, &cap) == 8) {
+        Plan p = kind == 'i' ? plan_ipar(na, n, iblk, tile, slots, split, cap)
+                             : plan_jpar(na, n, tile, iblk, slots, cap);
+        std::printf("%d %d %d %d\n", p.n_iblk, p.S, p.jslice, p.items);
+    }
+    return 0;
+}
+'''
+
+
+@pytest.fixture(scope="module")
+def planner(tmp_path_factory):
+    cxx = shutil.which("g++")
+    cuda_inc = "/usr/local/cuda/include"
+    if not cxx or not os.path.isdir(cuda_inc):
+        pytest.skip("needs g++ and the CUDA headers")
+    d = tmp_path_factory.mktemp("plan")
+    src = d / "plan.cpp"
+    src.write_text(SRC)
+    exe = d / "plan"
+    subprocess.run([cxx, "-std=c++17", "-O1", "-I" + os.path.join(ROOT, "include"),
+                    "-I" + os.path.join(ROOT, "paper_cs_0702135_gb300", "csrc"), "-I" + cuda_inc,
+                    str(src), "-o", str(exe)], check=True)
+    return exe
+
+
+def _run(exe, cases):
+    inp = "\n".join(" ".join(str(v) for v in c) for c in cases)
+    out = subprocess.run([str(exe)], input=inp, capture_output=True, text=True, check=True).stdout
+    return [tuple(int(v) for v in line.split()) for line in out.strip().splitlines()]
+
+
+def test_ipar_plans(planner):
+    cases = []
+    for na, n, (iblk, tile), slots, split in itertools.product(
+            [1, 17, 64, 191, 256, 1000, 4096, 65536, 1 << 20], [2, 130, 4099, 65536, 1 << 20],
+            [(256, 64), (64, 64), (128, 128)], [152, 608, 2432], [0, 1, 7]):
+        if na > n:
+            continue
+        cap = 7 * max(16 * slots * iblk, 4 * n)
+        cases.append(("i", na, n, iblk, tile, slots, split, cap))
+    for c, (nib, S, js, items) in zip(cases, _run(planner, cases)):
+        _, na, n, iblk, tile, slots, split, cap = c
+        assert nib == -(-na // iblk)
+        assert S >= 1 and js % tile == 0 and js > 0
+        assert (S - 1) * js < n <= S * js, c
+        assert items == nib * S
+        if S > 1:
+            assert S * 7 * na <= cap, c
+        if split:
+            assert S <= split
+        # enough work items to fill the GPU whenever the slices allow it: the
+        # plan aims at two per resident CTA; rounding slices up to whole tiles
+        # can at most halve the slice count, so at least one full wave remains
+        if split == 0 and nib < 2 * slots and -(-n // (2 * tile)) >= 2 * slots:
+            assert items >= slots, c
+
+
+def test_jpar_plans(planner):
+    cases = []
+    for na, n, slots in itertools.product([1, 2, 4, 5, 16, 32, 33], [2, 300, 65536, 1 << 20], [152, 304]):
+        if na > n:
+            continue
+        cap = 7 * 8 * slots * 4
+        cases.append(("j", na, n, 4, 256, slots, 0, cap))
+    for c, (nch, S, js, items) in zip(cases, _run(planner, cases)):
+        _, na, n, ic, nt, slots, _, cap = c
+        assert nch == -(-na // ic)
+        assert (S - 1) * js < n <= S * js and js % nt == 0
+        assert S * 7 * na <= cap
+        assert items == nch * S
+        assert S == 1 or js >= 8 * nt
