@@ -71,6 +71,12 @@ def lib():
                               _f64p, _f64p, _i64p, _i32p, ctypes.c_void_p, ctypes.POINTER(_i64),
                               _int]
         L.orc_run.restype = _i64
+        L.orc_force_vjp.argtypes = [_i64, _f64p, _f64p, _f64p, _dbl, _f64p, _f64p, _f64p, _f64p,
+                                    _f64p]
+        L.orc_force_vjp.restype = None
+        L.orc_traj_vjp.argtypes = [_i64, _f64p, _f64p, _f64p, _dbl, _dbl, _i64, _f64p, _f64p, _f64p,
+                                   _f64p, _f64p]
+        L.orc_traj_vjp.restype = _int
         L.orc_max_threads.argtypes = []
         L.orc_max_threads.restype = _int
         _lib = L
@@ -105,6 +111,37 @@ def energy(m, x, v, eps, nthreads=1):
     lib().orc_energy(m.shape[0], m, x, v, float(eps), ctypes.byref(ek), ctypes.byref(ep),
                      int(nthreads))
     return ek.value, ep.value
+
+
+def force_vjp(m, x, v, eps, abar, kbar):
+    """(xbar, vbar, mbar): VJP of every particle's acc and jerk w.r.t. x, v, m."""
+    m, x, v = _c(m), _c(x), _c(v)
+    n = m.shape[0]
+    xb, vb, mb = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n)
+    lib().orc_force_vjp(n, m, x, v, float(eps), _c(abar), _c(kbar), xb, vb, mb)
+    return xb, vb, mb
+
+
+def traj_vjp(m, x0, v0, eps, dt, steps, xbar_T, vbar_T):
+    """Fixed shared-step Hermite trajectory from (x0, v0): returns
+    (x_T, v_T, xbar_0, vbar_0, mbar) for cotangents (xbar_T, vbar_T)."""
+    m = _c(m)
+    n = m.shape[0]
+    x, v = _c(x0).copy(), _c(v0).copy()
+    xb, vb, mb = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n)
+    rc = lib().orc_traj_vjp(n, m, x, v, float(eps), float(dt), int(steps), _c(xbar_T), _c(vbar_T),
+                            xb, vb, mb)
+    if rc != 0:
+        raise RuntimeError("oracle trajectory failed: %d" % rc)
+    return x, v, xb, vb, mb
+
+
+def traj_final(m, x0, v0, eps, dt, steps):
+    """Final (x, v) of the fixed shared-step trajectory (no gradient)."""
+    n = _c(m).shape[0]
+    z = np.zeros((n, 3))
+    x, v, _, _, _ = traj_vjp(m, x0, v0, eps, dt, steps, z, z)
+    return x, v
 
 
 def predict_one(x, v, a, k, dt):

@@ -387,3 +387,166 @@ int64_t orc_run(int64_t n, const double *m, double eps, double eta, int kmin, in
     if (interactions) *interactions = inter;
     return steps;
 }
+
+/* ------------------------------------------------------------------------
+ * Differentiation (no counterpart in the paper, which has no gradients).
+ *
+ * Vector-Jacobian product of the direct-summation acceleration and jerk of
+ * every particle with respect to all positions, velocities and masses: given
+ * cotangents abar_i, kbar_i on acc_i, jerk_i, accumulate xbar, vbar, mbar.
+ * Written as the pair loop of the definition: for every ordered pair (i, j),
+ * j != i, with d = x_j - x_i, w = v_j - v_i, r^2 = |d|^2 + eps^2, s = d.w,
+ *   acc_i  += m_j d / r^3
+ *   jerk_i += m_j (w / r^3 - 3 s d / r^5)
+ * differentiate abar_i . acc_i + kbar_i . jerk_i with respect to d, w, m_j:
+ *   g_d = m_j [ abar/r^3 - 3 (abar.d) d/r^5 - 3 (kbar.w) d/r^5
+ *               - 3 (kbar.d) w/r^5 - 3 s kbar/r^5 + 15 s (kbar.d) d/r^7 ]
+ *   g_w = m_j [ kbar/r^3 - 3 (kbar.d) d/r^5 ]
+ *   g_m = abar.d/r^3 + kbar.(w/r^3 - 3 s d/r^5)
+ * and since d, w are x_j - x_i, v_j - v_i: xbar_j += g_d, xbar_i -= g_d,
+ * vbar_j += g_w, vbar_i -= g_w, mbar_j += g_m.  Outputs are overwritten.
+ */
+void orc_force_vjp(int64_t n, const double *m, const double *x, const double *v, double eps,
+                   const double *abar, const double *kbar, double *xbar, double *vbar,
+                   double *mbar)
+{
+    for (int64_t q = 0; q < 3 * n; q++) xbar[q] = vbar[q] = 0.0;
+    for (int64_t q = 0; q < n; q++) mbar[q] = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        const double *ab = abar + 3 * i, *kb = kbar + 3 * i;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            double d[3], w[3];
+            for (int c = 0; c < 3; c++) {
+                d[c] = x[3 * j + c] - x[3 * i + c];
+                w[c] = v[3 * j + c] - v[3 * i + c];
+            }
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + eps * eps;
+            double r = sqrt(r2);
+            double r3 = r2 * r, r5 = r3 * r2, r7 = r5 * r2;
+            double s = d[0] * w[0] + d[1] * w[1] + d[2] * w[2];
+            double ad = ab[0] * d[0] + ab[1] * d[1] + ab[2] * d[2];
+            double kd = kb[0] * d[0] + kb[1] * d[1] + kb[2] * d[2];
+            double kw = kb[0] * w[0] + kb[1] * w[1] + kb[2] * w[2];
+            for (int c = 0; c < 3; c++) {
+                double gd = m[j] * (ab[c] / r3 - 3.0 * ad * d[c] / r5 - 3.0 * kw * d[c] / r5
+                                    - 3.0 * kd * w[c] / r5 - 3.0 * s * kb[c] / r5
+                                    + 15.0 * s * kd * d[c] / r7);
+                double gw = m[j] * (kb[c] / r3 - 3.0 * kd * d[c] / r5);
+                xbar[3 * j + c] += gd;
+                xbar[3 * i + c] -= gd;
+                vbar[3 * j + c] += gw;
+                vbar[3 * i + c] -= gw;
+            }
+            mbar[j] += ad / r3 + kw / r3 - 3.0 * s * kd / r5;
+        }
+    }
+}
+
+/*
+ * Fixed shared-step Hermite trajectory and its gradient.  With every
+ * particle on the same step dt, one step is (Section 2): predict every
+ * particle, recompute acc and jerk of every particle at the predicted state,
+ * correct every particle.  The initial acc and jerk are the force of the
+ * initial state.  Given the cotangents xbar_T, vbar_T of the final positions
+ * and velocities, the gradient with respect to the initial x, v and the
+ * masses is accumulated by running the steps backwards, each through the
+ * transposes of the (linear) corrector and predictor and the force VJP above.
+ * All intermediate states are stored (plain reverse mode, no checkpointing).
+ * On return x, v hold the final state; xbar, vbar are overwritten with the
+ * gradient with respect to the initial state, mbar with that w.r.t. masses.
+ */
+int orc_traj_vjp(int64_t n, const double *m, double *x, double *v, double eps, double dt,
+                 int64_t steps, const double *xbar_T, const double *vbar_T, double *xbar,
+                 double *vbar, double *mbar)
+{
+    size_t n3 = 3 * (size_t)n;
+    size_t per = 4 * n3; /* x, v, a, k */
+    double *st = (double *)malloc(sizeof(double) * per * (size_t)(steps + 1));
+    double *xp = (double *)malloc(sizeof(double) * n3), *vp = (double *)malloc(sizeof(double) * n3);
+    double *a1 = (double *)malloc(sizeof(double) * n3), *k1 = (double *)malloc(sizeof(double) * n3);
+    double *pot = (double *)malloc(sizeof(double) * (size_t)n);
+    double *ab = (double *)malloc(sizeof(double) * n3), *kb = (double *)malloc(sizeof(double) * n3);
+    double *a1b = (double *)malloc(sizeof(double) * n3), *k1b = (double *)malloc(sizeof(double) * n3);
+    double *xg = (double *)malloc(sizeof(double) * n3), *vg = (double *)malloc(sizeof(double) * n3);
+    double *mg = (double *)malloc(sizeof(double) * (size_t)n);
+    int32_t *all = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!st || !xp || !vp || !a1 || !k1 || !pot || !ab || !kb || !a1b || !k1b || !xg || !vg ||
+        !mg || !all) {
+        free(st); free(xp); free(vp); free(a1); free(k1); free(pot); free(ab); free(kb);
+        free(a1b); free(k1b); free(xg); free(vg); free(mg); free(all);
+        return ORC_ENOMEM;
+    }
+    for (int64_t i = 0; i < n; i++) all[i] = (int32_t)i;
+    const double h = dt / 2.0, q = dt / 3.0;
+
+    /* forward */
+    double *s0 = st;
+    memcpy(s0, x, sizeof(double) * n3);
+    memcpy(s0 + n3, v, sizeof(double) * n3);
+    orc_force(n, m, x, v, eps, n, all, s0 + 2 * n3, s0 + 3 * n3, pot, 1);
+    for (int64_t s = 0; s < steps; s++) {
+        double *cur = st + per * (size_t)s, *nxt = st + per * (size_t)(s + 1);
+        for (int64_t i = 0; i < n; i++)
+            orc_predict_one(cur + 3 * i, cur + n3 + 3 * i, cur + 2 * n3 + 3 * i,
+                            cur + 3 * n3 + 3 * i, dt, xp + 3 * i, vp + 3 * i);
+        orc_force(n, m, xp, vp, eps, n, all, a1, k1, pot, 1);
+        for (int64_t i = 0; i < n; i++) {
+            double a2[3], a3[3];
+            orc_correct_one(xp + 3 * i, vp + 3 * i, cur + 2 * n3 + 3 * i, cur + 3 * n3 + 3 * i,
+                            a1 + 3 * i, k1 + 3 * i, dt, nxt + 3 * i, nxt + n3 + 3 * i, a2, a3);
+        }
+        memcpy(nxt + 2 * n3, a1, sizeof(double) * n3);
+        memcpy(nxt + 3 * n3, k1, sizeof(double) * n3);
+    }
+    memcpy(x, st + per * (size_t)steps, sizeof(double) * n3);
+    memcpy(v, st + per * (size_t)steps + n3, sizeof(double) * n3);
+
+    /* backward: cotangents of the state (x, v, a, k) after step s */
+    for (size_t c = 0; c < n3; c++) {
+        xbar[c] = xbar_T[c];
+        vbar[c] = vbar_T[c];
+        ab[c] = 0.0;
+        kb[c] = 0.0;
+    }
+    for (int64_t i = 0; i < n; i++) mbar[i] = 0.0;
+    for (int64_t s = steps - 1; s >= 0; s--) {
+        double *cur = st + per * (size_t)s;
+        /* corrector: x' = xp + (a2/12 + a3/20) dt^2, v' = vp + (a2/3 + a3/4) dt with
+           a3 = 2 D + (k + k1) dt, a2 = -3 D - (2 k + k1) dt, D = a - a1;
+           the new state's acc and jerk are a1, k1 (cotangents ab, kb on entry) */
+        for (size_t c = 0; c < n3; c++) {
+            double a2b = xbar[c] * dt * dt / 12.0 + vbar[c] * dt / 3.0;
+            double a3b = xbar[c] * dt * dt / 20.0 + vbar[c] * dt / 4.0;
+            double Db = 2.0 * a3b - 3.0 * a2b;
+            a1b[c] = ab[c] - Db;                        /* through D and the new acc */
+            k1b[c] = kb[c] + a3b * dt - a2b * dt;       /* through a3, a2 and the new jerk */
+            ab[c] = Db;                                 /* old acc, through D */
+            kb[c] = a3b * dt - 2.0 * a2b * dt;          /* old jerk */
+        }
+        /* xbar, vbar now hold the cotangents of xp, vp (the corrector adds them) */
+        for (int64_t i = 0; i < n; i++)
+            orc_predict_one(cur + 3 * i, cur + n3 + 3 * i, cur + 2 * n3 + 3 * i,
+                            cur + 3 * n3 + 3 * i, dt, xp + 3 * i, vp + 3 * i);
+        orc_force_vjp(n, m, xp, vp, eps, a1b, k1b, xg, vg, mg);
+        for (int64_t i = 0; i < n; i++) mbar[i] += mg[i];
+        for (size_t c = 0; c < n3; c++) {
+            double xpb = xbar[c] + xg[c], vpb = vbar[c] + vg[c];
+            /* predictor: xp = x + v dt + a h dt + k q h dt, vp = v + a dt + k h dt */
+            xbar[c] = xpb;
+            vbar[c] = xpb * dt + vpb;
+            ab[c] += xpb * h * dt + vpb * dt;
+            kb[c] += xpb * q * h * dt + vpb * h * dt;
+        }
+    }
+    /* initial acc and jerk are the force of the initial state */
+    orc_force_vjp(n, m, st, st + n3, eps, ab, kb, xg, vg, mg);
+    for (int64_t i = 0; i < n; i++) mbar[i] += mg[i];
+    for (size_t c = 0; c < n3; c++) {
+        xbar[c] += xg[c];
+        vbar[c] += vg[c];
+    }
+    free(st); free(xp); free(vp); free(a1); free(k1); free(pot); free(ab); free(kb);
+    free(a1b); free(k1b); free(xg); free(vg); free(mg); free(all);
+    return ORC_OK;
+}

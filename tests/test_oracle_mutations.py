@@ -15,7 +15,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "nbody_oracle.c")
-PINS = ["tests/test_oracle_force.py", "tests/test_oracle_hermite.py"]
+PINS = ["tests/test_oracle_force.py", "tests/test_oracle_hermite.py", "tests/test_oracle_adjoint.py"]
 
 MUTATIONS = {
     "force_sign_repulsive": ("dx[c] = x[3 * j + c] - x[3 * i + c];", "dx[c] = x[3 * i + c] - x[3 * j + c];"),
@@ -40,6 +40,15 @@ MUTATIONS = {
                                   "int64_t e = t[i] + ((int64_t)1 << (ORC_TICK_BITS - lev[i] - 1));"),
     "energy_kinetic_no_half": ("t += 0.5 * m[i] *", "t += m[i] *"),
     "energy_no_softening": ("d2 * d2 + eps * eps);", "d2 * d2);"),
+    "vjp_drop_15_term": ("\n                                    + 15.0 * s * kd * d[c] / r7);", ");"),
+    "vjp_gw_wrong_sign": ("vbar[3 * j + c] += gw;\n                vbar[3 * i + c] -= gw;",
+                          "vbar[3 * j + c] -= gw;\n                vbar[3 * i + c] += gw;"),
+    "vjp_mass_missing_term": ("mbar[j] += ad / r3 + kw / r3 - 3.0 * s * kd / r5;",
+                              "mbar[j] += ad / r3 - 3.0 * s * kd / r5;"),
+    "traj_predictor_transpose": ("kb[c] += xpb * q * h * dt + vpb * h * dt;", "kb[c] += xpb * h * dt + vpb * h * dt;"),
+    "traj_corrector_coeff": ("double a3b = xbar[c] * dt * dt / 20.0", "double a3b = xbar[c] * dt * dt / 12.0"),
+    "traj_k1b_sign": ("k1b[c] = kb[c] + a3b * dt - a2b * dt;", "k1b[c] = kb[c] + a3b * dt + a2b * dt;"),
+    "traj_no_initial_force_vjp": ("        xbar[c] += xg[c];\n        vbar[c] += vg[c];\n", ""),
 }
 
 
