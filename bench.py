@@ -59,12 +59,14 @@ def parse_args():
     p.add_argument("--impl", default="mine", choices=["mine", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT)
     p.add_argument("--no-extras", action="store_true", help="skip ladder, FP64 arm, e2e, CPU baseline")
-    p.add_argument("--workload", default="full_active_step", choices=["full_active_step", "blockstep"],
+    p.add_argument("--workload", default="full_active_step", choices=["full_active_step", "blockstep", "adjoint"],
                    help="blockstep: individual block steps of a Plummer run (Section 2 step loop)")
     p.add_argument("--t-end", type=float, default=0.25, help="blockstep: end time (multiple of dt_max)")
     p.add_argument("--eps", type=float, default=None, help="blockstep: softening (default 1/256)")
     p.add_argument("--seed", type=int, default=None)
     p.add_argument("--precision", default="ds", choices=["ds", "fp64", "both"])
+    p.add_argument("--fd-coords", type=int, default=32, help="adjoint: coordinates checked by FP64 FD")
+    p.add_argument("--oracle-n", type=int, default=1024, help="adjoint: size of the CPU FP64 comparison")
     p.add_argument("--sample-errors", type=int, default=0,
                    help="blockstep: check this many sampled i against the oracle at each of 16 checkpoints")
     return p.parse_args()
@@ -516,12 +518,111 @@ def sampled_force_errors(ctx, nb, m, eps, k, seed):
     return float(ea.max()), float(ek.max()), float(ep.max()), float(np.percentile(raw, 99))
 
 
+def run_adjoint(args):
+    """Differentiable run: Plummer N = 16384 (seed 4), eps = 1/256, 256 shared
+    Hermite steps of 1/1024, checkpoints every 16 steps, DS forward; loss =
+    sum |x_T - x_target|^2 against a seeded Plummer snapshot (seed 5).
+    Reports forward/backward times, gradients checked against FP64 central
+    differences (h = 1e-6, GPU FP64 trajectory) on random coordinates, against
+    the GPU FP64 adjoint, and against the CPU FP64 oracle adjoint at a size the
+    sequential oracle finishes (stated)."""
+    import torch
+    import paper_cs_0702135_gb300 as nb
+    from synth import plummer
+    n = args.n if args.n != N_DEFAULT else 16384
+    eps, level, steps, ck = 1.0 / 256, 10, 256, 16
+    torch.cuda.set_device(0)
+    m, x, v = plummer(n, 4)
+    tgt = plummer(n, 5)[1]
+    out = {"workload": "adjoint_plummer_N%d_eps1/256_dt1/1024_steps%d_ckpt%d" % (n, steps, ck),
+           "N": n, "steps": steps, "checkpoint_every": ck}
+
+    def run(prec, xx=x, vv=v, mm=m, backward=True):
+        c = nb.Context(mm, xx, vv, eps, precision=prec, level_fixed=level, flags=nb.NB_INIT_NO_FORCE)
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c.nb_traj_forward(steps, ck)
+            xt = c.nb_get_state()["x"]
+            t1 = time.perf_counter()
+            loss = float(np.sum((xt - tgt) ** 2))
+            if not backward:
+                return loss
+            g = c.nb_traj_backward(2 * (xt - tgt))
+            t2 = time.perf_counter()
+            return loss, g, t1 - t0, t2 - t1
+        finally:
+            c.nb_free()
+
+    run(nb.NB_DS)   # warm-up (module load, allocations)
+    loss, (gx, gv, gm), tf, tb = run(nb.NB_DS)
+    pairs_f = (steps + 1) * n * (n - 1)
+    out["ds"] = {"loss": loss, "forward_s": tf, "backward_s": tb,
+                 "forward_interactions_per_s": pairs_f / tf,
+                 "backward_pair_evaluations_per_s": (steps * n * (n - 1) + pairs_f) / tb,
+                 "backward_over_forward": tb / tf}
+    loss64, (hx, hv, hm), tf64, tb64 = run(nb.NB_FP64)
+    out["fp64_gpu"] = {"loss": loss64, "forward_s": tf64, "backward_s": tb64}
+    out["ds_vs_fp64_adjoint_rel_err"] = {
+        "x": float(np.linalg.norm(gx - hx) / np.linalg.norm(hx)),
+        "v": float(np.linalg.norm(gv - hv) / np.linalg.norm(hv)),
+        "m": float(np.linalg.norm(gm - hm) / np.linalg.norm(hm))}
+    # FP64 central differences on random coordinates of x0, v0 and m
+    r = np.random.default_rng(7)
+    h = 1e-6
+    rows = []
+    for q in range(args.fd_coords):
+        kind = ("x", "v", "m")[q % 3]
+        i = int(r.integers(n))
+        c3 = int(r.integers(3))
+        xx, vv, mm = x.copy(), v.copy(), m.copy()
+        if kind == "x":
+            xx[i, c3] += h; lp = run(nb.NB_FP64, xx, vv, mm, False); xx[i, c3] -= 2 * h
+            lm = run(nb.NB_FP64, xx, vv, mm, False); an_ds, an64 = gx[i, c3], hx[i, c3]
+        elif kind == "v":
+            vv[i, c3] += h; lp = run(nb.NB_FP64, xx, vv, mm, False); vv[i, c3] -= 2 * h
+            lm = run(nb.NB_FP64, xx, vv, mm, False); an_ds, an64 = gv[i, c3], hv[i, c3]
+        else:
+            mm[i] += h; lp = run(nb.NB_FP64, xx, vv, mm, False); mm[i] -= 2 * h
+            lm = run(nb.NB_FP64, xx, vv, mm, False); an_ds, an64 = gm[i], hm[i]
+        fd = (lp - lm) / (2 * h)
+        rows.append((kind, fd, an_ds, an64))
+    scale = max(abs(r_[1]) for r_ in rows)
+    out["fd_check"] = {"coords": len(rows), "h": h,
+                       "max_abs_err_ds_over_max_fd": max(abs(r_[2] - r_[1]) for r_ in rows) / scale,
+                       "max_abs_err_fp64_over_max_fd": max(abs(r_[3] - r_[1]) for r_ in rows) / scale,
+                       "median_rel_err_ds": float(np.median([abs(r_[2] - r_[1]) / max(abs(r_[1]), 1e-30) for r_ in rows])),
+                       "median_rel_err_fp64": float(np.median([abs(r_[3] - r_[1]) / max(abs(r_[1]), 1e-30) for r_ in rows]))}
+    # CPU FP64 oracle adjoint at a smaller N (the oracle's pair loops are sequential)
+    import oracle
+    no = args.oracle_n
+    mo, xo, vo = plummer(no, 4)
+    to = plummer(no, 5)[1]
+    t0 = time.perf_counter()
+    xt_o, _ = oracle.traj_final(mo, xo, vo, eps, 2.0 ** -level, steps)
+    _, _, oxb, ovb, omb = oracle.traj_vjp(mo, xo, vo, eps, 2.0 ** -level, steps, 2 * (xt_o - to),
+                                          np.zeros((no, 3)))
+    t_orc = time.perf_counter() - t0
+    c = nb.Context(mo, xo, vo, eps, level_fixed=level, flags=nb.NB_INIT_NO_FORCE)
+    c.nb_traj_forward(steps, ck)
+    xt_g = c.nb_get_state()["x"]
+    gxo, gvo, gmo = c.nb_traj_backward(2 * (xt_g - to))
+    c.nb_free()
+    out["oracle_comparison"] = {"N": no, "oracle_seconds": t_orc,
+                                "ds_rel_err_x": float(np.linalg.norm(gxo - oxb) / np.linalg.norm(oxb)),
+                                "ds_rel_err_v": float(np.linalg.norm(gvo - ovb) / np.linalg.norm(ovb)),
+                                "ds_rel_err_m": float(np.linalg.norm(gmo - omb) / np.linalg.norm(omb))}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "blockstep":
         run_blockstep(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_mine(args)
 

@@ -183,6 +183,46 @@ int nb_set_state(nb_ctx *ctx, const double *x, const double *v, const double *a,
  */
 int nb_get_active(nb_ctx *ctx, int32_t *idx, int32_t cap, int32_t *n_active, int64_t *t_ticks);
 
+/*
+ * Differentiation (the paper has no gradients; these extend its method).
+ *
+ * nb_force_vjp: vector-Jacobian product of every particle's acceleration and
+ * jerk (Eq. 1 and the Appendix A pair terms, all particles active) at the
+ * context's current positions and velocities: given the cotangents
+ * abar[n][3], kbar[n][3] (host) of acc and jerk, writes to host arrays
+ * xbar[n][3], vbar[n][3], mbar[n] (any may be NULL) the derivatives of
+ * sum_i (abar_i . acc_i + kbar_i . jerk_i) with respect to every position,
+ * velocity and mass.  Computed in the context's precision (NB_DS: FP32 pair
+ * arithmetic on double-single positions).  Errors: NB_EINVAL, NB_ENOMEM,
+ * NB_ECUDA.
+ */
+int nb_force_vjp(nb_ctx *ctx, const double *abar, const double *kbar, double *xbar, double *vbar,
+                 double *mbar);
+
+/*
+ * nb_traj_forward: from the current state, which must have every particle at
+ * the same time (a context made with opts.level_fixed > 0 keeps it so), run
+ * `steps` Hermite steps of the shared length 2^-level_fixed (Section 2
+ * predictor, force, corrector, with the initial acceleration and jerk taken
+ * as the force of the current state), keeping the state every
+ * `checkpoint_every` steps in device memory.  Afterwards the context holds
+ * the final state.  Errors: NB_ESTATE (no shared step), NB_EINVAL
+ * (need 1 <= checkpoint_every <= steps), NB_ENOMEM, NB_ECUDA.
+ *
+ * nb_traj_backward: given the cotangents xbar_T[n][3] and vbar_T[n][3]
+ * (NULL = zero) of the final positions and velocities of the last
+ * nb_traj_forward, writes the gradient with respect to the initial positions
+ * xbar0[n][3], velocities vbar0[n][3] and masses mbar[n] (host arrays, any may
+ * be NULL).  Each segment between checkpoints is recomputed forward (bit for
+ * bit the same steps), then run backwards through the transposes of the
+ * corrector and predictor and nb_force_vjp's kernel.  The context is left at
+ * the trajectory's final state; it can be called again with other
+ * cotangents.  Errors: NB_ESTATE (no trajectory), NB_EINVAL, NB_ECUDA.
+ */
+int nb_traj_forward(nb_ctx *ctx, int64_t steps, int64_t checkpoint_every);
+int nb_traj_backward(nb_ctx *ctx, const double *xbar_T, const double *vbar_T, double *xbar0,
+                     double *vbar0, double *mbar);
+
 /* Counters of a context (measurement aid; the paper has no counterpart). */
 typedef struct nb_stats {
     int64_t steps;            /* device-driven block steps taken */

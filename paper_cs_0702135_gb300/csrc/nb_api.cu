@@ -53,6 +53,20 @@ struct nb_ctx {
     long long step_nodes = 0;       // kernels in one captured step
     bool capturing = false;
 
+    // differentiable trajectory (nb_traj_forward / nb_traj_backward)
+    double *d_ck = nullptr;         // checkpoints, 12n doubles each: x, v, a, k (SoA)
+    long long ck_slots = 0;
+    double *d_seg = nullptr;        // step states of one segment, 12n doubles each
+    long long seg_slots = 0;
+    double *d_fin = nullptr;        // final state of the trajectory
+    long long *d_tfin = nullptr;    // particle times at its end
+    double *d_cot = nullptr;        // cotangents xb, vb, ab, kb [n][3], mb [n]; VJP xg, vg [n][3], mg [n]
+    VjpRecDS vrec{};
+    VjpRec64 vrec64{};
+    int slots_vjp = 0;
+    bool traj_valid = false;
+    long long traj_steps = 0, traj_ckpt = 0;
+
     // measurement counters (nb_get_stats)
     long long launches = 0;
     bool profiling = false;
@@ -269,7 +283,9 @@ void release(nb_ctx *c)
     void *ptrs[] = {c->d_x, c->d_v, c->d_a, c->d_k, c->d_m, c->d_t, c->d_lev, c->jds.pos_hi,
                     c->jds.pos_lo, c->jds.vel, c->jf.pos, c->jf.vel, c->d_res, c->d_part,
                     c->d_act, c->d_idx, c->d_all, c->d_bitmap, c->d_ctrl, c->d_blockmin,
-                    c->d_blockcnt, c->d_epart, c->d_stage};
+                    c->d_blockcnt, c->d_epart, c->d_stage, c->d_ck, c->d_seg, c->d_fin, c->d_tfin,
+                    c->d_cot, c->vrec.ph, c->vrec.pl, c->vrec.v, c->vrec.ab, c->vrec.kb,
+                    c->vrec64.x, c->vrec64.v, c->vrec64.ab, c->vrec64.kb};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
@@ -280,6 +296,66 @@ void release(nb_ctx *c)
 
 // Full sweep on all particles into d_res (predicted state must be current).
 void enqueue_full_sweep(nb_ctx *c) { enqueue_force(c, c->d_all, c->n, nullptr, res_out(c)); }
+
+// A State view of 12n doubles laid out x, v, a, k (SoA), with the context's
+// masses, times and levels.
+State state_view(nb_ctx *c, double *base)
+{
+    State s = c->S;
+    const long long n3 = 3LL * c->n;
+    s.x = base;
+    s.v = base + n3;
+    s.a = base + 2 * n3;
+    s.k = base + 3 * n3;
+    return s;
+}
+
+// Buffers of the force VJP (records, cotangents, results), allocated on first use.
+int vjp_alloc(nb_ctx *c)
+{
+    if (c->d_cot) return NB_OK;
+    const long long N = c->n;
+    int rc;
+    if ((rc = dalloc(c, &c->d_cot, 20 * N))) return rc;
+    if (c->o.precision == NB_FP64) {
+        if ((rc = dalloc(c, &c->vrec64.x, N)) || (rc = dalloc(c, &c->vrec64.v, N)) ||
+            (rc = dalloc(c, &c->vrec64.ab, N)) || (rc = dalloc(c, &c->vrec64.kb, N)))
+            return rc;
+    } else {
+        if ((rc = dalloc(c, &c->vrec.ph, N)) || (rc = dalloc(c, &c->vrec.pl, N)) ||
+            (rc = dalloc(c, &c->vrec.v, N)) || (rc = dalloc(c, &c->vrec.ab, N)) ||
+            (rc = dalloc(c, &c->vrec.kb, N)))
+            return rc;
+    }
+    c->slots_vjp = vjp_slots(c->o.precision, c->sms);
+    return NB_OK;
+}
+
+double *cot(nb_ctx *c, int which)  // 0 xb, 1 vb, 2 ab, 3 kb, 4 mb, 5 xg, 6 vg, 7 mg
+{
+    const long long n3 = 3LL * c->n, N = c->n;
+    const long long off[8] = {0, n3, 2 * n3, 3 * n3, 4 * n3, 4 * n3 + N, 5 * n3 + N, 6 * n3 + N};
+    return c->d_cot + off[which];
+}
+
+// VJP of every particle's acc and jerk at the records in c->vrec / vrec64,
+// results into xg, vg, mg.
+void enqueue_vjp(nb_ctx *c)
+{
+    VjpArgs va{};
+    va.n = c->n;
+    va.eps2 = c->eps * c->eps;
+    va.slots = c->slots_vjp;
+    va.part_cap = c->part_cap;
+    va.part = c->d_part;
+    va.rec = c->vrec;
+    va.rec64 = c->vrec64;
+    va.m = c->d_m;
+    va.xbar = cot(c, 5);
+    va.vbar = cot(c, 6);
+    va.mbar = cot(c, 7);
+    c->launches += launch_force_vjp(va, c->o.precision, c->eps > 0.0, c->st);
+}
 
 int copy_results_out(nb_ctx *c, int na, double *acc, double *jerk, double *pot, cudaMemcpyKind k)
 {
@@ -720,6 +796,143 @@ int nb_get_active(nb_ctx *c, int32_t *idx, int32_t cap, int32_t *na, int64_t *t_
         CK(cudaStreamSynchronize(c->st));
     }
     return NB_OK;
+}
+
+int nb_force_vjp(nb_ctx *c, const double *abar, const double *kbar, double *xbar, double *vbar,
+                 double *mbar)
+{
+    if (!c) return NB_EINVAL;
+    if (!abar || !kbar) return fail(c, NB_EINVAL, "abar and kbar are required");
+    const long long N = c->n;
+    if (!finite_all(abar, 3 * N) || !finite_all(kbar, 3 * N))
+        return fail(c, NB_EINVAL, "non-finite cotangent");
+    int rc = vjp_alloc(c);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(cot(c, 2), abar, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(cot(c, 3), kbar, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));
+    launch_adj_initial_rec(c->S, cot(c, 2), cot(c, 3), c->o.precision, c->vrec, c->vrec64, c->st);
+    c->launches += 1;
+    enqueue_vjp(c);
+    CK(cudaGetLastError());
+    if (xbar) CK(cudaMemcpyAsync(xbar, cot(c, 5), sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->st));
+    if (vbar) CK(cudaMemcpyAsync(vbar, cot(c, 6), sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->st));
+    if (mbar) CK(cudaMemcpyAsync(mbar, cot(c, 7), sizeof(double) * N, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return NB_OK;
+}
+
+int nb_traj_forward(nb_ctx *c, int64_t steps, int64_t checkpoint_every)
+{
+    if (!c) return NB_EINVAL;
+    if (c->o.level_fixed <= 0)
+        return fail(c, NB_ESTATE, "a trajectory needs the shared step (opts.level_fixed > 0)");
+    if (steps < 1 || checkpoint_every < 1 || checkpoint_every > steps || steps > (1LL << 30))
+        return fail(c, NB_EINVAL, "need 1 <= checkpoint_every <= steps");
+    int rc = vjp_alloc(c);
+    if (rc) return rc;
+    const long long N = c->n, per = 12 * N;
+    const long long nck = (steps + checkpoint_every - 1) / checkpoint_every;
+    if (c->ck_slots < nck) {
+        if (c->d_ck) cudaFree(c->d_ck);
+        c->d_ck = nullptr;
+        c->ck_slots = 0;
+        if ((rc = dalloc(c, &c->d_ck, nck * per))) return rc;
+        c->ck_slots = nck;
+    }
+    if (c->seg_slots < checkpoint_every) {
+        if (c->d_seg) cudaFree(c->d_seg);
+        c->d_seg = nullptr;
+        c->seg_slots = 0;
+        if ((rc = dalloc(c, &c->d_seg, checkpoint_every * per))) return rc;
+        c->seg_slots = checkpoint_every;
+    }
+    if (!c->d_fin && ((rc = dalloc(c, &c->d_fin, per)) || (rc = dalloc(c, &c->d_tfin, N)))) return rc;
+    if ((rc = set_t_end(c, LLONG_MAX))) return rc;
+    // the initial acceleration and jerk are the force of the initial state
+    launch_predict(c->S, 0, &c->d_ctrl->t_now, nullptr, c->o.precision, c->jds, c->jf, c->st);
+    enqueue_full_sweep(c);
+    launch_set_ak(c->S, c->d_res, c->d_res + 3 * N, c->st);
+    c->launches += 2;
+    for (long long s = 0; s < steps; ++s) {
+        if (s % checkpoint_every == 0) {
+            launch_copy_state(state_view(c, c->d_ck + (s / checkpoint_every) * per), c->S, c->st);
+            c->launches += 1;
+        }
+        enqueue_step(c);
+    }
+    launch_copy_state(state_view(c, c->d_fin), c->S, c->st);
+    c->launches += 1;
+    CK(cudaMemcpyAsync(c->d_tfin, c->d_t, sizeof(long long) * N, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaGetLastError());
+    c->force_valid = false;
+    if ((rc = sync_ctrl(c))) return rc;
+    c->traj_valid = true;
+    c->traj_steps = steps;
+    c->traj_ckpt = checkpoint_every;
+    return NB_OK;
+}
+
+int nb_traj_backward(nb_ctx *c, const double *xbar_T, const double *vbar_T, double *xbar0,
+                     double *vbar0, double *mbar)
+{
+    if (!c) return NB_EINVAL;
+    if (!c->traj_valid) return fail(c, NB_ESTATE, "nb_traj_backward needs nb_traj_forward first");
+    if (!xbar_T) return fail(c, NB_EINVAL, "xbar_T is required");
+    const long long N = c->n, per = 12 * N;
+    if (!finite_all(xbar_T, 3 * N) || (vbar_T && !finite_all(vbar_T, 3 * N)))
+        return fail(c, NB_EINVAL, "non-finite cotangent");
+    int rc = sync_ctrl(c);
+    if (rc) return rc;
+    const Ctrl saved = *c->h_ctrl;
+    const double dt = ldexp(1.0, -c->o.level_fixed);
+    CK(cudaMemcpyAsync(cot(c, 0), xbar_T, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));
+    if (vbar_T)
+        CK(cudaMemcpyAsync(cot(c, 1), vbar_T, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));
+    else
+        CK(cudaMemsetAsync(cot(c, 1), 0, sizeof(double) * 3 * N, c->st));
+    CK(cudaMemsetAsync(cot(c, 2), 0, sizeof(double) * (6 * N + N), c->st));  // ab, kb, mb
+    const long long steps = c->traj_steps, ck = c->traj_ckpt;
+    const long long nseg = (steps + ck - 1) / ck;
+    for (long long seg = nseg - 1; seg >= 0; --seg) {
+        const long long s0 = seg * ck, len = (s0 + ck < steps ? ck : steps - s0);
+        // recompute the segment's step states from its checkpoint
+        launch_copy_state(c->S, state_view(c, c->d_ck + seg * per), c->st);
+        c->launches += 1;
+        for (long long q = 0; q < len; ++q) {
+            launch_copy_state(state_view(c, c->d_seg + q * per), c->S, c->st);
+            c->launches += 1;
+            enqueue_step(c);
+        }
+        for (long long q = len - 1; q >= 0; --q) {
+            launch_adj_pre(state_view(c, c->d_seg + q * per), dt, cot(c, 0), cot(c, 1), cot(c, 2),
+                           cot(c, 3), c->o.precision, c->vrec, c->vrec64, c->st);
+            enqueue_vjp(c);
+            launch_adj_post(c->n, dt, cot(c, 0), cot(c, 1), cot(c, 2), cot(c, 3), cot(c, 4),
+                            cot(c, 5), cot(c, 6), cot(c, 7), c->st);
+            c->launches += 2;
+        }
+    }
+    // the initial acceleration and jerk were the force of the initial state
+    launch_adj_initial_rec(state_view(c, c->d_ck), cot(c, 2), cot(c, 3), c->o.precision, c->vrec,
+                           c->vrec64, c->st);
+    enqueue_vjp(c);
+    launch_add3(c->n, cot(c, 0), cot(c, 5), cot(c, 1), cot(c, 6), cot(c, 4), cot(c, 7), c->st);
+    c->launches += 2;
+    CK(cudaGetLastError());
+    if (xbar0) CK(cudaMemcpyAsync(xbar0, cot(c, 0), sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->st));
+    if (vbar0) CK(cudaMemcpyAsync(vbar0, cot(c, 1), sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->st));
+    if (mbar) CK(cudaMemcpyAsync(mbar, cot(c, 4), sizeof(double) * N, cudaMemcpyDeviceToHost, c->st));
+    // leave the context at the end of the trajectory, as after nb_traj_forward
+    launch_copy_state(c->S, state_view(c, c->d_fin), c->st);
+    CK(cudaMemcpyAsync(c->d_t, c->d_tfin, sizeof(long long) * N, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if ((rc = sync_ctrl(c))) return rc;  // errors raised during the recomputation
+    c->h_ctrl->t_now = saved.t_now;
+    c->h_ctrl->steps = saved.steps;
+    c->h_ctrl->interactions = saved.interactions;
+    CK(cudaMemcpyAsync(c->d_ctrl, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->st));
+    c->force_valid = false;
+    return sync_ctrl(c);
 }
 
 int nb_set_profiling(nb_ctx *c, int enable)

@@ -195,6 +195,30 @@ struct ForceArgs {
     int *err;                 // device error word
 };
 
+// Reverse mode (k_adjoint.cu).  Force-VJP records: DS (x_hi, y_hi, z_hi, m),
+// (x_lo, y_lo, z_lo, 0), (vx, vy, vz, 0), (abar, 0), (kbar, 0); FP64 (x, y,
+// z, m), (v, 0), (abar, 0), (kbar, 0).
+struct VjpRec {
+    float4 ph, pl, v, ab, kb;
+};
+struct VjpRecDS {
+    float4 *ph, *pl, *v, *ab, *kb;
+};
+struct VjpRec64 {
+    double4_32a *x, *v, *ab, *kb;
+};
+struct VjpArgs {
+    int n;
+    double eps2;
+    int slots;
+    long long part_cap;
+    double *part;          // slice partials part[(s * 7 + c) * n + k]
+    VjpRecDS rec;
+    VjpRec64 rec64;
+    const double *m;
+    double *xbar, *vbar, *mbar;  // outputs [n][3], [n][3], [n] (overwritten)
+};
+
 // ---------------------------------------------------------------------------
 // Launchers (defined in the .cu files).
 
@@ -227,5 +251,21 @@ void launch_gather_state(const State &s, double *x, double *v, double *a, double
 void launch_scatter_state(const State &s, const double *x, const double *v, const double *a,
                           const double *k, cudaStream_t st);
 void launch_iota(int *p, int n, cudaStream_t st);
+
+// k_adjoint.cu
+int vjp_slots(int precision, int sms);
+int vjp_tile();
+int launch_force_vjp(const VjpArgs &va, int precision, bool softened, cudaStream_t st);
+void launch_adj_pre(const State &s, double dt, const double *xb, const double *vb, double *ab,
+                    double *kb, int precision, const VjpRecDS &rec, const VjpRec64 &rec64,
+                    cudaStream_t st);
+void launch_adj_post(int n, double dt, double *xb, double *vb, double *ab, double *kb, double *mb,
+                     const double *xg, const double *vg, const double *mg, cudaStream_t st);
+void launch_adj_initial_rec(const State &s, const double *ab, const double *kb, int precision,
+                            const VjpRecDS &rec, const VjpRec64 &rec64, cudaStream_t st);
+void launch_add3(int n, double *dst, const double *src, double *dst2, const double *src2,
+                 double *dstm, const double *srcm, cudaStream_t st);
+void launch_set_ak(const State &s, const double *acc, const double *jerk, cudaStream_t st);
+void launch_copy_state(const State &dst, const State &src, cudaStream_t st);
 
 }  // namespace nbk

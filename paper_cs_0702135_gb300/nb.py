@@ -73,6 +73,9 @@ SIGNATURES = [
     ("nb_get_state", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("nb_set_state", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("nb_get_active", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _c_ip, _c_lp]),
+    ("nb_force_vjp", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    ("nb_traj_forward", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64]),
+    ("nb_traj_backward", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("nb_set_profiling", ctypes.c_int, [_vp, ctypes.c_int]),
     ("nb_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(nb_stats), ctypes.c_int]),
     ("nb_force_few_noalloc", ctypes.c_int, [ctypes.c_int64, _vp, _vp, _vp, ctypes.c_double, _vp,
@@ -236,6 +239,29 @@ def nb_get_active(ctx):
     return idx[:na.value].copy(), tt.value
 
 
+def nb_force_vjp(ctx, abar, kbar):
+    """(xbar[n,3], vbar[n,3], mbar[n]) for cotangents of every acc and jerk."""
+    n = int(lib().nb_num_particles(ctx))
+    a, k = _f64(abar, (n, 3)), _f64(kbar, (n, 3))
+    xb, vb, mb = np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
+    _check(ctx, lib().nb_force_vjp(ctx, _ptr(a), _ptr(k), _ptr(xb), _ptr(vb), _ptr(mb)))
+    return xb, vb, mb
+
+
+def nb_traj_forward(ctx, steps, checkpoint_every):
+    _check(ctx, lib().nb_traj_forward(ctx, int(steps), int(checkpoint_every)))
+
+
+def nb_traj_backward(ctx, xbar_T, vbar_T=None):
+    """(xbar0[n,3], vbar0[n,3], mbar[n]) for cotangents of the final x, v."""
+    n = int(lib().nb_num_particles(ctx))
+    xt = _f64(xbar_T, (n, 3))
+    vt = None if vbar_T is None else _f64(vbar_T, (n, 3))
+    xb, vb, mb = np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
+    _check(ctx, lib().nb_traj_backward(ctx, _ptr(xt), _ptr(vt), _ptr(xb), _ptr(vb), _ptr(mb)))
+    return xb, vb, mb
+
+
 def nb_set_profiling(ctx, enable=True):
     _check(ctx, lib().nb_set_profiling(ctx, 1 if enable else 0))
 
@@ -311,6 +337,15 @@ class Context:
 
     def nb_get_active(self):
         return nb_get_active(self.ctx)
+
+    def nb_force_vjp(self, abar, kbar):
+        return nb_force_vjp(self.ctx, abar, kbar)
+
+    def nb_traj_forward(self, steps, checkpoint_every):
+        return nb_traj_forward(self.ctx, steps, checkpoint_every)
+
+    def nb_traj_backward(self, xbar_T, vbar_T=None):
+        return nb_traj_backward(self.ctx, xbar_T, vbar_T)
 
     def nb_set_profiling(self, enable=True):
         return nb_set_profiling(self.ctx, enable)
