@@ -59,13 +59,16 @@ def parse_args():
     p.add_argument("--impl", default="mine", choices=["mine", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT)
     p.add_argument("--no-extras", action="store_true", help="skip ladder, FP64 arm, e2e, CPU baseline")
-    p.add_argument("--workload", default="full_active_step", choices=["full_active_step", "blockstep", "adjoint"],
+    p.add_argument("--workload", default="full_active_step", choices=["full_active_step", "blockstep", "adjoint", "ensemble"],
                    help="blockstep: individual block steps of a Plummer run (Section 2 step loop)")
     p.add_argument("--t-end", type=float, default=0.25, help="blockstep: end time (multiple of dt_max)")
     p.add_argument("--eps", type=float, default=None, help="blockstep: softening (default 1/256)")
     p.add_argument("--seed", type=int, default=None)
     p.add_argument("--precision", default="ds", choices=["ds", "fp64", "both"])
     p.add_argument("--fd-coords", type=int, default=32, help="adjoint: coordinates checked by FP64 FD")
+    p.add_argument("--clusters", type=int, default=4096, help="ensemble: number of clusters")
+    p.add_argument("--baseline-sample", type=int, default=32,
+                   help="ensemble: clusters timed one by one through the single-system path")
     p.add_argument("--oracle-n", type=int, default=1024, help="adjoint: size of the CPU FP64 comparison")
     p.add_argument("--sample-errors", type=int, default=0,
                    help="blockstep: check this many sampled i against the oracle at each of 16 checkpoints")
@@ -615,6 +618,74 @@ def run_adjoint(args):
     print(json.dumps(out), flush=True)
 
 
+def run_ensemble(args):
+    """Batched ensemble: independent Plummer clusters (N log-uniform in
+    [32, 4096], Salpeter masses on [0.1, 100], virial ratio uniform in
+    [0.3, 0.7], seed 5), eps = 1/256, eta = 0.01, each to t = 1 with its own
+    block steps; one graph-replayed launch per ensemble step, launch
+    configuration from the autotuner.  Compared with per-cluster launches: the
+    single-system path (nb_run per cluster), timed on a seeded sample of
+    clusters and scaled to all of them."""
+    import torch
+    import paper_cs_0702135_gb300 as nb
+    from synth import ensemble
+    torch.cuda.set_device(0)
+    C = args.clusters
+    t0 = time.perf_counter()
+    cl = ensemble(C, 5)
+    gen_s = time.perf_counter() - t0
+    off = np.zeros(C + 1, dtype=np.int64)
+    for c, (m, _, _) in enumerate(cl):
+        off[c + 1] = off[c] + m.shape[0]
+    m = np.concatenate([c[0] for c in cl])
+    x = np.concatenate([c[1] for c in cl])
+    v = np.concatenate([c[2] for c in cl])
+    eps = 1.0 / 256
+    e = nb.Ensemble(off, m, x, v, eps)
+    th, gm, ms_tuned = e.nb_ens_tune(10)
+    k0, p0 = e.nb_ens_energy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    launches, inter = e.nb_ens_run(1.0)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    k1, p1 = e.nb_ens_energy()
+    st = e.nb_ens_get_state()
+    e.nb_ens_free()
+    dE = np.abs((k1 + p1) - (k0 + p0)) / np.abs(k0 + p0)
+    sizes = np.diff(off)
+    out = {"workload": "ensemble_%d_plummer_salpeter_N32-4096_eps1/256_t1" % C, "clusters": C,
+           "particles": int(off[-1]), "generation_s": gen_s,
+           "tuned": {"threads": th, "gmax": gm, "ms_per_step_at_start": ms_tuned},
+           "launches": launches, "seconds": el, "clusters_per_s": C / el,
+           "interactions": inter, "interactions_per_s": inter / el, "gflops": 60 * inter / el / 1e9,
+           "steps_per_cluster": {"min": int(st["steps"].min()), "median": float(np.median(st["steps"])),
+                                 "max": int(st["steps"].max())},
+           "energy_rel_err": {"median": float(np.median(dE)), "p90": float(np.percentile(dE, 90)),
+                              "max": float(dE.max()), "frac_le_1e-6": float(np.mean(dE <= 1e-6))},
+           "all_at_t_end": bool(np.all(st["t"] == (1 << 40)))}
+    # per-cluster launches: the single-system path, one cluster at a time
+    r = np.random.default_rng(55)
+    pick = np.sort(r.choice(C, size=min(args.baseline_sample, C), replace=False))
+    tb, ib = 0.0, 0
+    for c in pick:
+        mc, xc, vc = cl[c]
+        ctx = nb.Context(mc, xc, vc, eps)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, it = ctx.nb_run(1.0)
+        torch.cuda.synchronize()
+        tb += time.perf_counter() - t0
+        ib += it
+        ctx.nb_free()
+    out["per_cluster_launches"] = {"sample": int(len(pick)), "sample_seconds": tb,
+                                   "sample_interactions": ib,
+                                   "extrapolated_seconds": tb * C / len(pick),
+                                   "clusters_per_s": len(pick) / tb,
+                                   "ensemble_speedup_clusters_per_s": (C / el) / (len(pick) / tb)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -623,6 +694,8 @@ def main():
         run_blockstep(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
+    elif args.workload == "ensemble":
+        run_ensemble(args)
     else:
         run_mine(args)
 

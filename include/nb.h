@@ -223,6 +223,63 @@ int nb_traj_forward(nb_ctx *ctx, int64_t steps, int64_t checkpoint_every);
 int nb_traj_backward(nb_ctx *ctx, const double *xbar_T, const double *vbar_T, double *xbar0,
                      double *vbar0, double *mbar);
 
+/*
+ * Ensembles: many independent systems ("clusters") integrated together, each
+ * with its own block time steps (Section 2 step loop per cluster).  The paper
+ * integrates one system; this batches it.  Cluster c holds particles
+ * offsets[c] .. offsets[c+1]-1 of the concatenated arrays m[P], x[P][3],
+ * v[P][3] (host, FP64; 1 <= cluster size <= 4096; P = offsets[n_clusters]).
+ * Precision is NB_DS; opts.level_fixed must be 0.  One ensemble step is one
+ * GPU launch in which every unfinished cluster takes its next block step
+ * (schedule, predict, force, correct for that cluster in one CTA).
+ */
+typedef struct nb_ens nb_ens;
+
+/* Creates the ensemble and computes every cluster's start-up force and steps.
+ * Errors: NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ESTEP.  On error *ens is NULL and
+ * nb_ens_last_error(NULL) describes it. */
+int nb_ens_init(nb_ens **ens, int32_t n_clusters, const int64_t *offsets, const double *m,
+                const double *x, const double *v, double eps, const nb_opts *opts);
+
+/* Launch configuration: threads per CTA (256, 512 or 1024) and the largest
+ * number of lanes that share one active particle's j loop (1, 2, ..., 32). */
+int nb_ens_configure(nb_ens *ens, int threads, int gmax);
+
+/* Autotuner: times `launches_per_candidate` ensemble steps for every
+ * configuration from the current state (restored after each), keeps the
+ * fastest and reports it (outputs may be NULL; *ms_out per step).  The state
+ * is unchanged on return.  Errors: NB_EINVAL, NB_ENOMEM, NB_ECUDA. */
+int nb_ens_tune(nb_ens *ens, int launches_per_candidate, int *threads_out, int *gmax_out,
+                double *ms_out);
+
+/* Ensemble steps (replayed from a captured CUDA graph) until every cluster
+ * has reached t_end (a multiple of its largest step) or max_launches steps;
+ * outputs (may be NULL): steps launched and interactions (sum over clusters
+ * of n_active (n_c - 1)).  Errors: NB_EINVAL, NB_ESTEP, NB_ECUDA. */
+int nb_ens_run(nb_ens *ens, double t_end, int64_t max_launches, int64_t *launches_out,
+               int64_t *interactions_out);
+
+/* One ensemble step (waits for it).  Errors: NB_ESTEP, NB_ECUDA. */
+int nb_ens_step(nb_ens *ens);
+
+/* Force on every particle of every cluster at the particles' current state
+ * (all active; host outputs acc[P][3], jerk[P][3], pot[P], any may be NULL). */
+int nb_ens_force(nb_ens *ens, double *acc, double *jerk, double *pot);
+
+/* Per-cluster kinetic and softened potential energy (FP64) at the stored
+ * state (exact when the cluster is synchronised): host ekin[C], epot[C]. */
+int nb_ens_energy(nb_ens *ens, double *ekin, double *epot);
+
+/* State I/O ([P][3] FP64, int64 ticks, levels; per-cluster step and
+ * interaction counters), any output may be NULL; set requires all arrays. */
+int nb_ens_get_state(nb_ens *ens, double *x, double *v, double *a, double *k, int64_t *t_ticks,
+                     int32_t *level, int64_t *steps, int64_t *interactions);
+int nb_ens_set_state(nb_ens *ens, const double *x, const double *v, const double *a,
+                     const double *k, const int64_t *t_ticks, const int32_t *level);
+
+const char *nb_ens_last_error(const nb_ens *ens);
+void nb_ens_free(nb_ens *ens);
+
 /* Counters of a context (measurement aid; the paper has no counterpart). */
 typedef struct nb_stats {
     int64_t steps;            /* device-driven block steps taken */

@@ -1,0 +1,950 @@
+// k_ensemble.cu -- many independent clusters advanced together: one launch per
+// ensemble block step advances every unfinished cluster by its own next block
+// step (Section 2 step loop: select the block, predict, force, correct).
+//
+// A CTA owns a whole cluster for that step, so nothing waits across CTAs:
+//   1. block time t_next = min over the cluster of t_i + dt_i (CTA reduction);
+//   2. every particle predicted to t_next (FP64, same arithmetic as the
+//      single-system predictor) into double-single j records in shared memory
+//      (a 4096-particle cluster takes 192 KiB), and the block compacted in
+//      ascending order (ballot + prefix sums);
+//   3. force on the block: g consecutive lanes share one active particle and
+//      split its j loop (g = the largest power of two <= threads / n_active,
+//      capped at gmax), FP32 pair arithmetic on double-single positions with
+//      TwoSum-promoted partials, a shuffle reduction inside the lane group;
+//   4. the group's first lane corrects its particle (FP64 corrector and Aarseth
+//      step, same arithmetic as the single-system corrector).  The force reads
+//      only shared-memory records, so correcting while other groups still sum
+//      is safe.
+// CTAs take clusters from a work counter in decreasing size (largest first);
+// each cluster is computed by one CTA, so results do not depend on which.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nb_internal.cuh"
+
+namespace nbk {
+namespace {
+
+constexpr int kEnsMaxN = 4096;       // largest cluster
+constexpr int kPromote = 64;         // j per FP32 partial before TwoSum promotion
+constexpr double kTickD = 0x1p-40;
+
+struct EnsArgs {
+    int C;                    // clusters
+    const long long *off;     // [C + 1] particle offsets
+    const int *order;         // clusters in decreasing size
+    State s;                  // all particles, SoA over the total count
+    float eps2;
+    double eta, eta_init;
+    int level_min;
+    long long t_end;
+    int gmax;                 // largest lane group per active particle
+    int *work;                // work counter (zeroed before each launch)
+    int *done;                // [C]
+    long long *steps;         // [C]
+    long long *inter;         // [C] sum of n_active (n - 1)
+    int *err;
+    double *out_acc, *out_jerk, *out_pot;  // force-only mode: [P][3], [P][3], [P]
+};
+
+__device__ __forceinline__ float rsqrt_sfu(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
+{
+    float s = hi + x;
+    float bb = s - hi;
+    float e = (hi - (s - bb)) + (x - bb);
+    hi = s;
+    lo += e;
+}
+
+__device__ __forceinline__ void ds_add(float &h, float &l, float h2, float l2)
+{
+    float s = h + h2;
+    float bb = s - h;
+    float e = (h - (s - bb)) + (h2 - bb);
+    h = s;
+    l = (l + l2) + e;
+}
+
+__device__ __forceinline__ double ticks_to_time(long long d)
+{
+    return __dmul_rn(__ll2double_rn(d), kTickD);
+}
+
+__device__ __forceinline__ void predict1(double x, double v, double a, double k, double dt,
+                                         double &xp, double &vp)
+{
+    const double h = __ddiv_rn(dt, 2.0);
+    const double q = __ddiv_rn(dt, 3.0);
+    xp = __dadd_rn(x, __dmul_rn(__dadd_rn(v, __dmul_rn(h, __dadd_rn(a, __dmul_rn(q, k)))), dt));
+    vp = __dadd_rn(v, __dmul_rn(__dadd_rn(a, __dmul_rn(h, k)), dt));
+}
+
+__device__ __forceinline__ double norm3(double u0, double u1, double u2)
+{
+    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(u0, u0), __dmul_rn(u1, u1)), __dmul_rn(u2, u2)));
+}
+
+__device__ __forceinline__ bool level_of(double dt_raw, int kmin, int &level)
+{
+    if (isnan(dt_raw) || dt_raw < 0x1p-40) return false;
+    int k;
+    if (isinf(dt_raw)) {
+        k = kmin;
+    } else {
+        const long long bits = __double_as_longlong(dt_raw);
+        k = 1023 - (int)((bits >> 52) & 0x7FF);
+        if (k < kmin) k = kmin;
+    }
+    level = k;
+    return true;
+}
+
+__device__ __forceinline__ int next_level(int k_old, int k_q, long long t_new, int kmin)
+{
+    if (k_q > k_old) return k_q;
+    if (k_q < k_old && k_old > kmin) {
+        const long long twice_old = 1LL << (kTickBits - k_old + 1);
+        if (t_new % twice_old == 0) return k_old - 1;
+    }
+    return k_old;
+}
+
+// FP32 pair on double-single positions; pair j == i contributes nothing.
+__device__ __forceinline__ void pair(const float4 &p, const float4 &l, const float4 &w,
+                                     const float4 &ip, const float4 &il, const float4 &iv,
+                                     float eps2, bool self, float acc[3], float jk[3], float &pot)
+{
+    const float dx = (p.x - ip.x) + (l.x - il.x);
+    const float dy = (p.y - ip.y) + (l.y - il.y);
+    const float dz = (p.z - ip.z) + (l.z - il.z);
+    const float ux = w.x - iv.x, uy = w.y - iv.y, uz = w.z - iv.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+    const float rv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+    float rinv = rsqrt_sfu(r2);
+    rinv = (self || !(r2 > 0.0f)) ? 0.0f : rinv;
+    const float rinv2 = rinv * rinv;
+    const float mr = p.w * rinv;
+    const float mr3 = mr * rinv2;
+    const float b = -3.0f * rv * rinv2;
+    acc[0] = fmaf(mr3, dx, acc[0]);
+    acc[1] = fmaf(mr3, dy, acc[1]);
+    acc[2] = fmaf(mr3, dz, acc[2]);
+    jk[0] = fmaf(mr3, fmaf(b, dx, ux), jk[0]);
+    jk[1] = fmaf(mr3, fmaf(b, dy, uy), jk[1]);
+    jk[2] = fmaf(mr3, fmaf(b, dz, uz), jk[2]);
+    pot -= mr;
+}
+
+template <typename T, typename Op>
+__device__ __forceinline__ T cta_reduce(T v, Op op, T *smem)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) smem[warp] = v;
+    __syncthreads();
+    T r = smem[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = op(r, smem[w]);
+    __syncthreads();
+    return r;
+}
+
+struct MinLL {
+    __device__ long long operator()(long long a, long long b) const { return a < b ? a : b; }
+};
+
+// Force on the listed particles of one cluster from its shared-memory records;
+// the lane group's first lane receives the double-precision sums in res[7].
+// Returns false for lanes that hold no result (or when `s` is out of range).
+__device__ __forceinline__ void group_force(const float4 *s_ph, const float4 *s_pl,
+                                            const float4 *s_v, int n, int i, int g, int lig,
+                                            float eps2, double res[7])
+{
+    const float4 ip = s_ph[i], il = s_pl[i], iv = s_v[i];
+    float hi[7] = {0, 0, 0, 0, 0, 0, 0}, lo[7] = {0, 0, 0, 0, 0, 0, 0};
+    float ta[3] = {0, 0, 0}, tk[3] = {0, 0, 0}, tp = 0.0f;
+    int cnt = 0;
+    for (int j = lig; j < n; j += g) {
+        pair(s_ph[j], s_pl[j], s_v[j], ip, il, iv, eps2, j == i, ta, tk, tp);
+        if (++cnt == kPromote) {
+            const float t7[7] = {ta[0], ta[1], ta[2], tk[0], tk[1], tk[2], tp};
+#pragma unroll
+            for (int c = 0; c < 7; ++c) two_sum_acc(hi[c], lo[c], t7[c]);
+            ta[0] = ta[1] = ta[2] = tk[0] = tk[1] = tk[2] = tp = 0.0f;
+            cnt = 0;
+        }
+    }
+    {
+        const float t7[7] = {ta[0], ta[1], ta[2], tk[0], tk[1], tk[2], tp};
+#pragma unroll
+        for (int c = 0; c < 7; ++c) two_sum_acc(hi[c], lo[c], t7[c]);
+    }
+    // reduce inside the lane group (g consecutive lanes of one warp)
+    for (int o = 1; o < g; o <<= 1) {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi[c], o);
+            const float l2 = __shfl_xor_sync(0xffffffffu, lo[c], o);
+            ds_add(hi[c], lo[c], h2, l2);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 7; ++c) res[c] = (double)hi[c] + (double)lo[c];
+}
+
+enum EnsMode { kEnsStep = 0, kEnsForce = 1, kEnsInit = 2 };
+
+template <int NT, int MODE>
+__global__ void __launch_bounds__(NT) k_ens(EnsArgs ea)
+{
+    extern __shared__ float4 sm[];
+    float4 *s_ph = sm, *s_pl = sm + kEnsMaxN, *s_v = sm + 2 * kEnsMaxN;
+    int *s_act = (int *)(sm + 3 * kEnsMaxN);
+    __shared__ long long s_red[NT / 32];
+    __shared__ int s_wtot[NT / 32];
+    __shared__ int s_cluster;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const State &S = ea.s;
+    const int P = S.n;
+
+    for (;;) {
+        if (tid == 0) s_cluster = atomicAdd(ea.work, 1);
+        __syncthreads();
+        const int q = s_cluster;
+        __syncthreads();
+        if (q >= ea.C) break;
+        const int c = ea.order[q];
+        const long long o = ea.off[c];
+        const int n = (int)(ea.off[c + 1] - o);
+        if (MODE == kEnsStep && ea.done[c]) continue;
+
+        // 1. block time
+        long long tn = 0;
+        if (MODE == kEnsStep) {
+            long long mn = LLONG_MAX;
+            for (int i = tid; i < n; i += NT)
+                mn = min(mn, S.t[o + i] + (1LL << (kTickBits - S.lev[o + i])));
+            tn = cta_reduce(mn, MinLL(), s_red);
+            if (tn > ea.t_end) {
+                if (tid == 0) ea.done[c] = 1;
+                continue;
+            }
+        }
+        // 2. predict into shared memory, compact the block
+        int running = 0;
+        for (int base = 0; base < n; base += NT) {
+            const int i = base + tid;
+            bool f = false;
+            if (i < n) {
+                const long long gi = o + i;
+                const double dt = MODE == kEnsStep ? ticks_to_time(tn - S.t[gi]) : 0.0;
+                double xp[3], vp[3];
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc)
+                    predict1(S.x[cc * (long long)P + gi], S.v[cc * (long long)P + gi],
+                             S.a[cc * (long long)P + gi], S.k[cc * (long long)P + gi], dt, xp[cc], vp[cc]);
+                float hi[3], lo[3];
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    hi[cc] = __double2float_rn(xp[cc]);
+                    lo[cc] = __double2float_rn(__dsub_rn(xp[cc], (double)hi[cc]));
+                }
+                s_ph[i] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(S.m[gi]));
+                s_pl[i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+                s_v[i] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
+                                     __double2float_rn(vp[2]), 0.0f);
+                f = MODE == kEnsStep ? (S.t[gi] + (1LL << (kTickBits - S.lev[gi])) == tn) : true;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (lane == 0) s_wtot[warp] = __popc(bal);
+            __syncthreads();
+            int woff = 0, tot = 0;
+            for (int w = 0; w < NT / 32; ++w) {
+                woff += w < warp ? s_wtot[w] : 0;
+                tot += s_wtot[w];
+            }
+            if (f) s_act[running + woff + __popc(bal & ((1u << lane) - 1u))] = i;
+            running += tot;
+            __syncthreads();
+        }
+        const int na = running;
+        if (MODE == kEnsStep && tid == 0) {
+            ea.steps[c] += 1;
+            ea.inter[c] += (long long)na * (n - 1);
+        }
+        // 3./4. force on the block and correction (or output)
+        int g = 1;
+        while (g < ea.gmax && g * 2 * na <= NT) g <<= 1;
+        const int groups = NT / g;
+        const int grp = tid / g, lig = tid % g;
+        const int iters = (na + groups - 1) / groups;  // the same for every lane (shuffles below)
+        for (int it = 0; it < iters; ++it) {
+            const int sidx = grp + it * groups;
+            const bool valid = sidx < na;
+            const int i = s_act[valid ? sidx : 0];
+            double res[7];
+            group_force(s_ph, s_pl, s_v, n, i, g, lig, ea.eps2, res);
+            if (!valid || lig != 0) continue;
+            const long long gi = o + i;
+            if (MODE == kEnsForce) {
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    ea.out_acc[3 * gi + cc] = res[cc];
+                    ea.out_jerk[3 * gi + cc] = res[3 + cc];
+                }
+                ea.out_pot[gi] = res[6];
+                continue;
+            }
+            if (MODE == kEnsInit) {
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    S.a[cc * (long long)P + gi] = res[cc];
+                    S.k[cc * (long long)P + gi] = res[3 + cc];
+                }
+                S.t[gi] = 0;
+                const double nk = norm3(res[3], res[4], res[5]);
+                const double dt0 = nk == 0.0 ? (double)INFINITY
+                                             : __ddiv_rn(__dmul_rn(ea.eta_init, norm3(res[0], res[1], res[2])), nk);
+                int lv;
+                if (!level_of(dt0, ea.level_min, lv)) {
+                    atomicCAS(ea.err, 0, NB_ESTEP);
+                    lv = kTickBits;
+                }
+                S.lev[gi] = lv;
+                continue;
+            }
+            // corrector and new step (same arithmetic as the single-system corrector)
+            const double dt = ticks_to_time(tn - S.t[gi]);
+            double a2[3], a3[3], ap[3] = {res[0], res[1], res[2]}, kp[3] = {res[3], res[4], res[5]};
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const long long e = cc * (long long)P + gi;
+                const double x = S.x[e], v = S.v[e], a = S.a[e], k = S.k[e];
+                double xp, vp;
+                predict1(x, v, a, k, dt, xp, vp);
+                const double d = __dsub_rn(a, ap[cc]);
+                a3[cc] = __dadd_rn(__dmul_rn(2.0, d), __dmul_rn(__dadd_rn(k, kp[cc]), dt));
+                a2[cc] = __dsub_rn(__dmul_rn(-3.0, d), __dmul_rn(__dadd_rn(__dmul_rn(2.0, k), kp[cc]), dt));
+                S.x[e] = __dadd_rn(xp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[cc], 12.0), __ddiv_rn(a3[cc], 20.0)),
+                                                 __dmul_rn(dt, dt)));
+                S.v[e] = __dadd_rn(vp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[cc], 3.0), __ddiv_rn(a3[cc], 4.0)), dt));
+                S.a[e] = ap[cc];
+                S.k[e] = kp[cc];
+            }
+            S.t[gi] = tn;
+            const double dt2 = __dmul_rn(dt, dt), dt3 = __dmul_rn(dt2, dt);
+            double s1[3], cr[3];
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const double s0 = __ddiv_rn(__dmul_rn(2.0, a2[cc]), dt2);
+                cr[cc] = __ddiv_rn(__dmul_rn(6.0, a3[cc]), dt3);
+                s1[cc] = __dadd_rn(s0, __dmul_rn(cr[cc], dt));
+            }
+            const double nav = norm3(ap[0], ap[1], ap[2]), nk = norm3(kp[0], kp[1], kp[2]);
+            const double ns = norm3(s1[0], s1[1], s1[2]), nc = norm3(cr[0], cr[1], cr[2]);
+            const double num = __dadd_rn(__dmul_rn(nav, ns), __dmul_rn(nk, nk));
+            const double den = __dadd_rn(__dmul_rn(nk, nc), __dmul_rn(ns, ns));
+            const double dt_raw = den == 0.0 ? (double)INFINITY : __dsqrt_rn(__ddiv_rn(__dmul_rn(ea.eta, num), den));
+            int kq;
+            if (!level_of(dt_raw, ea.level_min, kq)) {
+                atomicCAS(ea.err, 0, NB_ESTEP);
+                kq = kTickBits;
+            }
+            S.lev[gi] = next_level(S.lev[gi], kq, tn, ea.level_min);
+        }
+        __syncthreads();
+    }
+}
+
+// Energy of every cluster at its particles' own times (exact when the cluster
+// is synchronised): kinetic from FP64 velocities, potential as the FP64 pair
+// sum -sum_{i<j} m_i m_j / sqrt(r^2 + eps^2), per cluster in a fixed order.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_ens_energy(EnsArgs ea, double eps2, double *ekin, double *epot)
+{
+    __shared__ double s_red[NT / 32];
+    const int tid = threadIdx.x;
+    const State &S = ea.s;
+    const long long P = S.n;
+    for (int c = blockIdx.x; c < ea.C; c += gridDim.x) {
+        const long long o = ea.off[c];
+        const int n = (int)(ea.off[c + 1] - o);
+        double ke = 0.0, pe = 0.0;
+        for (int i = tid; i < n; i += NT) {
+            const long long gi = o + i;
+            const double vx = S.v[gi], vy = S.v[P + gi], vz = S.v[2 * P + gi];
+            ke += 0.5 * S.m[gi] * (vx * vx + vy * vy + vz * vz);
+            const double xi = S.x[gi], yi = S.x[P + gi], zi = S.x[2 * P + gi];
+            double row = 0.0;
+            for (int j = i + 1; j < n; ++j) {
+                const long long gj = o + j;
+                const double dx = S.x[gj] - xi, dy = S.x[P + gj] - yi, dz = S.x[2 * P + gj] - zi;
+                row += S.m[gj] / sqrt(dx * dx + dy * dy + dz * dz + eps2);
+            }
+            pe -= S.m[gi] * row;
+        }
+        struct Add {
+            __device__ double operator()(double a, double b) const { return a + b; }
+        };
+        ke = cta_reduce(ke, Add(), s_red);
+        pe = cta_reduce(pe, Add(), s_red);
+        if (tid == 0) {
+            ekin[c] = ke;
+            epot[c] = pe;
+        }
+    }
+}
+
+// host AoS [P][3] -> device SoA staging -> state arrays
+__global__ void k_aos_to_soa(const double *aos, double *soa, long long P)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 3 * P;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / 3, c = e % 3;
+        soa[c * P + i] = aos[e];
+    }
+}
+
+__global__ void k_soa_to_aos(const double *soa, double *aos, long long P)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 3 * P;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / 3, c = e % 3;
+        aos[e] = soa[c * P + i];
+    }
+}
+
+}  // namespace
+}  // namespace nbk
+
+using namespace nbk;
+
+// ---------------------------------------------------------------------------
+// Host side: the nb_ens context and its C ABI.
+
+struct nb_ens {
+    int C = 0;
+    long long P = 0;
+    double eps = 0.0;
+    nb_opts o{};
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int sms = 0;
+    State S{};
+    long long *d_off = nullptr;
+    int *d_order = nullptr;
+    double *d_x = nullptr, *d_v = nullptr, *d_a = nullptr, *d_k = nullptr, *d_m = nullptr;
+    long long *d_t = nullptr;
+    int *d_lev = nullptr;
+    int *d_work = nullptr, *d_done = nullptr, *d_err = nullptr;
+    long long *d_steps = nullptr, *d_inter = nullptr;
+    double *d_stage = nullptr;   // [7 P] host I/O staging
+    double *d_backup = nullptr;  // state copy for tuning
+    long long *d_tbak = nullptr;
+    int *d_lbak = nullptr;
+    int nt = 512, gmax = 8;      // launch configuration (tunable)
+    long long t_end = LLONG_MAX;
+    cudaGraphExec_t graph = nullptr;
+    int graph_nt = 0, graph_gmax = 0;
+    long long graph_tend = -1;
+    long long launches = 0;
+    std::string err;
+};
+
+namespace ens_impl {
+
+thread_local std::string g_ens_init_err;
+
+int efail(nb_ens *e, int code, const char *fmt, ...)
+{
+    if (e) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        e->err = buf;
+    }
+    return code;
+}
+
+#define ECK(call)                                                                         \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return efail(e, e_ == cudaErrorMemoryAllocation ? NB_ENOMEM : NB_ECUDA,       \
+                         "%s: %s", #call, cudaGetErrorString(e_));                        \
+    } while (0)
+
+size_t ens_smem() { return 3 * sizeof(float4) * kEnsMaxN + sizeof(int) * kEnsMaxN; }
+
+EnsArgs ens_args(nb_ens *e)
+{
+    EnsArgs a{};
+    a.C = e->C;
+    a.off = e->d_off;
+    a.order = e->d_order;
+    a.s = e->S;
+    a.eps2 = (float)(e->eps * e->eps);
+    a.eta = e->o.eta;
+    a.eta_init = e->o.eta_init;
+    a.level_min = e->o.level_min;
+    a.t_end = e->t_end;
+    a.gmax = e->gmax;
+    a.work = e->d_work;
+    a.done = e->d_done;
+    a.steps = e->d_steps;
+    a.inter = e->d_inter;
+    a.err = e->d_err;
+    return a;
+}
+
+template <int NT, int MODE>
+int launch_ens_t(nb_ens *e, const EnsArgs &a)
+{
+    static bool configured = false;
+    if (!configured) {
+        if (cudaFuncSetAttribute(k_ens<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ens_smem()) != cudaSuccess)
+            return efail(e, NB_ECUDA, "cannot reserve %zu bytes of shared memory", ens_smem());
+        configured = true;
+    }
+    k_ens<NT, MODE><<<e->sms, NT, ens_smem(), e->st>>>(a);
+    return NB_OK;
+}
+
+template <int MODE>
+int launch_ens(nb_ens *e, const EnsArgs &a)
+{
+    switch (e->nt) {
+    case 256: return launch_ens_t<256, MODE>(e, a);
+    case 1024: return launch_ens_t<1024, MODE>(e, a);
+    default: return launch_ens_t<512, MODE>(e, a);
+    }
+}
+
+// One ensemble block step: zero the work counter, one persistent launch.
+int enqueue_ens_step(nb_ens *e)
+{
+    ECK(cudaMemsetAsync(e->d_work, 0, sizeof(int), e->st));
+    int rc = launch_ens<kEnsStep>(e, ens_args(e));
+    e->launches += 1;
+    return rc;
+}
+
+int ens_sync(nb_ens *e)
+{
+    int h_err = 0;
+    ECK(cudaMemcpyAsync(&h_err, e->d_err, sizeof(int), cudaMemcpyDeviceToHost, e->st));
+    ECK(cudaStreamSynchronize(e->st));
+    ECK(cudaGetLastError());
+    if (h_err) {
+        ECK(cudaMemsetAsync(e->d_err, 0, sizeof(int), e->st));
+        ECK(cudaStreamSynchronize(e->st));
+        return efail(e, h_err, "a new time step fell below 2^-40 in some cluster");
+    }
+    return NB_OK;
+}
+
+template <typename T>
+int ealloc(nb_ens *e, T **p, long long count)
+{
+    if (count < 1) count = 1;
+    if (cudaMalloc((void **)p, sizeof(T) * (size_t)count) != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return efail(e, NB_ENOMEM, "cudaMalloc of %lld bytes failed", (long long)(sizeof(T) * count));
+    }
+    return NB_OK;
+}
+
+void ens_release(nb_ens *e)
+{
+    if (e->st) cudaStreamSynchronize(e->st);
+    if (e->graph) cudaGraphExecDestroy(e->graph);
+    void *ptrs[] = {e->d_off, e->d_order, e->d_x, e->d_v, e->d_a, e->d_k, e->d_m, e->d_t,
+                    e->d_lev, e->d_work, e->d_done, e->d_err, e->d_steps, e->d_inter,
+                    e->d_stage, e->d_backup, e->d_tbak, e->d_lbak};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (e->own_stream && e->st) cudaStreamDestroy(e->st);
+}
+
+bool finite_all(const double *p, long long cnt)
+{
+    for (long long i = 0; i < cnt; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+int grid_of(long long n) { return (int)std::min<long long>(4096, std::max<long long>(1, (n + 255) / 256)); }
+
+int ens_init_impl(nb_ens *e, int32_t C, const int64_t *off, const double *m, const double *x,
+                  const double *v, double eps, const nb_opts *opts)
+{
+    nb_opts o;
+    nb_default_opts(&o);
+    if (opts) o = *opts;
+    if (C < 1 || !off || !m || !x || !v) return efail(e, NB_EINVAL, "bad arguments");
+    if (!std::isfinite(eps) || eps < 0.0) return efail(e, NB_EINVAL, "eps must be finite and >= 0");
+    if (o.level_min < 0 || o.level_min > kTickBits || o.level_fixed != 0 || o.precision != NB_DS)
+        return efail(e, NB_EINVAL, "ensembles use DS precision and individual block steps");
+    if (!(o.eta > 0.0) || !(o.eta_init > 0.0)) return efail(e, NB_EINVAL, "eta must be positive");
+    if (off[0] != 0) return efail(e, NB_EINVAL, "offsets must start at 0");
+    std::vector<std::pair<long long, int>> sizes;
+    for (int c = 0; c < C; ++c) {
+        const long long nc = off[c + 1] - off[c];
+        if (nc < 1 || nc > kEnsMaxN)
+            return efail(e, NB_EINVAL, "cluster %d has %lld particles (1..%d allowed)", c, nc, kEnsMaxN);
+        sizes.push_back({-nc, c});
+    }
+    const long long P = off[C];
+    if (P > INT_MAX / 8) return efail(e, NB_EINVAL, "too many particles");
+    if (!finite_all(m, P) || !finite_all(x, 3 * P) || !finite_all(v, 3 * P))
+        return efail(e, NB_EINVAL, "non-finite input");
+    for (long long i = 0; i < P; ++i)
+        if (m[i] < 0.0) return efail(e, NB_EINVAL, "negative mass");
+    std::stable_sort(sizes.begin(), sizes.end());
+    std::vector<int> order(C);
+    for (int q = 0; q < C; ++q) order[q] = sizes[q].second;
+
+    e->C = C;
+    e->P = P;
+    e->eps = eps;
+    e->o = o;
+    if (o.stream) {
+        e->st = (cudaStream_t)o.stream;
+    } else {
+        ECK(cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking));
+        e->own_stream = true;
+    }
+    int dev = 0;
+    ECK(cudaGetDevice(&dev));
+    ECK(cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, dev));
+    int rc;
+    if ((rc = ealloc(e, &e->d_off, C + 1)) || (rc = ealloc(e, &e->d_order, C)) ||
+        (rc = ealloc(e, &e->d_x, 3 * P)) || (rc = ealloc(e, &e->d_v, 3 * P)) ||
+        (rc = ealloc(e, &e->d_a, 3 * P)) || (rc = ealloc(e, &e->d_k, 3 * P)) ||
+        (rc = ealloc(e, &e->d_m, P)) || (rc = ealloc(e, &e->d_t, P)) || (rc = ealloc(e, &e->d_lev, P)) ||
+        (rc = ealloc(e, &e->d_work, 1)) || (rc = ealloc(e, &e->d_done, C)) || (rc = ealloc(e, &e->d_err, 1)) ||
+        (rc = ealloc(e, &e->d_steps, C)) || (rc = ealloc(e, &e->d_inter, C)) ||
+        (rc = ealloc(e, &e->d_stage, 7 * P)))
+        return rc;
+    e->S.x = e->d_x;
+    e->S.v = e->d_v;
+    e->S.a = e->d_a;
+    e->S.k = e->d_k;
+    e->S.m = e->d_m;
+    e->S.t = e->d_t;
+    e->S.lev = e->d_lev;
+    e->S.n = (int)P;
+    ECK(cudaMemcpyAsync(e->d_off, off, sizeof(long long) * (C + 1), cudaMemcpyHostToDevice, e->st));
+    ECK(cudaMemcpyAsync(e->d_order, order.data(), sizeof(int) * C, cudaMemcpyHostToDevice, e->st));
+    ECK(cudaMemcpyAsync(e->d_m, m, sizeof(double) * P, cudaMemcpyHostToDevice, e->st));
+    ECK(cudaMemcpyAsync(e->d_stage, x, sizeof(double) * 3 * P, cudaMemcpyHostToDevice, e->st));
+    k_aos_to_soa<<<grid_of(3 * P), 256, 0, e->st>>>(e->d_stage, e->d_x, P);
+    ECK(cudaStreamSynchronize(e->st));
+    ECK(cudaMemcpyAsync(e->d_stage, v, sizeof(double) * 3 * P, cudaMemcpyHostToDevice, e->st));
+    k_aos_to_soa<<<grid_of(3 * P), 256, 0, e->st>>>(e->d_stage, e->d_v, P);
+    ECK(cudaMemsetAsync(e->d_a, 0, sizeof(double) * 3 * P, e->st));
+    ECK(cudaMemsetAsync(e->d_k, 0, sizeof(double) * 3 * P, e->st));
+    ECK(cudaMemsetAsync(e->d_t, 0, sizeof(long long) * P, e->st));
+    ECK(cudaMemsetAsync(e->d_done, 0, sizeof(int) * C, e->st));
+    ECK(cudaMemsetAsync(e->d_err, 0, sizeof(int), e->st));
+    ECK(cudaMemsetAsync(e->d_steps, 0, sizeof(long long) * C, e->st));
+    ECK(cudaMemsetAsync(e->d_inter, 0, sizeof(long long) * C, e->st));
+    // start-up: force on every particle of every cluster, initial steps
+    ECK(cudaMemsetAsync(e->d_work, 0, sizeof(int), e->st));
+    if ((rc = launch_ens<kEnsInit>(e, ens_args(e)))) return rc;
+    ECK(cudaGetLastError());
+    return ens_sync(e);
+}
+
+}  // namespace ens_impl
+
+using namespace ens_impl;
+
+extern "C" {
+
+int nb_ens_init(nb_ens **ens, int32_t n_clusters, const int64_t *offsets, const double *m,
+                const double *x, const double *v, double eps, const nb_opts *opts)
+{
+    g_ens_init_err.clear();
+    if (!ens) return NB_EINVAL;
+    *ens = nullptr;
+    nb_ens *e = new (std::nothrow) nb_ens();
+    if (!e) return NB_ENOMEM;
+    const int rc = ens_init_impl(e, n_clusters, offsets, m, x, v, eps, opts);
+    if (rc != NB_OK) {
+        g_ens_init_err = e->err;
+        ens_release(e);
+        delete e;
+        return rc;
+    }
+    *ens = e;
+    return NB_OK;
+}
+
+void nb_ens_free(nb_ens *e)
+{
+    if (!e) return;
+    ens_release(e);
+    delete e;
+}
+
+const char *nb_ens_last_error(const nb_ens *e)
+{
+    if (e) return e->err.c_str();
+    return g_ens_init_err.empty() ? "null ensemble" : g_ens_init_err.c_str();
+}
+
+int nb_ens_configure(nb_ens *e, int threads, int gmax)
+{
+    if (!e) return NB_EINVAL;
+    if ((threads != 256 && threads != 512 && threads != 1024) ||
+        (gmax != 1 && gmax != 2 && gmax != 4 && gmax != 8 && gmax != 16 && gmax != 32))
+        return efail(e, NB_EINVAL, "threads in {256, 512, 1024}, gmax a power of two <= 32");
+    e->nt = threads;
+    e->gmax = gmax;
+    return NB_OK;
+}
+
+int nb_ens_run(nb_ens *e, double t_end, int64_t max_launches, int64_t *launches_out,
+               int64_t *interactions_out)
+{
+    if (!e) return NB_EINVAL;
+    if (!std::isfinite(t_end) || t_end < 0.0 || t_end >= 0x1p22 || t_end * 0x1p40 != std::floor(t_end * 0x1p40))
+        return efail(e, NB_EINVAL, "t_end is not on the 2^-40 grid");
+    if (max_launches < 0) return efail(e, NB_EINVAL, "max_launches < 0");
+    const long long te = (long long)(t_end * 0x1p40);
+    if (te != e->t_end) {
+        // a new end time re-opens finished clusters
+        ECK(cudaMemsetAsync(e->d_done, 0, sizeof(int) * e->C, e->st));
+        e->t_end = te;
+    }
+    // capture one ensemble step (memset + persistent launch) into a graph
+    if (!e->graph || e->graph_nt != e->nt || e->graph_gmax != e->gmax || e->graph_tend != te) {
+        if (e->graph) cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
+        int rc0 = 0;
+        // the first launch of each configuration sets its shared-memory limit outside capture
+        EnsArgs probe = ens_args(e);
+        probe.C = 0;
+        ECK(cudaMemsetAsync(e->d_work, 0, sizeof(int), e->st));
+        if ((rc0 = launch_ens<kEnsStep>(e, probe))) return rc0;
+        ECK(cudaStreamSynchronize(e->st));
+        cudaGraph_t g;
+        ECK(cudaStreamBeginCapture(e->st, cudaStreamCaptureModeThreadLocal));
+        const long long l0 = e->launches;
+        const int rc = enqueue_ens_step(e);
+        e->launches = l0;
+        cudaError_t ce = cudaStreamEndCapture(e->st, &g);
+        if (rc) return rc;
+        if (ce != cudaSuccess) return efail(e, NB_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&e->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+            e->graph = nullptr;
+            return efail(e, NB_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+        }
+        e->graph_nt = e->nt;
+        e->graph_gmax = e->gmax;
+        e->graph_tend = te;
+    }
+    std::vector<int> done(e->C);
+    long long n = 0;
+    std::vector<long long> inter0(e->C), inter1(e->C);
+    ECK(cudaMemcpyAsync(inter0.data(), e->d_inter, sizeof(long long) * e->C, cudaMemcpyDeviceToHost, e->st));
+    while (n < max_launches) {
+        const long long k = std::min<long long>(32, max_launches - n);
+        for (long long q = 0; q < k; ++q) ECK(cudaGraphLaunch(e->graph, e->st));
+        n += k;
+        e->launches += k;
+        ECK(cudaMemcpyAsync(done.data(), e->d_done, sizeof(int) * e->C, cudaMemcpyDeviceToHost, e->st));
+        int rc = ens_sync(e);
+        if (rc) return rc;
+        bool all = true;
+        for (int c = 0; c < e->C && all; ++c) all = done[c] != 0;
+        if (all) break;
+    }
+    ECK(cudaMemcpyAsync(inter1.data(), e->d_inter, sizeof(long long) * e->C, cudaMemcpyDeviceToHost, e->st));
+    ECK(cudaStreamSynchronize(e->st));
+    long long it = 0;
+    for (int c = 0; c < e->C; ++c) it += inter1[c] - inter0[c];
+    if (launches_out) *launches_out = n;
+    if (interactions_out) *interactions_out = it;
+    return NB_OK;
+}
+
+int nb_ens_tune(nb_ens *e, int launches_per_candidate, int *threads_out, int *gmax_out,
+                double *ms_out)
+{
+    if (!e) return NB_EINVAL;
+    if (launches_per_candidate < 1) return efail(e, NB_EINVAL, "launches_per_candidate < 1");
+    const long long P = e->P, C = e->C;
+    int rc;
+    if (!e->d_backup && ((rc = ealloc(e, &e->d_backup, 12 * P + 2 * C)) ||
+                         (rc = ealloc(e, &e->d_tbak, P)) || (rc = ealloc(e, &e->d_lbak, P + C))))
+        return rc;
+    // snapshot: x, v, a, k, times, levels, per-cluster counters and flags
+    double *arrs[4] = {e->d_x, e->d_v, e->d_a, e->d_k};
+    auto save = [&](bool restore) -> int {
+        for (int q = 0; q < 4; ++q) {
+            double *b = e->d_backup + q * 3 * P;
+            ECK(cudaMemcpyAsync(restore ? arrs[q] : b, restore ? b : arrs[q], sizeof(double) * 3 * P,
+                                cudaMemcpyDeviceToDevice, e->st));
+        }
+        long long *cb = (long long *)(e->d_backup + 12 * P);
+        ECK(cudaMemcpyAsync(restore ? e->d_t : e->d_tbak, restore ? e->d_tbak : e->d_t,
+                            sizeof(long long) * P, cudaMemcpyDeviceToDevice, e->st));
+        ECK(cudaMemcpyAsync(restore ? e->d_lev : e->d_lbak, restore ? e->d_lbak : e->d_lev,
+                            sizeof(int) * P, cudaMemcpyDeviceToDevice, e->st));
+        ECK(cudaMemcpyAsync(restore ? e->d_done : e->d_lbak + P, restore ? e->d_lbak + P : e->d_done,
+                            sizeof(int) * C, cudaMemcpyDeviceToDevice, e->st));
+        ECK(cudaMemcpyAsync(restore ? e->d_steps : cb, restore ? cb : e->d_steps,
+                            sizeof(long long) * C, cudaMemcpyDeviceToDevice, e->st));
+        ECK(cudaMemcpyAsync(restore ? e->d_inter : cb + C, restore ? cb + C : e->d_inter,
+                            sizeof(long long) * C, cudaMemcpyDeviceToDevice, e->st));
+        return NB_OK;
+    };
+    if ((rc = save(false))) return rc;
+    cudaEvent_t e0, e1;
+    ECK(cudaEventCreate(&e0));
+    ECK(cudaEventCreate(&e1));
+    const int cand_nt[3] = {256, 512, 1024};
+    const int cand_g[6] = {1, 2, 4, 8, 16, 32};
+    float best = 1e30f;
+    int bnt = e->nt, bg = e->gmax;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 6; ++b) {
+            e->nt = cand_nt[a];
+            e->gmax = cand_g[b];
+            if ((rc = save(true))) return rc;
+            if ((rc = enqueue_ens_step(e))) return rc;  // warm-up (and shared-memory set-up)
+            ECK(cudaEventRecord(e0, e->st));
+            for (int q = 0; q < launches_per_candidate; ++q)
+                if ((rc = enqueue_ens_step(e))) return rc;
+            ECK(cudaEventRecord(e1, e->st));
+            if ((rc = ens_sync(e))) return rc;
+            float ms = 0.0f;
+            ECK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                bnt = e->nt;
+                bg = e->gmax;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if ((rc = save(true))) return rc;
+    ECK(cudaStreamSynchronize(e->st));
+    e->nt = bnt;
+    e->gmax = bg;
+    if (threads_out) *threads_out = bnt;
+    if (gmax_out) *gmax_out = bg;
+    if (ms_out) *ms_out = best / launches_per_candidate;
+    return NB_OK;
+}
+
+int nb_ens_step(nb_ens *e)
+{
+    if (!e) return NB_EINVAL;
+    int rc = enqueue_ens_step(e);
+    if (rc) return rc;
+    return ens_sync(e);
+}
+
+int nb_ens_force(nb_ens *e, double *acc, double *jerk, double *pot)
+{
+    if (!e) return NB_EINVAL;
+    const long long P = e->P;
+    EnsArgs a = ens_args(e);
+    a.out_acc = e->d_stage;
+    a.out_jerk = e->d_stage + 3 * P;
+    a.out_pot = e->d_stage + 6 * P;
+    ECK(cudaMemsetAsync(e->d_work, 0, sizeof(int), e->st));
+    int rc = launch_ens<kEnsForce>(e, a);
+    if (rc) return rc;
+    e->launches += 1;
+    if (acc) ECK(cudaMemcpyAsync(acc, a.out_acc, sizeof(double) * 3 * P, cudaMemcpyDeviceToHost, e->st));
+    if (jerk) ECK(cudaMemcpyAsync(jerk, a.out_jerk, sizeof(double) * 3 * P, cudaMemcpyDeviceToHost, e->st));
+    if (pot) ECK(cudaMemcpyAsync(pot, a.out_pot, sizeof(double) * P, cudaMemcpyDeviceToHost, e->st));
+    return ens_sync(e);
+}
+
+int nb_ens_energy(nb_ens *e, double *ekin, double *epot)
+{
+    if (!e) return NB_EINVAL;
+    double *d = e->d_stage;
+    k_ens_energy<256><<<std::max(1, std::min(e->C, 8 * e->sms)), 256, 0, e->st>>>(
+        ens_args(e), e->eps * e->eps, d, d + e->C);
+    e->launches += 1;
+    if (ekin) ECK(cudaMemcpyAsync(ekin, d, sizeof(double) * e->C, cudaMemcpyDeviceToHost, e->st));
+    if (epot) ECK(cudaMemcpyAsync(epot, d + e->C, sizeof(double) * e->C, cudaMemcpyDeviceToHost, e->st));
+    return ens_sync(e);
+}
+
+int nb_ens_get_state(nb_ens *e, double *x, double *v, double *a, double *k, int64_t *t,
+                     int32_t *level, int64_t *steps, int64_t *interactions)
+{
+    if (!e) return NB_EINVAL;
+    const long long P = e->P;
+    double *src[4] = {e->d_x, e->d_v, e->d_a, e->d_k};
+    double *dst[4] = {x, v, a, k};
+    for (int q = 0; q < 4; ++q) {
+        if (!dst[q]) continue;
+        k_soa_to_aos<<<grid_of(3 * P), 256, 0, e->st>>>(src[q], e->d_stage, P);
+        ECK(cudaMemcpyAsync(dst[q], e->d_stage, sizeof(double) * 3 * P, cudaMemcpyDeviceToHost, e->st));
+        ECK(cudaStreamSynchronize(e->st));
+    }
+    if (t) ECK(cudaMemcpyAsync(t, e->d_t, sizeof(long long) * P, cudaMemcpyDeviceToHost, e->st));
+    if (level) ECK(cudaMemcpyAsync(level, e->d_lev, sizeof(int) * P, cudaMemcpyDeviceToHost, e->st));
+    if (steps) ECK(cudaMemcpyAsync(steps, e->d_steps, sizeof(long long) * e->C, cudaMemcpyDeviceToHost, e->st));
+    if (interactions)
+        ECK(cudaMemcpyAsync(interactions, e->d_inter, sizeof(long long) * e->C, cudaMemcpyDeviceToHost, e->st));
+    return ens_sync(e);
+}
+
+int nb_ens_set_state(nb_ens *e, const double *x, const double *v, const double *a, const double *k,
+                     const int64_t *t, const int32_t *level)
+{
+    if (!e) return NB_EINVAL;
+    if (!x || !v || !a || !k || !t || !level) return efail(e, NB_EINVAL, "all arrays are required");
+    const long long P = e->P;
+    if (!finite_all(x, 3 * P) || !finite_all(v, 3 * P) || !finite_all(a, 3 * P) || !finite_all(k, 3 * P))
+        return efail(e, NB_EINVAL, "non-finite state");
+    for (long long i = 0; i < P; ++i) {
+        if (level[i] < e->o.level_min || level[i] > kTickBits) return efail(e, NB_EINVAL, "bad level");
+        if (t[i] < 0 || t[i] % (1LL << (kTickBits - level[i])) != 0)
+            return efail(e, NB_EINVAL, "time not a multiple of its step");
+    }
+    const double *src[4] = {x, v, a, k};
+    double *dst[4] = {e->d_x, e->d_v, e->d_a, e->d_k};
+    for (int q = 0; q < 4; ++q) {
+        ECK(cudaMemcpyAsync(e->d_stage, src[q], sizeof(double) * 3 * P, cudaMemcpyHostToDevice, e->st));
+        k_aos_to_soa<<<grid_of(3 * P), 256, 0, e->st>>>(e->d_stage, dst[q], P);
+        ECK(cudaStreamSynchronize(e->st));
+    }
+    ECK(cudaMemcpyAsync(e->d_t, t, sizeof(long long) * P, cudaMemcpyHostToDevice, e->st));
+    ECK(cudaMemcpyAsync(e->d_lev, level, sizeof(int) * P, cudaMemcpyHostToDevice, e->st));
+    ECK(cudaMemsetAsync(e->d_done, 0, sizeof(int) * e->C, e->st));
+    return ens_sync(e);
+}
+
+}  // extern "C"

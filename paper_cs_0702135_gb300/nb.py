@@ -76,6 +76,18 @@ SIGNATURES = [
     ("nb_force_vjp", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("nb_traj_forward", ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64]),
     ("nb_traj_backward", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    ("nb_ens_init", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, _vp, _vp, _vp, _vp,
+                                    ctypes.c_double, ctypes.POINTER(nb_opts)]),
+    ("nb_ens_configure", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    ("nb_ens_tune", ctypes.c_int, [_vp, ctypes.c_int, _c_ip, _c_ip, _c_dp]),
+    ("nb_ens_run", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int64, _c_lp, _c_lp]),
+    ("nb_ens_step", ctypes.c_int, [_vp]),
+    ("nb_ens_force", ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    ("nb_ens_energy", ctypes.c_int, [_vp, _vp, _vp]),
+    ("nb_ens_get_state", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("nb_ens_set_state", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("nb_ens_last_error", ctypes.c_char_p, [_vp]),
+    ("nb_ens_free", None, [_vp]),
     ("nb_set_profiling", ctypes.c_int, [_vp, ctypes.c_int]),
     ("nb_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(nb_stats), ctypes.c_int]),
     ("nb_force_few_noalloc", ctypes.c_int, [ctypes.c_int64, _vp, _vp, _vp, ctypes.c_double, _vp,
@@ -284,6 +296,128 @@ def nb_force_few_noalloc(n, d_m, d_x, d_v, eps, d_active_idx, n_active, d_acc=No
     if rc != NB_OK:
         raise NbError(rc, "nb_force_few_noalloc rejected n=%d n_active=%d eps=%r (limit %d)"
                       % (n, n_active, eps, NB_NOALLOC_MAX_ACTIVE))
+
+
+def _echeck(ens, rc):
+    if rc != NB_OK:
+        raise NbError(rc, lib().nb_ens_last_error(ens).decode())
+
+
+def nb_ens_init(offsets, m, x, v, eps, opts=None):
+    """Ensemble of clusters offsets[c] .. offsets[c+1]-1; returns a handle."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    C = off.shape[0] - 1
+    P = int(off[-1])
+    m = _f64(m)
+    x = _f64(x, (P, 3))
+    v = _f64(v, (P, 3))
+    e = ctypes.c_void_p()
+    rc = lib().nb_ens_init(ctypes.byref(e), C, _ptr(off), _ptr(m), _ptr(x), _ptr(v), float(eps),
+                           None if opts is None else ctypes.byref(opts))
+    if rc != NB_OK:
+        raise NbError(rc, lib().nb_ens_last_error(None).decode())
+    return e
+
+
+def nb_ens_configure(ens, threads, gmax):
+    _echeck(ens, lib().nb_ens_configure(ens, int(threads), int(gmax)))
+
+
+def nb_ens_tune(ens, launches_per_candidate=10):
+    th, g, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _echeck(ens, lib().nb_ens_tune(ens, int(launches_per_candidate), ctypes.byref(th),
+                                   ctypes.byref(g), ctypes.byref(ms)))
+    return th.value, g.value, ms.value
+
+
+def nb_ens_run(ens, t_end, max_launches=1 << 62):
+    n, it = ctypes.c_int64(), ctypes.c_int64()
+    _echeck(ens, lib().nb_ens_run(ens, float(t_end), int(max_launches), ctypes.byref(n), ctypes.byref(it)))
+    return n.value, it.value
+
+
+def nb_ens_step(ens):
+    _echeck(ens, lib().nb_ens_step(ens))
+
+
+def nb_ens_force(ens, P):
+    acc, jerk, pot = np.empty((P, 3)), np.empty((P, 3)), np.empty(P)
+    _echeck(ens, lib().nb_ens_force(ens, _ptr(acc), _ptr(jerk), _ptr(pot)))
+    return acc, jerk, pot
+
+
+def nb_ens_energy(ens, C):
+    ek, ep = np.empty(C), np.empty(C)
+    _echeck(ens, lib().nb_ens_energy(ens, _ptr(ek), _ptr(ep)))
+    return ek, ep
+
+
+def nb_ens_get_state(ens, C, P):
+    st = {"x": np.empty((P, 3)), "v": np.empty((P, 3)), "a": np.empty((P, 3)), "k": np.empty((P, 3)),
+          "t": np.empty(P, dtype=np.int64), "level": np.empty(P, dtype=np.int32),
+          "steps": np.empty(C, dtype=np.int64), "interactions": np.empty(C, dtype=np.int64)}
+    _echeck(ens, lib().nb_ens_get_state(ens, *[_ptr(st[k]) for k in
+                                              ("x", "v", "a", "k", "t", "level", "steps", "interactions")]))
+    return st
+
+
+def nb_ens_set_state(ens, x, v, a, k, t, level):
+    arrs = [_f64(x), _f64(v), _f64(a), _f64(k), np.ascontiguousarray(t, dtype=np.int64),
+            np.ascontiguousarray(level, dtype=np.int32)]
+    _echeck(ens, lib().nb_ens_set_state(ens, *[_ptr(q) for q in arrs]))
+
+
+def nb_ens_last_error(ens) -> str:
+    return lib().nb_ens_last_error(ens).decode()
+
+
+def nb_ens_free(ens):
+    if ens is not None and ens.value:
+        lib().nb_ens_free(ens)
+        ens.value = None
+
+
+class Ensemble:
+    """Owns one nb_ens; each method calls the entry point of the same name."""
+
+    def __init__(self, offsets, m, x, v, eps, **opts):
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        self.C = self.offsets.shape[0] - 1
+        self.P = int(self.offsets[-1])
+        self.ens = nb_ens_init(self.offsets, m, x, v, eps, nb_default_opts(**opts) if opts else None)
+
+    def nb_ens_configure(self, threads, gmax):
+        return nb_ens_configure(self.ens, threads, gmax)
+
+    def nb_ens_tune(self, launches_per_candidate=10):
+        return nb_ens_tune(self.ens, launches_per_candidate)
+
+    def nb_ens_run(self, t_end, max_launches=1 << 62):
+        return nb_ens_run(self.ens, t_end, max_launches)
+
+    def nb_ens_step(self):
+        return nb_ens_step(self.ens)
+
+    def nb_ens_force(self):
+        return nb_ens_force(self.ens, self.P)
+
+    def nb_ens_energy(self):
+        return nb_ens_energy(self.ens, self.C)
+
+    def nb_ens_get_state(self):
+        return nb_ens_get_state(self.ens, self.C, self.P)
+
+    def nb_ens_set_state(self, x, v, a, k, t, level):
+        return nb_ens_set_state(self.ens, x, v, a, k, t, level)
+
+    def nb_ens_free(self):
+        nb_ens_free(self.ens)
+
+    def __del__(self):
+        try:
+            self.nb_ens_free()
+        except Exception:
+            pass
 
 
 def nb_num_particles(ctx) -> int:

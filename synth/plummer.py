@@ -33,7 +33,7 @@ from . import rng
 
 # Independent streams, one per kind of draw.
 _S_RADIUS, _S_POSDIR, _S_SPEED, _S_VELDIR, _S_ACTIVE = 1, 2, 3, 4, 5
-_S_ENS_N, _S_ENS_IMF, _S_ENS_Q = 11, 12, 13
+_S_ENS_N, _S_ENS_IMF, _S_ENS_Q, _S_PAIRS = 11, 12, 13, 14
 
 _ATTEMPTS = 1 << 16          # counter space reserved per particle for redraws
 LENGTH_UNIT = 3.0 * math.pi / 16.0
@@ -103,8 +103,20 @@ def unsoftened_potential_energy(m: np.ndarray, x: np.ndarray, chunk: int = 1024)
     return 0.5 * w
 
 
+def sampled_potential_energy(m: np.ndarray, x: np.ndarray, seed: int, pairs: int) -> float:
+    """W estimated from `pairs` uniformly drawn pairs i != j (seeded):
+    W ~ -(n (n - 1) / 2) * mean(m_i m_j / |x_i - x_j|); relative error ~ pairs^-1/2."""
+    n = m.shape[0]
+    c = np.arange(pairs, dtype=np.int64)
+    i = (rng.u64(seed, _S_PAIRS, 2 * c) % np.uint64(n)).astype(np.int64)
+    j = (rng.u64(seed, _S_PAIRS, 2 * c + 1) % np.uint64(n - 1)).astype(np.int64)
+    j = j + (j >= i)
+    r = np.linalg.norm(x[i] - x[j], axis=1)
+    return -0.5 * n * (n - 1) * float(np.mean(m[i] * m[j] / r))
+
+
 def plummer(n: int, seed: int, r_cut: float = 22.8, masses: np.ndarray | None = None,
-            virial_ratio: float = 0.5, exact_virial_max: int = 16384):
+            virial_ratio: float = 0.5, exact_virial_max: int = 16384, sample_pairs: int = 0):
     """Plummer sphere of ``n`` bodies; returns (m[n], x[n,3], v[n,3]) in float64.
 
     ``masses`` (normalised to total 1) replaces the equal masses 1/n.  With
@@ -128,7 +140,10 @@ def plummer(n: int, seed: int, r_cut: float = 22.8, masses: np.ndarray | None = 
     x -= (m[:, None] * x).sum(axis=0) / m.sum()
     v -= (m[:, None] * v).sum(axis=0) / m.sum()
     if n >= 2 and (n <= exact_virial_max or masses is not None or virial_ratio != 0.5):
-        w = unsoftened_potential_energy(m, x)
+        if n > exact_virial_max and sample_pairs > 0:
+            w = sampled_potential_energy(m, x, seed, sample_pairs)
+        else:
+            w = unsoftened_potential_energy(m, x)
         t = kinetic_energy(m, v)
         x *= w / -0.5
         v *= math.sqrt(0.5 * virial_ratio / t)
@@ -157,7 +172,8 @@ def salpeter_masses(n: int, seed: int, stream_offset: int = 0, slope: float = -2
 def ensemble(n_clusters: int, seed: int, n_lo: int = 32, n_hi: int = 4096,
              q_lo: float = 0.3, q_hi: float = 0.7):
     """Independent clusters: N log-uniform in [n_lo, n_hi], Salpeter masses,
-    virial ratio uniform in [q_lo, q_hi].  Returns a list of (m, x, v)."""
+    virial ratio uniform in [q_lo, q_hi].  Returns a list of (m, x, v).  Clusters
+    above 1024 bodies are scaled with W estimated from 2e5 sampled pairs."""
     c = np.arange(n_clusters, dtype=np.int64)
     un = rng.uniform(seed, _S_ENS_N, c)
     sizes = np.floor(np.exp(math.log(n_lo) + un * (math.log(n_hi + 1) - math.log(n_lo)))).astype(np.int64)
@@ -168,5 +184,6 @@ def ensemble(n_clusters: int, seed: int, n_lo: int = 32, n_hi: int = 4096,
         nc = int(sizes[ci])
         sub = (seed * 1000003 + ci) & 0x7FFFFFFFFFFFFFFF
         m = salpeter_masses(nc, sub)
-        out.append(plummer(nc, sub, masses=m, virial_ratio=float(q_lo + uq[ci] * (q_hi - q_lo))))
+        out.append(plummer(nc, sub, masses=m, virial_ratio=float(q_lo + uq[ci] * (q_hi - q_lo)),
+                           exact_virial_max=1024, sample_pairs=200000))
     return out
