@@ -59,7 +59,7 @@ def parse_args():
     p.add_argument("--impl", default="mine", choices=["mine", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT)
     p.add_argument("--no-extras", action="store_true", help="skip ladder, FP64 arm, e2e, CPU baseline")
-    p.add_argument("--workload", default="full_active_step", choices=["full_active_step", "blockstep", "adjoint", "ensemble"],
+    p.add_argument("--workload", default="full_active_step", choices=["full_active_step", "blockstep", "adjoint", "ensemble", "replay"],
                    help="blockstep: individual block steps of a Plummer run (Section 2 step loop)")
     p.add_argument("--t-end", type=float, default=0.25, help="blockstep: end time (multiple of dt_max)")
     p.add_argument("--eps", type=float, default=None, help="blockstep: softening (default 1/256)")
@@ -67,6 +67,7 @@ def parse_args():
     p.add_argument("--precision", default="ds", choices=["ds", "fp64", "both"])
     p.add_argument("--fd-coords", type=int, default=32, help="adjoint: coordinates checked by FP64 FD")
     p.add_argument("--clusters", type=int, default=4096, help="ensemble: number of clusters")
+    p.add_argument("--n-max", type=int, default=524288, help="replay: largest N of the ladder")
     p.add_argument("--baseline-sample", type=int, default=32,
                    help="ensemble: clusters timed one by one through the single-system path")
     p.add_argument("--oracle-n", type=int, default=1024, help="adjoint: size of the CPU FP64 comparison")
@@ -686,6 +687,52 @@ def run_ensemble(args):
     print(json.dumps(out), flush=True)
 
 
+# Wall-clock seconds for 0.25 N-body time units (t = 0.25 -> 0.5), equal-mass
+# Plummer spheres, eps = 1/256, dt_max = 0.125: the paper's Tab:Results
+# (GRAPE-6Af, GeForce 8800GTX through Cg/OpenGL, Quadro FX1400, one Xeon core).
+PAPER_TAB_RESULTS = {
+    256: (0.07098, 2.708, 3.423, 0.1325), 512: (0.1410, 8.777, 10.59, 0.5941),
+    1024: (0.3327, 17.46, 20.20, 2.584), 2048: (0.7652, 45.27, 54.16, 10.59),
+    4096: (1.991, 128.3, 157.8, 50.40), 8192: (5.552, 342.7, 617.3, 224.7),
+    16384: (16.32, 924.4, 3398, 994.0), 32768: (51.68, 1907, 13180, 4328),
+    65536: (178.2, 3973, 40560, 19290), 131072: (None, 8844, None, None),
+    262144: (None, 22330, None, None), 524288: (None, 63960, None, None)}
+
+
+def run_replay(args):
+    """The paper's timing experiment (Section 4, Tab:Results) on this GPU: for
+    each N, an equal-mass Plummer sphere (seed 7), eps = 1/256, dt_max = 0.125,
+    eta = 0.01, integrated from t = 0 to 0.5 with block steps; the wall clock is
+    measured over the last quarter, t = 0.25 -> 0.5, as in the paper."""
+    import torch
+    import paper_cs_0702135_gb300 as nb
+    from synth import plummer
+    torch.cuda.set_device(0)
+    rows = []
+    n = 256
+    while n <= args.n_max:
+        m, x, v = plummer(n, 7)
+        ctx = nb.Context(m, x, v, 1.0 / 256)
+        e0 = sum(ctx.nb_energy())
+        ctx.nb_run(0.25)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps, inter = ctx.nb_run(0.5)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e1 = sum(ctx.nb_energy())
+        ctx.nb_free()
+        paper = PAPER_TAB_RESULTS.get(n, (None,) * 4)
+        rows.append({"N": n, "seconds_0.25_to_0.5": el, "steps": steps, "interactions": inter,
+                     "interactions_per_s": inter / el, "mean_block": inter / max(1, steps) / (n - 1),
+                     "energy_rel_err_0_to_0.5": abs(e1 - e0) / abs(e0),
+                     "paper_seconds": {"grape6af": paper[0], "8800gtx": paper[1], "fx1400": paper[2],
+                                       "xeon": paper[3]},
+                     "speedup_vs_8800gtx": (paper[1] / el) if paper[1] else None})
+        n *= 2
+    print(json.dumps({"workload": "paper_tab_results_replay", "eps": 1.0 / 256, "rows": rows}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -696,6 +743,8 @@ def main():
         run_adjoint(args)
     elif args.workload == "ensemble":
         run_ensemble(args)
+    elif args.workload == "replay":
+        run_replay(args)
     else:
         run_mine(args)
 
