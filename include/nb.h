@@ -230,8 +230,10 @@ int nb_traj_backward(nb_ctx *ctx, const double *xbar_T, const double *vbar_T, do
  * offsets[c] .. offsets[c+1]-1 of the concatenated arrays m[P], x[P][3],
  * v[P][3] (host, FP64; 1 <= cluster size <= 4096; P = offsets[n_clusters]).
  * Precision is NB_DS; opts.level_fixed must be 0.  One ensemble step is one
- * GPU launch in which every unfinished cluster takes its next block step
- * (schedule, predict, force, correct for that cluster in one CTA).
+ * pair of GPU launches in which every unfinished cluster takes its next block
+ * step: one CTA per cluster schedules, predicts and lists the block, then
+ * work items of up to `threads` block particles (any CTA) sum the force and
+ * correct.
  */
 typedef struct nb_ens nb_ens;
 
@@ -241,8 +243,9 @@ typedef struct nb_ens nb_ens;
 int nb_ens_init(nb_ens **ens, int32_t n_clusters, const int64_t *offsets, const double *m,
                 const double *x, const double *v, double eps, const nb_opts *opts);
 
-/* Launch configuration: threads per CTA (256, 512 or 1024) and the largest
- * number of lanes that share one active particle's j loop (1, 2, ..., 32). */
+/* Launch configuration of the force launch: threads per CTA (128, 256 or
+ * 512; also the active particles per work item) and the largest number of
+ * lanes that share one active particle's j loop (1, 2, ..., 32). */
 int nb_ens_configure(nb_ens *ens, int threads, int gmax);
 
 /* Autotuner: times `launches_per_candidate` ensemble steps for every

@@ -1,23 +1,25 @@
-// k_ensemble.cu -- many independent clusters advanced together: one launch per
+// k_ensemble.cu -- many independent clusters advanced together: every
 // ensemble block step advances every unfinished cluster by its own next block
-// step (Section 2 step loop: select the block, predict, force, correct).
-//
-// A CTA owns a whole cluster for that step, so nothing waits across CTAs:
-//   1. block time t_next = min over the cluster of t_i + dt_i (CTA reduction);
-//   2. every particle predicted to t_next (FP64, same arithmetic as the
-//      single-system predictor) into double-single j records in shared memory
-//      (a 4096-particle cluster takes 192 KiB), and the block compacted in
-//      ascending order (ballot + prefix sums);
-//   3. force on the block: g consecutive lanes share one active particle and
-//      split its j loop (g = the largest power of two <= threads / n_active,
-//      capped at gmax), FP32 pair arithmetic on double-single positions with
-//      TwoSum-promoted partials, a shuffle reduction inside the lane group;
-//   4. the group's first lane corrects its particle (FP64 corrector and Aarseth
-//      step, same arithmetic as the single-system corrector).  The force reads
-//      only shared-memory records, so correcting while other groups still sum
-//      is safe.
-// CTAs take clusters from a work counter in decreasing size (largest first);
-// each cluster is computed by one CTA, so results do not depend on which.
+// step (Section 2 step loop: select the block, predict, force, correct), in two
+// launches replayed from one CUDA graph:
+//   A. a CTA per cluster (taken largest first from a work counter): block time
+//      t_next = min over the cluster of t_i + dt_i, every particle predicted to
+//      t_next (FP64, the single-system predictor's arithmetic) into global
+//      double-single j records, the block compacted in ascending order (ballot
+//      + prefix sums), and one work item per chunk of up to `threads` active
+//      particles appended to a queue;
+//   B. persistent CTAs take queue items: the cluster's j records stream through
+//      shared-memory tiles, g consecutive lanes share one active particle and
+//      split its j loop when the chunk is small (g = the largest power of two
+//      with g * chunk <= threads, capped at gmax), FP32 pair arithmetic on
+//      double-single positions with TwoSum-promoted partials and a shuffle
+//      reduction in the lane group; the group's first lane corrects its
+//      particle (FP64 corrector and Aarseth step, the single-system
+//      corrector's arithmetic).  The force reads only the j records, so
+//      correcting while other items still sum is safe.
+// A block of thousands of particles in one cluster is thus spread over many
+// SMs.  Every item is computed by one CTA in a fixed order, so results do not
+// depend on which CTA takes it.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -34,7 +36,6 @@ namespace nbk {
 namespace {
 
 constexpr int kEnsMaxN = 4096;       // largest cluster
-constexpr int kPromote = 64;         // j per FP32 partial before TwoSum promotion
 constexpr double kTickD = 0x1p-40;
 
 struct EnsArgs {
@@ -47,7 +48,15 @@ struct EnsArgs {
     int level_min;
     long long t_end;
     int gmax;                 // largest lane group per active particle
-    int *work;                // work counter (zeroed before each launch)
+    int chunk;                // active particles per work item (= launch B threads)
+    int *work;                // launch A: cluster counter; launch B: item counter
+    int *work_b;
+    int *qlen;                // queue length (items appended by launch A)
+    int *qc, *qk;             // queue: cluster and chunk of each item
+    float4 *jph, *jpl, *jv;   // [P] predicted double-single records
+    int *act;                 // [P] active particles of each cluster (local indices)
+    int *na;                  // [C] block sizes
+    long long *tnext;         // [C] block times
     int *done;                // [C]
     long long *steps;         // [C]
     long long *inter;         // [C] sum of n_active (n - 1)
@@ -169,60 +178,18 @@ struct MinLL {
     __device__ long long operator()(long long a, long long b) const { return a < b ? a : b; }
 };
 
-// Force on the listed particles of one cluster from its shared-memory records;
-// the lane group's first lane receives the double-precision sums in res[7].
-// Returns false for lanes that hold no result (or when `s` is out of range).
-__device__ __forceinline__ void group_force(const float4 *s_ph, const float4 *s_pl,
-                                            const float4 *s_v, int n, int i, int g, int lig,
-                                            float eps2, double res[7])
-{
-    const float4 ip = s_ph[i], il = s_pl[i], iv = s_v[i];
-    float hi[7] = {0, 0, 0, 0, 0, 0, 0}, lo[7] = {0, 0, 0, 0, 0, 0, 0};
-    float ta[3] = {0, 0, 0}, tk[3] = {0, 0, 0}, tp = 0.0f;
-    int cnt = 0;
-    for (int j = lig; j < n; j += g) {
-        pair(s_ph[j], s_pl[j], s_v[j], ip, il, iv, eps2, j == i, ta, tk, tp);
-        if (++cnt == kPromote) {
-            const float t7[7] = {ta[0], ta[1], ta[2], tk[0], tk[1], tk[2], tp};
-#pragma unroll
-            for (int c = 0; c < 7; ++c) two_sum_acc(hi[c], lo[c], t7[c]);
-            ta[0] = ta[1] = ta[2] = tk[0] = tk[1] = tk[2] = tp = 0.0f;
-            cnt = 0;
-        }
-    }
-    {
-        const float t7[7] = {ta[0], ta[1], ta[2], tk[0], tk[1], tk[2], tp};
-#pragma unroll
-        for (int c = 0; c < 7; ++c) two_sum_acc(hi[c], lo[c], t7[c]);
-    }
-    // reduce inside the lane group (g consecutive lanes of one warp)
-    for (int o = 1; o < g; o <<= 1) {
-#pragma unroll
-        for (int c = 0; c < 7; ++c) {
-            const float h2 = __shfl_xor_sync(0xffffffffu, hi[c], o);
-            const float l2 = __shfl_xor_sync(0xffffffffu, lo[c], o);
-            ds_add(hi[c], lo[c], h2, l2);
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 7; ++c) res[c] = (double)hi[c] + (double)lo[c];
-}
-
 enum EnsMode { kEnsStep = 0, kEnsForce = 1, kEnsInit = 2 };
 
+// Launch A: schedule, predict, compact, enqueue.
 template <int NT, int MODE>
-__global__ void __launch_bounds__(NT) k_ens(EnsArgs ea)
+__global__ void __launch_bounds__(NT) k_ens_a(EnsArgs ea)
 {
-    extern __shared__ float4 sm[];
-    float4 *s_ph = sm, *s_pl = sm + kEnsMaxN, *s_v = sm + 2 * kEnsMaxN;
-    int *s_act = (int *)(sm + 3 * kEnsMaxN);
     __shared__ long long s_red[NT / 32];
     __shared__ int s_wtot[NT / 32];
     __shared__ int s_cluster;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const State &S = ea.s;
-    const int P = S.n;
-
+    const long long P = S.n;
     for (;;) {
         if (tid == 0) s_cluster = atomicAdd(ea.work, 1);
         __syncthreads();
@@ -233,8 +200,6 @@ __global__ void __launch_bounds__(NT) k_ens(EnsArgs ea)
         const long long o = ea.off[c];
         const int n = (int)(ea.off[c + 1] - o);
         if (MODE == kEnsStep && ea.done[c]) continue;
-
-        // 1. block time
         long long tn = 0;
         if (MODE == kEnsStep) {
             long long mn = LLONG_MAX;
@@ -246,7 +211,6 @@ __global__ void __launch_bounds__(NT) k_ens(EnsArgs ea)
                 continue;
             }
         }
-        // 2. predict into shared memory, compact the block
         int running = 0;
         for (int base = 0; base < n; base += NT) {
             const int i = base + tid;
@@ -257,18 +221,18 @@ __global__ void __launch_bounds__(NT) k_ens(EnsArgs ea)
                 double xp[3], vp[3];
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc)
-                    predict1(S.x[cc * (long long)P + gi], S.v[cc * (long long)P + gi],
-                             S.a[cc * (long long)P + gi], S.k[cc * (long long)P + gi], dt, xp[cc], vp[cc]);
+                    predict1(S.x[cc * P + gi], S.v[cc * P + gi], S.a[cc * P + gi], S.k[cc * P + gi],
+                             dt, xp[cc], vp[cc]);
                 float hi[3], lo[3];
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) {
                     hi[cc] = __double2float_rn(xp[cc]);
                     lo[cc] = __double2float_rn(__dsub_rn(xp[cc], (double)hi[cc]));
                 }
-                s_ph[i] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(S.m[gi]));
-                s_pl[i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
-                s_v[i] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
-                                     __double2float_rn(vp[2]), 0.0f);
+                ea.jph[gi] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(S.m[gi]));
+                ea.jpl[gi] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+                ea.jv[gi] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
+                                        __double2float_rn(vp[2]), 0.0f);
                 f = MODE == kEnsStep ? (S.t[gi] + (1LL << (kTickBits - S.lev[gi])) == tn) : true;
             }
             const unsigned bal = __ballot_sync(0xffffffffu, f);
@@ -279,96 +243,156 @@ __global__ void __launch_bounds__(NT) k_ens(EnsArgs ea)
                 woff += w < warp ? s_wtot[w] : 0;
                 tot += s_wtot[w];
             }
-            if (f) s_act[running + woff + __popc(bal & ((1u << lane) - 1u))] = i;
+            if (f) ea.act[o + running + woff + __popc(bal & ((1u << lane) - 1u))] = i;
             running += tot;
             __syncthreads();
         }
-        const int na = running;
-        if (MODE == kEnsStep && tid == 0) {
-            ea.steps[c] += 1;
-            ea.inter[c] += (long long)na * (n - 1);
+        if (tid == 0) {
+            const int na = running;
+            ea.na[c] = na;
+            ea.tnext[c] = tn;
+            if (MODE == kEnsStep) {
+                ea.steps[c] += 1;
+                ea.inter[c] += (long long)na * (n - 1);
+            }
+            const int items = (na + ea.chunk - 1) / ea.chunk;
+            const int base = atomicAdd(ea.qlen, items);
+            for (int k = 0; k < items; ++k) {
+                ea.qc[base + k] = c;
+                ea.qk[base + k] = k;
+            }
         }
-        // 3./4. force on the block and correction (or output)
-        int g = 1;
-        while (g < ea.gmax && g * 2 * na <= NT) g <<= 1;
-        const int groups = NT / g;
-        const int grp = tid / g, lig = tid % g;
-        const int iters = (na + groups - 1) / groups;  // the same for every lane (shuffles below)
-        for (int it = 0; it < iters; ++it) {
-            const int sidx = grp + it * groups;
-            const bool valid = sidx < na;
-            const int i = s_act[valid ? sidx : 0];
-            double res[7];
-            group_force(s_ph, s_pl, s_v, n, i, g, lig, ea.eps2, res);
-            if (!valid || lig != 0) continue;
-            const long long gi = o + i;
-            if (MODE == kEnsForce) {
-#pragma unroll
-                for (int cc = 0; cc < 3; ++cc) {
-                    ea.out_acc[3 * gi + cc] = res[cc];
-                    ea.out_jerk[3 * gi + cc] = res[3 + cc];
-                }
-                ea.out_pot[gi] = res[6];
-                continue;
-            }
-            if (MODE == kEnsInit) {
-#pragma unroll
-                for (int cc = 0; cc < 3; ++cc) {
-                    S.a[cc * (long long)P + gi] = res[cc];
-                    S.k[cc * (long long)P + gi] = res[3 + cc];
-                }
-                S.t[gi] = 0;
-                const double nk = norm3(res[3], res[4], res[5]);
-                const double dt0 = nk == 0.0 ? (double)INFINITY
-                                             : __ddiv_rn(__dmul_rn(ea.eta_init, norm3(res[0], res[1], res[2])), nk);
-                int lv;
-                if (!level_of(dt0, ea.level_min, lv)) {
-                    atomicCAS(ea.err, 0, NB_ESTEP);
-                    lv = kTickBits;
-                }
-                S.lev[gi] = lv;
-                continue;
-            }
-            // corrector and new step (same arithmetic as the single-system corrector)
-            const double dt = ticks_to_time(tn - S.t[gi]);
-            double a2[3], a3[3], ap[3] = {res[0], res[1], res[2]}, kp[3] = {res[3], res[4], res[5]};
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                const long long e = cc * (long long)P + gi;
-                const double x = S.x[e], v = S.v[e], a = S.a[e], k = S.k[e];
-                double xp, vp;
-                predict1(x, v, a, k, dt, xp, vp);
-                const double d = __dsub_rn(a, ap[cc]);
-                a3[cc] = __dadd_rn(__dmul_rn(2.0, d), __dmul_rn(__dadd_rn(k, kp[cc]), dt));
-                a2[cc] = __dsub_rn(__dmul_rn(-3.0, d), __dmul_rn(__dadd_rn(__dmul_rn(2.0, k), kp[cc]), dt));
-                S.x[e] = __dadd_rn(xp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[cc], 12.0), __ddiv_rn(a3[cc], 20.0)),
-                                                 __dmul_rn(dt, dt)));
-                S.v[e] = __dadd_rn(vp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[cc], 3.0), __ddiv_rn(a3[cc], 4.0)), dt));
-                S.a[e] = ap[cc];
-                S.k[e] = kp[cc];
-            }
-            S.t[gi] = tn;
-            const double dt2 = __dmul_rn(dt, dt), dt3 = __dmul_rn(dt2, dt);
-            double s1[3], cr[3];
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                const double s0 = __ddiv_rn(__dmul_rn(2.0, a2[cc]), dt2);
-                cr[cc] = __ddiv_rn(__dmul_rn(6.0, a3[cc]), dt3);
-                s1[cc] = __dadd_rn(s0, __dmul_rn(cr[cc], dt));
-            }
-            const double nav = norm3(ap[0], ap[1], ap[2]), nk = norm3(kp[0], kp[1], kp[2]);
-            const double ns = norm3(s1[0], s1[1], s1[2]), nc = norm3(cr[0], cr[1], cr[2]);
-            const double num = __dadd_rn(__dmul_rn(nav, ns), __dmul_rn(nk, nk));
-            const double den = __dadd_rn(__dmul_rn(nk, nc), __dmul_rn(ns, ns));
-            const double dt_raw = den == 0.0 ? (double)INFINITY : __dsqrt_rn(__ddiv_rn(__dmul_rn(ea.eta, num), den));
-            int kq;
-            if (!level_of(dt_raw, ea.level_min, kq)) {
-                atomicCAS(ea.err, 0, NB_ESTEP);
-                kq = kTickBits;
-            }
-            S.lev[gi] = next_level(S.lev[gi], kq, tn, ea.level_min);
-        }
+    }
+}
+
+// Launch B: force on one chunk of a cluster's block, then correction (or the
+// start-up levels, or plain output).
+template <int NT, int MODE>
+__global__ void __launch_bounds__(NT) k_ens_b(EnsArgs ea)
+{
+    __shared__ float4 s_ph[NT], s_pl[NT], s_v[NT];
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    const State &S = ea.s;
+    const long long P = S.n;
+    const int qlen = *ea.qlen;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(ea.work_b, 1);
         __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= qlen) break;
+        const int c = ea.qc[it], k = ea.qk[it];
+        const long long o = ea.off[c];
+        const int n = (int)(ea.off[c + 1] - o);
+        const int s0 = k * ea.chunk;
+        const int cnt = min(ea.chunk, ea.na[c] - s0);
+        int g = 1;
+        while (g < ea.gmax && g * 2 * cnt <= NT) g <<= 1;
+        const int grp = tid / g, lig = tid % g;
+        const bool valid = grp < cnt;
+        const int i = ea.act[o + s0 + (valid ? grp : 0)];
+        const float4 ip = ea.jph[o + i], il = ea.jpl[o + i], iv = ea.jv[o + i];
+        float hi[7] = {0, 0, 0, 0, 0, 0, 0}, lo[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int jt = 0; jt < n; jt += NT) {
+            __syncthreads();
+            const int j = jt + tid;
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            s_ph[tid] = j < n ? ea.jph[o + j] : z;
+            s_pl[tid] = j < n ? ea.jpl[o + j] : z;
+            s_v[tid] = j < n ? ea.jv[o + j] : z;
+            __syncthreads();
+            const int jc = min(NT, n - jt);
+            // FP32 partials over at most 64 pairs per lane, then TwoSum promotion
+            for (int jb = 0; jb < jc; jb += 64 * g) {
+                const int je = min(jc, jb + 64 * g);
+                float ta[3] = {0, 0, 0}, tk[3] = {0, 0, 0}, tp = 0.0f;
+                for (int jj = jb + lig; jj < je; jj += g)
+                    pair(s_ph[jj], s_pl[jj], s_v[jj], ip, il, iv, ea.eps2, jt + jj == i, ta, tk, tp);
+                const float t7[7] = {ta[0], ta[1], ta[2], tk[0], tk[1], tk[2], tp};
+#pragma unroll
+                for (int cc = 0; cc < 7; ++cc) two_sum_acc(hi[cc], lo[cc], t7[cc]);
+            }
+        }
+        for (int sh = 1; sh < g; sh <<= 1) {
+#pragma unroll
+            for (int cc = 0; cc < 7; ++cc) {
+                const float h2 = __shfl_xor_sync(0xffffffffu, hi[cc], sh);
+                const float l2 = __shfl_xor_sync(0xffffffffu, lo[cc], sh);
+                ds_add(hi[cc], lo[cc], h2, l2);
+            }
+        }
+        if (!valid || lig != 0) continue;
+        double res[7];
+#pragma unroll
+        for (int cc = 0; cc < 7; ++cc) res[cc] = (double)hi[cc] + (double)lo[cc];
+        const long long gi = o + i;
+        if (MODE == kEnsForce) {
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                ea.out_acc[3 * gi + cc] = res[cc];
+                ea.out_jerk[3 * gi + cc] = res[3 + cc];
+            }
+            ea.out_pot[gi] = res[6];
+            continue;
+        }
+        if (MODE == kEnsInit) {
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                S.a[cc * P + gi] = res[cc];
+                S.k[cc * P + gi] = res[3 + cc];
+            }
+            S.t[gi] = 0;
+            const double nk = norm3(res[3], res[4], res[5]);
+            const double dt0 = nk == 0.0 ? (double)INFINITY
+                                         : __ddiv_rn(__dmul_rn(ea.eta_init, norm3(res[0], res[1], res[2])), nk);
+            int lv;
+            if (!level_of(dt0, ea.level_min, lv)) {
+                atomicCAS(ea.err, 0, NB_ESTEP);
+                lv = kTickBits;
+            }
+            S.lev[gi] = lv;
+            continue;
+        }
+        // corrector and new step (the single-system corrector's arithmetic)
+        const long long tn = ea.tnext[c];
+        const double dt = ticks_to_time(tn - S.t[gi]);
+        double a2[3], a3[3], ap[3] = {res[0], res[1], res[2]}, kp[3] = {res[3], res[4], res[5]};
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            const long long e = cc * P + gi;
+            const double x = S.x[e], v = S.v[e], a = S.a[e], kk = S.k[e];
+            double xp, vp;
+            predict1(x, v, a, kk, dt, xp, vp);
+            const double d = __dsub_rn(a, ap[cc]);
+            a3[cc] = __dadd_rn(__dmul_rn(2.0, d), __dmul_rn(__dadd_rn(kk, kp[cc]), dt));
+            a2[cc] = __dsub_rn(__dmul_rn(-3.0, d), __dmul_rn(__dadd_rn(__dmul_rn(2.0, kk), kp[cc]), dt));
+            S.x[e] = __dadd_rn(xp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[cc], 12.0), __ddiv_rn(a3[cc], 20.0)),
+                                             __dmul_rn(dt, dt)));
+            S.v[e] = __dadd_rn(vp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[cc], 3.0), __ddiv_rn(a3[cc], 4.0)), dt));
+            S.a[e] = ap[cc];
+            S.k[e] = kp[cc];
+        }
+        S.t[gi] = tn;
+        const double dt2 = __dmul_rn(dt, dt), dt3 = __dmul_rn(dt2, dt);
+        double s1[3], cr[3];
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            const double sv0 = __ddiv_rn(__dmul_rn(2.0, a2[cc]), dt2);
+            cr[cc] = __ddiv_rn(__dmul_rn(6.0, a3[cc]), dt3);
+            s1[cc] = __dadd_rn(sv0, __dmul_rn(cr[cc], dt));
+        }
+        const double nav = norm3(ap[0], ap[1], ap[2]), nk = norm3(kp[0], kp[1], kp[2]);
+        const double ns = norm3(s1[0], s1[1], s1[2]), nc = norm3(cr[0], cr[1], cr[2]);
+        const double num = __dadd_rn(__dmul_rn(nav, ns), __dmul_rn(nk, nk));
+        const double den = __dadd_rn(__dmul_rn(nk, nc), __dmul_rn(ns, ns));
+        const double dt_raw = den == 0.0 ? (double)INFINITY : __dsqrt_rn(__ddiv_rn(__dmul_rn(ea.eta, num), den));
+        int kq;
+        if (!level_of(dt_raw, ea.level_min, kq)) {
+            atomicCAS(ea.err, 0, NB_ESTEP);
+            kq = kTickBits;
+        }
+        S.lev[gi] = next_level(S.lev[gi], kq, tn, ea.level_min);
     }
 }
 
@@ -452,13 +476,17 @@ struct nb_ens {
     double *d_x = nullptr, *d_v = nullptr, *d_a = nullptr, *d_k = nullptr, *d_m = nullptr;
     long long *d_t = nullptr;
     int *d_lev = nullptr;
-    int *d_work = nullptr, *d_done = nullptr, *d_err = nullptr;
+    int *d_work = nullptr, *d_done = nullptr, *d_err = nullptr;  // d_work: [3] counters A, B, queue
+    float4 *d_jph = nullptr, *d_jpl = nullptr, *d_jv = nullptr;
+    int *d_act = nullptr, *d_na = nullptr, *d_qc = nullptr, *d_qk = nullptr;
+    long long *d_tnext = nullptr;
+    long long qcap = 0;
     long long *d_steps = nullptr, *d_inter = nullptr;
     double *d_stage = nullptr;   // [7 P] host I/O staging
     double *d_backup = nullptr;  // state copy for tuning
     long long *d_tbak = nullptr;
     int *d_lbak = nullptr;
-    int nt = 512, gmax = 8;      // launch configuration (tunable)
+    int nt = 256, gmax = 8;      // launch B threads (= chunk) and lane-group cap (tunable)
     long long t_end = LLONG_MAX;
     cudaGraphExec_t graph = nullptr;
     int graph_nt = 0, graph_gmax = 0;
@@ -492,8 +520,6 @@ int efail(nb_ens *e, int code, const char *fmt, ...)
                          "%s: %s", #call, cudaGetErrorString(e_));                        \
     } while (0)
 
-size_t ens_smem() { return 3 * sizeof(float4) * kEnsMaxN + sizeof(int) * kEnsMaxN; }
-
 EnsArgs ens_args(nb_ens *e)
 {
     EnsArgs a{};
@@ -507,7 +533,18 @@ EnsArgs ens_args(nb_ens *e)
     a.level_min = e->o.level_min;
     a.t_end = e->t_end;
     a.gmax = e->gmax;
+    a.chunk = e->nt;
     a.work = e->d_work;
+    a.work_b = e->d_work + 1;
+    a.qlen = e->d_work + 2;
+    a.qc = e->d_qc;
+    a.qk = e->d_qk;
+    a.jph = e->d_jph;
+    a.jpl = e->d_jpl;
+    a.jv = e->d_jv;
+    a.act = e->d_act;
+    a.na = e->d_na;
+    a.tnext = e->d_tnext;
     a.done = e->d_done;
     a.steps = e->d_steps;
     a.inter = e->d_inter;
@@ -515,38 +552,34 @@ EnsArgs ens_args(nb_ens *e)
     return a;
 }
 
+constexpr int kNTA = 256;  // launch A threads
+
 template <int NT, int MODE>
-int launch_ens_t(nb_ens *e, const EnsArgs &a)
+void launch_b_t(nb_ens *e, const EnsArgs &a)
 {
-    static bool configured = false;
-    if (!configured) {
-        if (cudaFuncSetAttribute(k_ens<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)ens_smem()) != cudaSuccess)
-            return efail(e, NB_ECUDA, "cannot reserve %zu bytes of shared memory", ens_smem());
-        configured = true;
+    static int bps = 0;
+    if (bps == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_ens_b<NT, MODE>, NT, 0) != cudaSuccess)
+        bps = 1;
+    k_ens_b<NT, MODE><<<e->sms * (bps > 0 ? bps : 1), NT, 0, e->st>>>(a);
+}
+
+// One pass of the two launches (counters zeroed first).
+template <int MODE>
+int enqueue_ens(nb_ens *e, const EnsArgs &a)
+{
+    ECK(cudaMemsetAsync(e->d_work, 0, 3 * sizeof(int), e->st));
+    k_ens_a<kNTA, MODE><<<e->sms * 4, kNTA, 0, e->st>>>(a);
+    switch (e->nt) {
+    case 128: launch_b_t<128, MODE>(e, a); break;
+    case 512: launch_b_t<512, MODE>(e, a); break;
+    default: launch_b_t<256, MODE>(e, a); break;
     }
-    k_ens<NT, MODE><<<e->sms, NT, ens_smem(), e->st>>>(a);
+    e->launches += 2;
     return NB_OK;
 }
 
-template <int MODE>
-int launch_ens(nb_ens *e, const EnsArgs &a)
-{
-    switch (e->nt) {
-    case 256: return launch_ens_t<256, MODE>(e, a);
-    case 1024: return launch_ens_t<1024, MODE>(e, a);
-    default: return launch_ens_t<512, MODE>(e, a);
-    }
-}
-
-// One ensemble block step: zero the work counter, one persistent launch.
-int enqueue_ens_step(nb_ens *e)
-{
-    ECK(cudaMemsetAsync(e->d_work, 0, sizeof(int), e->st));
-    int rc = launch_ens<kEnsStep>(e, ens_args(e));
-    e->launches += 1;
-    return rc;
-}
+// One ensemble block step.
+int enqueue_ens_step(nb_ens *e) { return enqueue_ens<kEnsStep>(e, ens_args(e)); }
 
 int ens_sync(nb_ens *e)
 {
@@ -580,7 +613,8 @@ void ens_release(nb_ens *e)
     if (e->graph) cudaGraphExecDestroy(e->graph);
     void *ptrs[] = {e->d_off, e->d_order, e->d_x, e->d_v, e->d_a, e->d_k, e->d_m, e->d_t,
                     e->d_lev, e->d_work, e->d_done, e->d_err, e->d_steps, e->d_inter,
-                    e->d_stage, e->d_backup, e->d_tbak, e->d_lbak};
+                    e->d_stage, e->d_backup, e->d_tbak, e->d_lbak, e->d_jph, e->d_jpl, e->d_jv,
+                    e->d_act, e->d_na, e->d_qc, e->d_qk, e->d_tnext};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (e->own_stream && e->st) cudaStreamDestroy(e->st);
@@ -642,9 +676,13 @@ int ens_init_impl(nb_ens *e, int32_t C, const int64_t *off, const double *m, con
         (rc = ealloc(e, &e->d_x, 3 * P)) || (rc = ealloc(e, &e->d_v, 3 * P)) ||
         (rc = ealloc(e, &e->d_a, 3 * P)) || (rc = ealloc(e, &e->d_k, 3 * P)) ||
         (rc = ealloc(e, &e->d_m, P)) || (rc = ealloc(e, &e->d_t, P)) || (rc = ealloc(e, &e->d_lev, P)) ||
-        (rc = ealloc(e, &e->d_work, 1)) || (rc = ealloc(e, &e->d_done, C)) || (rc = ealloc(e, &e->d_err, 1)) ||
+        (rc = ealloc(e, &e->d_work, 3)) || (rc = ealloc(e, &e->d_done, C)) || (rc = ealloc(e, &e->d_err, 1)) ||
         (rc = ealloc(e, &e->d_steps, C)) || (rc = ealloc(e, &e->d_inter, C)) ||
-        (rc = ealloc(e, &e->d_stage, 7 * P)))
+        (rc = ealloc(e, &e->d_stage, 7 * P)) || (rc = ealloc(e, &e->d_jph, P)) ||
+        (rc = ealloc(e, &e->d_jpl, P)) || (rc = ealloc(e, &e->d_jv, P)) ||
+        (rc = ealloc(e, &e->d_act, P)) || (rc = ealloc(e, &e->d_na, C)) ||
+        (rc = ealloc(e, &e->d_tnext, C)) || (rc = ealloc(e, &e->d_qc, P + C)) ||
+        (rc = ealloc(e, &e->d_qk, P + C)))
         return rc;
     e->S.x = e->d_x;
     e->S.v = e->d_v;
@@ -670,8 +708,7 @@ int ens_init_impl(nb_ens *e, int32_t C, const int64_t *off, const double *m, con
     ECK(cudaMemsetAsync(e->d_steps, 0, sizeof(long long) * C, e->st));
     ECK(cudaMemsetAsync(e->d_inter, 0, sizeof(long long) * C, e->st));
     // start-up: force on every particle of every cluster, initial steps
-    ECK(cudaMemsetAsync(e->d_work, 0, sizeof(int), e->st));
-    if ((rc = launch_ens<kEnsInit>(e, ens_args(e)))) return rc;
+    if ((rc = enqueue_ens<kEnsInit>(e, ens_args(e)))) return rc;
     ECK(cudaGetLastError());
     return ens_sync(e);
 }
@@ -717,9 +754,9 @@ const char *nb_ens_last_error(const nb_ens *e)
 int nb_ens_configure(nb_ens *e, int threads, int gmax)
 {
     if (!e) return NB_EINVAL;
-    if ((threads != 256 && threads != 512 && threads != 1024) ||
+    if ((threads != 128 && threads != 256 && threads != 512) ||
         (gmax != 1 && gmax != 2 && gmax != 4 && gmax != 8 && gmax != 16 && gmax != 32))
-        return efail(e, NB_EINVAL, "threads in {256, 512, 1024}, gmax a power of two <= 32");
+        return efail(e, NB_EINVAL, "threads in {128, 256, 512}, gmax a power of two <= 32");
     e->nt = threads;
     e->gmax = gmax;
     return NB_OK;
@@ -743,11 +780,10 @@ int nb_ens_run(nb_ens *e, double t_end, int64_t max_launches, int64_t *launches_
         if (e->graph) cudaGraphExecDestroy(e->graph);
         e->graph = nullptr;
         int rc0 = 0;
-        // the first launch of each configuration sets its shared-memory limit outside capture
+        // a first launch of this configuration outside capture (occupancy query)
         EnsArgs probe = ens_args(e);
         probe.C = 0;
-        ECK(cudaMemsetAsync(e->d_work, 0, sizeof(int), e->st));
-        if ((rc0 = launch_ens<kEnsStep>(e, probe))) return rc0;
+        if ((rc0 = enqueue_ens<kEnsStep>(e, probe))) return rc0;
         ECK(cudaStreamSynchronize(e->st));
         cudaGraph_t g;
         ECK(cudaStreamBeginCapture(e->st, cudaStreamCaptureModeThreadLocal));
@@ -827,7 +863,7 @@ int nb_ens_tune(nb_ens *e, int launches_per_candidate, int *threads_out, int *gm
     cudaEvent_t e0, e1;
     ECK(cudaEventCreate(&e0));
     ECK(cudaEventCreate(&e1));
-    const int cand_nt[3] = {256, 512, 1024};
+    const int cand_nt[3] = {128, 256, 512};
     const int cand_g[6] = {1, 2, 4, 8, 16, 32};
     float best = 1e30f;
     int bnt = e->nt, bg = e->gmax;
@@ -878,10 +914,8 @@ int nb_ens_force(nb_ens *e, double *acc, double *jerk, double *pot)
     a.out_acc = e->d_stage;
     a.out_jerk = e->d_stage + 3 * P;
     a.out_pot = e->d_stage + 6 * P;
-    ECK(cudaMemsetAsync(e->d_work, 0, sizeof(int), e->st));
-    int rc = launch_ens<kEnsForce>(e, a);
+    int rc = enqueue_ens<kEnsForce>(e, a);
     if (rc) return rc;
-    e->launches += 1;
     if (acc) ECK(cudaMemcpyAsync(acc, a.out_acc, sizeof(double) * 3 * P, cudaMemcpyDeviceToHost, e->st));
     if (jerk) ECK(cudaMemcpyAsync(jerk, a.out_jerk, sizeof(double) * 3 * P, cudaMemcpyDeviceToHost, e->st));
     if (pot) ECK(cudaMemcpyAsync(pot, a.out_pot, sizeof(double) * P, cudaMemcpyDeviceToHost, e->st));

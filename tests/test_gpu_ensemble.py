@@ -40,7 +40,7 @@ def _clusters():
     return cl
 
 
-@pytest.mark.parametrize("threads,gmax", [(512, 8), (256, 1), (1024, 32)])
+@pytest.mark.parametrize("threads,gmax", [(512, 8), (256, 1), (128, 32)])
 def test_startup_force_and_levels(nb, threads, gmax):
     cl = _clusters()
     off, m, x, v = _flatten(cl)
@@ -164,7 +164,7 @@ def test_tune_keeps_state_and_picks_a_candidate(nb):
         before = e.nb_ens_get_state()
         th, g, ms = e.nb_ens_tune(3)
         after = e.nb_ens_get_state()
-        assert th in (256, 512, 1024) and g in (1, 2, 4, 8, 16, 32) and ms > 0
+        assert th in (128, 256, 512) and g in (1, 2, 4, 8, 16, 32) and ms > 0
         for key in before:
             assert np.array_equal(before[key], after[key]), key
     finally:
