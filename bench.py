@@ -167,19 +167,30 @@ def fp32_peak_tflops(sms, mhz):
     return 2.0 * FP32_LANES_PER_SM * sms * mhz * 1e6 / 1e12
 
 
+FORCE_SOURCES = ("k_force.cu", "nb_device.cuh", "nb_internal.cuh")
+
+
+def force_sources_sha256():
+    """sha256 over the force kernel's sources, concatenated in FORCE_SOURCES order."""
+    h = hashlib.sha256()
+    for name in FORCE_SOURCES:
+        with open(os.path.join(ROOT, "paper_cs_0702135_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def force_traffic_per_launch(n):
     """DRAM bytes per full-N force launch from the committed ncu summary, or
-    None when the kernel source changed since that capture."""
+    None when the kernel's sources changed since that capture."""
     path = os.path.join(ROOT, "profiles", "k_force_ipar_ds.md")
-    src = os.path.join(ROOT, "paper_cs_0702135_gb300", "csrc", "k_force.cu")
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    mh = re.search(r"k_force\.cu sha256:\s*([0-9a-f]{64})", text)
+    mh = re.search(r"force sources sha256[^:]*:\s*([0-9a-f]{64})", text)
     mb = re.search(r"dram bytes per launch at N=(\d+):\s*([0-9.eE+]+)", text)
     if not mh or not mb:
         return None
-    if hashlib.sha256(open(src, "rb").read()).hexdigest() != mh.group(1):
+    if force_sources_sha256() != mh.group(1):
         return None
     # With the j records resident in L2 the kernel's DRAM traffic is O(N)
     # (records, block outputs), so a smaller capture scales linearly.

@@ -21,28 +21,14 @@
 // k and streams the partners through shared memory in tiles, like the
 // forward i-parallel kernel (double-single positions, FP32 pair arithmetic,
 // TwoSum-promoted tile partials).
-#include "nb_internal.cuh"
+#include "nb_device.cuh"
 
 namespace nbk {
 namespace {
 
+using namespace dev;
+
 constexpr int kVNT = 128;  // threads per CTA = partners per tile
-
-__device__ __forceinline__ float rsqrt_sfu(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
-{
-    float s = hi + x;
-    float bb = s - hi;
-    float e = (hi - (s - bb)) + (x - bb);
-    hi = s;
-    lo += e;
-}
 
 __device__ __forceinline__ int clamp_index(int i, int n) { return min(max(i, 0), n - 1); }
 
@@ -60,10 +46,7 @@ __device__ __forceinline__ void write_vjp_record(int i, const double x[3], const
     } else {
         float hi[3], lo[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            hi[c] = __double2float_rn(x[c]);
-            lo[c] = __double2float_rn(__dsub_rn(x[c], (double)hi[c]));
-        }
+        for (int c = 0; c < 3; ++c) split_ds(x[c], hi[c], lo[c]);
         rec.ph[i] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(m));
         rec.pl[i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
         rec.v[i] = make_float4(__double2float_rn(v[0]), __double2float_rn(v[1]),
@@ -272,16 +255,6 @@ __global__ void k_vjp_combine(VjpArgs va, int S)
         else if (c < 6) va.vbar[3 * (long long)k + (c - 3)] = s;
         else va.mbar[k] = s;
     }
-}
-
-// Hermite predictor (same operation order as the forward predictor).
-__device__ __forceinline__ void predict1(double x, double v, double a, double k, double dt,
-                                         double &xp, double &vp)
-{
-    const double h = __ddiv_rn(dt, 2.0);
-    const double q = __ddiv_rn(dt, 3.0);
-    xp = __dadd_rn(x, __dmul_rn(__dadd_rn(v, __dmul_rn(h, __dadd_rn(a, __dmul_rn(q, k)))), dt));
-    vp = __dadd_rn(v, __dmul_rn(__dadd_rn(a, __dmul_rn(h, k)), dt));
 }
 
 // Backward step, first half: from the cotangents (xb, vb, ab, kb) of the state

@@ -30,13 +30,14 @@
 #include <string>
 #include <vector>
 
-#include "nb_internal.cuh"
+#include "nb_device.cuh"
 
 namespace nbk {
 namespace {
 
+using namespace dev;
+
 constexpr int kEnsMaxN = 4096;       // largest cluster
-constexpr double kTickD = 0x1p-40;
 
 struct EnsArgs {
     int C;                    // clusters
@@ -63,101 +64,6 @@ struct EnsArgs {
     int *err;
     double *out_acc, *out_jerk, *out_pot;  // force-only mode: [P][3], [P][3], [P]
 };
-
-__device__ __forceinline__ float rsqrt_sfu(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
-{
-    float s = hi + x;
-    float bb = s - hi;
-    float e = (hi - (s - bb)) + (x - bb);
-    hi = s;
-    lo += e;
-}
-
-__device__ __forceinline__ void ds_add(float &h, float &l, float h2, float l2)
-{
-    float s = h + h2;
-    float bb = s - h;
-    float e = (h - (s - bb)) + (h2 - bb);
-    h = s;
-    l = (l + l2) + e;
-}
-
-__device__ __forceinline__ double ticks_to_time(long long d)
-{
-    return __dmul_rn(__ll2double_rn(d), kTickD);
-}
-
-__device__ __forceinline__ void predict1(double x, double v, double a, double k, double dt,
-                                         double &xp, double &vp)
-{
-    const double h = __ddiv_rn(dt, 2.0);
-    const double q = __ddiv_rn(dt, 3.0);
-    xp = __dadd_rn(x, __dmul_rn(__dadd_rn(v, __dmul_rn(h, __dadd_rn(a, __dmul_rn(q, k)))), dt));
-    vp = __dadd_rn(v, __dmul_rn(__dadd_rn(a, __dmul_rn(h, k)), dt));
-}
-
-__device__ __forceinline__ double norm3(double u0, double u1, double u2)
-{
-    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(u0, u0), __dmul_rn(u1, u1)), __dmul_rn(u2, u2)));
-}
-
-__device__ __forceinline__ bool level_of(double dt_raw, int kmin, int &level)
-{
-    if (isnan(dt_raw) || dt_raw < 0x1p-40) return false;
-    int k;
-    if (isinf(dt_raw)) {
-        k = kmin;
-    } else {
-        const long long bits = __double_as_longlong(dt_raw);
-        k = 1023 - (int)((bits >> 52) & 0x7FF);
-        if (k < kmin) k = kmin;
-    }
-    level = k;
-    return true;
-}
-
-__device__ __forceinline__ int next_level(int k_old, int k_q, long long t_new, int kmin)
-{
-    if (k_q > k_old) return k_q;
-    if (k_q < k_old && k_old > kmin) {
-        const long long twice_old = 1LL << (kTickBits - k_old + 1);
-        if (t_new % twice_old == 0) return k_old - 1;
-    }
-    return k_old;
-}
-
-// FP32 pair on double-single positions; pair j == i contributes nothing.
-__device__ __forceinline__ void pair(const float4 &p, const float4 &l, const float4 &w,
-                                     const float4 &ip, const float4 &il, const float4 &iv,
-                                     float eps2, bool self, float acc[3], float jk[3], float &pot)
-{
-    const float dx = (p.x - ip.x) + (l.x - il.x);
-    const float dy = (p.y - ip.y) + (l.y - il.y);
-    const float dz = (p.z - ip.z) + (l.z - il.z);
-    const float ux = w.x - iv.x, uy = w.y - iv.y, uz = w.z - iv.z;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-    const float rv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
-    float rinv = rsqrt_sfu(r2);
-    rinv = (self || !(r2 > 0.0f)) ? 0.0f : rinv;
-    const float rinv2 = rinv * rinv;
-    const float mr = p.w * rinv;
-    const float mr3 = mr * rinv2;
-    const float b = -3.0f * rv * rinv2;
-    acc[0] = fmaf(mr3, dx, acc[0]);
-    acc[1] = fmaf(mr3, dy, acc[1]);
-    acc[2] = fmaf(mr3, dz, acc[2]);
-    jk[0] = fmaf(mr3, fmaf(b, dx, ux), jk[0]);
-    jk[1] = fmaf(mr3, fmaf(b, dy, uy), jk[1]);
-    jk[2] = fmaf(mr3, fmaf(b, dz, uz), jk[2]);
-    pot -= mr;
-}
 
 template <typename T, typename Op>
 __device__ __forceinline__ T cta_reduce(T v, Op op, T *smem)
@@ -225,10 +131,7 @@ __global__ void __launch_bounds__(NT) k_ens_a(EnsArgs ea)
                              dt, xp[cc], vp[cc]);
                 float hi[3], lo[3];
 #pragma unroll
-                for (int cc = 0; cc < 3; ++cc) {
-                    hi[cc] = __double2float_rn(xp[cc]);
-                    lo[cc] = __double2float_rn(__dsub_rn(xp[cc], (double)hi[cc]));
-                }
+                for (int cc = 0; cc < 3; ++cc) split_ds(xp[cc], hi[cc], lo[cc]);
                 ea.jph[gi] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(S.m[gi]));
                 ea.jpl[gi] = make_float4(lo[0], lo[1], lo[2], 0.0f);
                 ea.jv[gi] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
@@ -293,6 +196,7 @@ __global__ void __launch_bounds__(NT) k_ens_b(EnsArgs ea)
         const bool valid = grp < cnt;
         const int i = ea.act[o + s0 + (valid ? grp : 0)];
         const float4 ip = ea.jph[o + i], il = ea.jpl[o + i], iv = ea.jv[o + i];
+        const float xh[3] = {ip.x, ip.y, ip.z}, xl[3] = {il.x, il.y, il.z}, vi[3] = {iv.x, iv.y, iv.z};
         float hi[7] = {0, 0, 0, 0, 0, 0, 0}, lo[7] = {0, 0, 0, 0, 0, 0, 0};
         for (int jt = 0; jt < n; jt += NT) {
             __syncthreads();
@@ -308,7 +212,8 @@ __global__ void __launch_bounds__(NT) k_ens_b(EnsArgs ea)
                 const int je = min(jc, jb + 64 * g);
                 float ta[3] = {0, 0, 0}, tk[3] = {0, 0, 0}, tp = 0.0f;
                 for (int jj = jb + lig; jj < je; jj += g)
-                    pair(s_ph[jj], s_pl[jj], s_v[jj], ip, il, iv, ea.eps2, jt + jj == i, ta, tk, tp);
+                    pair_ds<false, true>(s_ph[jj], s_pl[jj], s_v[jj], xh, xl, vi, ea.eps2, ta, tk, tp,
+                                         jt + jj, i);
                 const float t7[7] = {ta[0], ta[1], ta[2], tk[0], tk[1], tk[2], tp};
 #pragma unroll
                 for (int cc = 0; cc < 7; ++cc) two_sum_acc(hi[cc], lo[cc], t7[cc]);
@@ -343,11 +248,8 @@ __global__ void __launch_bounds__(NT) k_ens_b(EnsArgs ea)
                 S.k[cc * P + gi] = res[3 + cc];
             }
             S.t[gi] = 0;
-            const double nk = norm3(res[3], res[4], res[5]);
-            const double dt0 = nk == 0.0 ? (double)INFINITY
-                                         : __ddiv_rn(__dmul_rn(ea.eta_init, norm3(res[0], res[1], res[2])), nk);
             int lv;
-            if (!level_of(dt0, ea.level_min, lv)) {
+            if (!level_of(initial_dt(res, res + 3, ea.eta_init), ea.level_min, lv)) {
                 atomicCAS(ea.err, 0, NB_ESTEP);
                 lv = kTickBits;
             }
@@ -355,44 +257,9 @@ __global__ void __launch_bounds__(NT) k_ens_b(EnsArgs ea)
             continue;
         }
         // corrector and new step (the single-system corrector's arithmetic)
-        const long long tn = ea.tnext[c];
-        const double dt = ticks_to_time(tn - S.t[gi]);
-        double a2[3], a3[3], ap[3] = {res[0], res[1], res[2]}, kp[3] = {res[3], res[4], res[5]};
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-            const long long e = cc * P + gi;
-            const double x = S.x[e], v = S.v[e], a = S.a[e], kk = S.k[e];
-            double xp, vp;
-            predict1(x, v, a, kk, dt, xp, vp);
-            const double d = __dsub_rn(a, ap[cc]);
-            a3[cc] = __dadd_rn(__dmul_rn(2.0, d), __dmul_rn(__dadd_rn(kk, kp[cc]), dt));
-            a2[cc] = __dsub_rn(__dmul_rn(-3.0, d), __dmul_rn(__dadd_rn(__dmul_rn(2.0, kk), kp[cc]), dt));
-            S.x[e] = __dadd_rn(xp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[cc], 12.0), __ddiv_rn(a3[cc], 20.0)),
-                                             __dmul_rn(dt, dt)));
-            S.v[e] = __dadd_rn(vp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[cc], 3.0), __ddiv_rn(a3[cc], 4.0)), dt));
-            S.a[e] = ap[cc];
-            S.k[e] = kp[cc];
-        }
-        S.t[gi] = tn;
-        const double dt2 = __dmul_rn(dt, dt), dt3 = __dmul_rn(dt2, dt);
-        double s1[3], cr[3];
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-            const double sv0 = __ddiv_rn(__dmul_rn(2.0, a2[cc]), dt2);
-            cr[cc] = __ddiv_rn(__dmul_rn(6.0, a3[cc]), dt3);
-            s1[cc] = __dadd_rn(sv0, __dmul_rn(cr[cc], dt));
-        }
-        const double nav = norm3(ap[0], ap[1], ap[2]), nk = norm3(kp[0], kp[1], kp[2]);
-        const double ns = norm3(s1[0], s1[1], s1[2]), nc = norm3(cr[0], cr[1], cr[2]);
-        const double num = __dadd_rn(__dmul_rn(nav, ns), __dmul_rn(nk, nk));
-        const double den = __dadd_rn(__dmul_rn(nk, nc), __dmul_rn(ns, ns));
-        const double dt_raw = den == 0.0 ? (double)INFINITY : __dsqrt_rn(__ddiv_rn(__dmul_rn(ea.eta, num), den));
-        int kq;
-        if (!level_of(dt_raw, ea.level_min, kq)) {
+        const double ap[3] = {res[0], res[1], res[2]}, kp[3] = {res[3], res[4], res[5]};
+        if (!correct_particle(S, gi, P, ea.tnext[c], ap, kp, ea.eta, ea.level_min, 0))
             atomicCAS(ea.err, 0, NB_ESTEP);
-            kq = kTickBits;
-        }
-        S.lev[gi] = next_level(S.lev[gi], kq, tn, ea.level_min);
     }
 }
 

@@ -28,34 +28,16 @@
 // tile partial of the potential by m_i / eps, which at small N or large mass
 // ratios is larger than the potential itself.)  With eps = 0 a pair at r = 0
 // between distinct particles is dropped as well.
-#include "nb_internal.cuh"
+#include "nb_device.cuh"
 
 namespace nbk {
 namespace {
 
+using namespace dev;
+
 __device__ __forceinline__ int read_na(const ForceArgs &fa)
 {
     return fa.na_dev ? *fa.na_dev : fa.na_host;
-}
-
-// Knuth's TwoSum: hi + lo absorbs x, with the rounding error of hi + x in lo.
-__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
-{
-    float s = hi + x;
-    float bb = s - hi;
-    float e = (hi - (s - bb)) + (x - bb);
-    hi = s;
-    lo += e;
-}
-
-// Sum of two double-single values (h, l) += (h2, l2).
-__device__ __forceinline__ void ds_add(float &h, float &l, float h2, float l2)
-{
-    float s = h + h2;
-    float bb = s - h;
-    float e = (h - (s - bb)) + (h2 - bb);
-    h = s;
-    l = (l + l2) + e;
 }
 
 __device__ __forceinline__ void store_result(const ForceOut &o, int a, const double r[kComp])
@@ -71,51 +53,6 @@ __device__ __forceinline__ void store_result(const ForceOut &o, int a, const dou
         o.jerk[3 * (long long)a + 2] = r[5];
     }
     if (o.pot) o.pot[a] = r[6];
-}
-
-// 1/sqrt(x) on the SFU: the PTX approximate reciprocal square root with
-// flush-to-zero (one MUFU instruction; relative error about 2^-23).  r^2 >=
-// eps^2 is never subnormal, so the denormal handling of rsqrtf() would only
-// cost issue slots here.
-__device__ __forceinline__ float rsqrt_sfu(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// One FP32 pair interaction on double-single positions.
-template <bool SOFT, bool GUARD>
-__device__ __forceinline__ void pair_ds(const float4 &p, const float4 &l, const float4 &w,
-                                        const float xh[3], const float xl[3], const float vi[3],
-                                        float eps2, float acc[3], float jk[3], float &pot,
-                                        int j = 0, int i = 1)
-{
-    const float dx = (p.x - xh[0]) + (l.x - xl[0]);
-    const float dy = (p.y - xh[1]) + (l.y - xl[1]);
-    const float dz = (p.z - xh[2]) + (l.z - xl[2]);
-    const float ux = w.x - vi[0];
-    const float uy = w.y - vi[1];
-    const float uz = w.z - vi[2];
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-    const float rv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
-    float rinv = rsqrt_sfu(r2);
-    if (!SOFT) rinv = (r2 > 0.0f) ? rinv : 0.0f;
-    if (GUARD) rinv = (j == i) ? 0.0f : rinv;
-    const float rinv2 = rinv * rinv;
-    const float mr = p.w * rinv;           // m_j / r
-    const float mr3 = mr * rinv2;          // m_j / r^3
-    const float b = -3.0f * rv * rinv2;    // -3 (dx . dv) / r^2
-    acc[0] = fmaf(mr3, dx, acc[0]);
-    acc[1] = fmaf(mr3, dy, acc[1]);
-    acc[2] = fmaf(mr3, dz, acc[2]);
-    const float qx = fmaf(b, dx, ux);
-    const float qy = fmaf(b, dy, uy);
-    const float qz = fmaf(b, dz, uz);
-    jk[0] = fmaf(mr3, qx, jk[0]);
-    jk[1] = fmaf(mr3, qy, jk[1]);
-    jk[2] = fmaf(mr3, qz, jk[2]);
-    pot -= mr;
 }
 
 // One FP64 pair interaction.

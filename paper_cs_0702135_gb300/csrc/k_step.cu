@@ -1,7 +1,8 @@
 // k_step.cu -- the O(N) kernels around the force: Hermite predictor, Hermite
 // corrector with the block time step, block scheduler, energy reduction.
 //
-// All FP64 arithmetic of the predictor, corrector and time-step criterion uses
+// All FP64 arithmetic of the predictor, corrector and time-step criterion
+// (nb_device.cuh, shared with the ensemble and reverse-mode kernels) uses
 // explicit round-to-nearest intrinsics (__dadd_rn, __dmul_rn, __ddiv_rn,
 // __dsqrt_rn) in the order the formulas are written, so that no multiply-add
 // is contracted and the same inputs give the same bits as any IEEE FP64
@@ -9,67 +10,16 @@
 // levels be compared bit for bit with a CPU evaluation.
 #include <climits>
 
-#include "nb_internal.cuh"
+#include "nb_device.cuh"
 
 namespace nbk {
 namespace {
 
-constexpr double kTick = 0x1p-40;  // one tick in N-body time units
-
-__device__ __forceinline__ double ticks_to_time(long long d)
-{
-    return __dmul_rn(__ll2double_rn(d), kTick);
-}
-
-// Hermite predictor (Section 2):
-//   x_p = x + (v + (dt/2)(a + (dt/3) k)) dt,   v_p = v + (a + (dt/2) k) dt.
-__device__ __forceinline__ void predict1(double x, double v, double a, double k, double dt,
-                                         double &xp, double &vp)
-{
-    const double h = __ddiv_rn(dt, 2.0);
-    const double q = __ddiv_rn(dt, 3.0);
-    xp = __dadd_rn(x, __dmul_rn(__dadd_rn(v, __dmul_rn(h, __dadd_rn(a, __dmul_rn(q, k)))), dt));
-    vp = __dadd_rn(v, __dmul_rn(__dadd_rn(a, __dmul_rn(h, k)), dt));
-}
-
-__device__ __forceinline__ double norm3(double u0, double u1, double u2)
-{
-    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(u0, u0), __dmul_rn(u1, u1)), __dmul_rn(u2, u2)));
-}
+using namespace dev;
 
 __device__ __forceinline__ void raise_err(int *err, int code)
 {
     atomicCAS(err, 0, code);
-}
-
-// Block level of a raw step: k of the largest 2^-k <= dt_raw, from the FP64
-// exponent field (dt_raw >= 2^-40 is a normal number), clamped to k >= kmin.
-// Returns false when dt_raw is not a number or below 2^-40.
-__device__ __forceinline__ bool level_of(double dt_raw, int kmin, int &level)
-{
-    if (isnan(dt_raw) || dt_raw < 0x1p-40) return false;
-    int k;
-    if (isinf(dt_raw)) {
-        k = kmin;
-    } else {
-        const long long bits = __double_as_longlong(dt_raw);
-        k = 1023 - (int)((bits >> 52) & 0x7FF);
-        if (k < kmin) k = kmin;
-    }
-    level = k;
-    return true;
-}
-
-// Halve at once; double by one level only when the new time is a multiple of
-// the doubled step; never above the largest step.
-__device__ __forceinline__ int next_level(int k_old, int k_q, long long t_new, int kmin)
-{
-    if (k_q > k_old) return k_q;
-    if (k_q < k_old && k_old > kmin) {
-        const long long twice_old = 1LL << (kTickBits - k_old + 1);
-        if (t_new % twice_old == 0) return k_old - 1;
-    }
-    return k_old;
 }
 
 // ---------------------------------------------------------------------------
@@ -94,10 +44,7 @@ __global__ void k_predict(State s, long long t_val, const long long *t_ptr, cons
         } else {
             float hi[3], lo[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                hi[c] = __double2float_rn(xp[c]);
-                lo[c] = __double2float_rn(__dsub_rn(xp[c], (double)hi[c]));
-            }
+            for (int c = 0; c < 3; ++c) split_ds(xp[c], hi[c], lo[c]);
             jds.pos_hi[i] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(m));
             jds.pos_lo[i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
             jds.vel[i] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
@@ -106,12 +53,8 @@ __global__ void k_predict(State s, long long t_val, const long long *t_ptr, cons
     }
 }
 
-// Hermite corrector and Aarseth step for the block (Section 2).  In the
-// paper's notation a, k are the old values and a_p, k_p the new ones:
-//   a3 = 2 (a - a_p) + (k + k_p) dt,   a2 = -3 (a - a_p) - (2 k + k_p) dt,
-//   x = x_p + (a2/12 + a3/20) dt^2,    v = v_p + (a2/3 + a3/4) dt.
-// Snap s0 = 2 a2 / dt^2, crackle c = 6 a3 / dt^3, s1 = s0 + c dt, and
-//   dt_new = sqrt(eta (|a_p| |s1| + |k_p|^2) / (|k_p| |c| + |s1|^2)).
+// Hermite corrector and Aarseth step for the block (Section 2), one thread
+// per active particle; the arithmetic is correct_particle's.
 __global__ void k_correct(State s, const int *act, int na_host, const int *na_dev, long long t_val,
                           const long long *t_ptr, const double *acc_new, const double *jerk_new,
                           double eta, int level_min, int level_fixed, int *err)
@@ -119,58 +62,15 @@ __global__ void k_correct(State s, const int *act, int na_host, const int *na_de
     const int na = na_dev ? *na_dev : na_host;
     if (na <= 0) return;
     const long long tn = t_ptr ? *t_ptr : t_val;
-    const int n = s.n;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < na; b += gridDim.x * blockDim.x) {
-        const int i = act[b];
-        const double dt = ticks_to_time(tn - s.t[i]);
-        double ap[3], kp[3], a2[3], a3[3];
+        double ap[3], kp[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             ap[c] = acc_new[3 * (long long)b + c];
             kp[c] = jerk_new[3 * (long long)b + c];
-            const double x = s.x[c * n + i], v = s.v[c * n + i];
-            const double a = s.a[c * n + i], k = s.k[c * n + i];
-            double xp, vp;
-            predict1(x, v, a, k, dt, xp, vp);
-            const double d = __dsub_rn(a, ap[c]);
-            a3[c] = __dadd_rn(__dmul_rn(2.0, d), __dmul_rn(__dadd_rn(k, kp[c]), dt));
-            a2[c] = __dsub_rn(__dmul_rn(-3.0, d), __dmul_rn(__dadd_rn(__dmul_rn(2.0, k), kp[c]), dt));
-            s.x[c * n + i] = __dadd_rn(
-                xp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[c], 12.0), __ddiv_rn(a3[c], 20.0)),
-                              __dmul_rn(dt, dt)));
-            s.v[c * n + i] =
-                __dadd_rn(vp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[c], 3.0), __ddiv_rn(a3[c], 4.0)), dt));
-            s.a[c * n + i] = ap[c];
-            s.k[c * n + i] = kp[c];
         }
-        s.t[i] = tn;
-        if (level_fixed > 0) {
-            s.lev[i] = level_fixed;
-            continue;
-        }
-        const double dt2 = __dmul_rn(dt, dt);
-        const double dt3 = __dmul_rn(dt2, dt);
-        double s1[3], cr[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const double s0 = __ddiv_rn(__dmul_rn(2.0, a2[c]), dt2);
-            cr[c] = __ddiv_rn(__dmul_rn(6.0, a3[c]), dt3);
-            s1[c] = __dadd_rn(s0, __dmul_rn(cr[c], dt));
-        }
-        const double na_ = norm3(ap[0], ap[1], ap[2]);
-        const double nk = norm3(kp[0], kp[1], kp[2]);
-        const double ns = norm3(s1[0], s1[1], s1[2]);
-        const double nc = norm3(cr[0], cr[1], cr[2]);
-        const double num = __dadd_rn(__dmul_rn(na_, ns), __dmul_rn(nk, nk));
-        const double den = __dadd_rn(__dmul_rn(nk, nc), __dmul_rn(ns, ns));
-        const double dt_raw =
-            den == 0.0 ? (double)INFINITY : __dsqrt_rn(__ddiv_rn(__dmul_rn(eta, num), den));
-        int kq;
-        if (!level_of(dt_raw, level_min, kq)) {
+        if (!correct_particle(s, act[b], s.n, tn, ap, kp, eta, level_min, level_fixed))
             raise_err(err, NB_ESTEP);
-            kq = kTickBits;
-        }
-        s.lev[i] = next_level(s.lev[i], kq, tn, level_min);
     }
 }
 
@@ -194,11 +94,8 @@ __global__ void k_initial(State s, const double *acc, const double *jerk, double
             s.lev[i] = level_fixed;
             continue;
         }
-        const double nk = norm3(k[0], k[1], k[2]);
-        const double dt0 =
-            nk == 0.0 ? (double)INFINITY : __ddiv_rn(__dmul_rn(eta_init, norm3(a[0], a[1], a[2])), nk);
         int lv;
-        if (!level_of(dt0, level_min, lv)) {
+        if (!level_of(initial_dt(a, k, eta_init), level_min, lv)) {
             raise_err(err, NB_ESTEP);
             lv = kTickBits;
         }

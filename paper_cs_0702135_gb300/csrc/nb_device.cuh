@@ -1,0 +1,207 @@
+// nb_device.cuh -- device arithmetic shared by every kernel that predicts,
+// corrects or sums pair forces, so that the single-system step, the ensemble
+// step and the reverse mode evaluate the same formulas bit for bit.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "nb_internal.cuh"
+
+namespace nbk {
+namespace dev {
+
+constexpr double kTick = 0x1p-40;  // one tick in N-body time units
+
+__device__ __forceinline__ double ticks_to_time(long long d)
+{
+    return __dmul_rn(__ll2double_rn(d), kTick);
+}
+
+// 1/sqrt(x) on the SFU: the PTX approximate reciprocal square root with
+// flush-to-zero (one MUFU instruction; relative error about 2^-23).  r^2 >=
+// eps^2 is never subnormal, so the denormal handling of rsqrtf() would only
+// cost issue slots here.
+__device__ __forceinline__ float rsqrt_sfu(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Knuth's TwoSum: hi + lo absorbs x, with the rounding error of hi + x in lo.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
+{
+    float s = hi + x;
+    float bb = s - hi;
+    float e = (hi - (s - bb)) + (x - bb);
+    hi = s;
+    lo += e;
+}
+
+// Sum of two double-single values (h, l) += (h2, l2).
+__device__ __forceinline__ void ds_add(float &h, float &l, float h2, float l2)
+{
+    float s = h + h2;
+    float bb = s - h;
+    float e = (h - (s - bb)) + (h2 - bb);
+    h = s;
+    l = (l + l2) + e;
+}
+
+// Hermite predictor (Section 2), round-to-nearest in the formula's order:
+//   x_p = x + (v + (dt/2)(a + (dt/3) k)) dt,   v_p = v + (a + (dt/2) k) dt.
+__device__ __forceinline__ void predict1(double x, double v, double a, double k, double dt,
+                                         double &xp, double &vp)
+{
+    const double h = __ddiv_rn(dt, 2.0);
+    const double q = __ddiv_rn(dt, 3.0);
+    xp = __dadd_rn(x, __dmul_rn(__dadd_rn(v, __dmul_rn(h, __dadd_rn(a, __dmul_rn(q, k)))), dt));
+    vp = __dadd_rn(v, __dmul_rn(__dadd_rn(a, __dmul_rn(h, k)), dt));
+}
+
+// A predicted FP64 position split into double-single: x = hi + lo to 2^-48.
+__device__ __forceinline__ void split_ds(double x, float &hi, float &lo)
+{
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(__dsub_rn(x, (double)hi));
+}
+
+__device__ __forceinline__ double norm3(double u0, double u1, double u2)
+{
+    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(u0, u0), __dmul_rn(u1, u1)), __dmul_rn(u2, u2)));
+}
+
+// Block level of a raw step: k of the largest 2^-k <= dt_raw, from the FP64
+// exponent field (dt_raw >= 2^-40 is a normal number), clamped to k >= kmin.
+// Returns false when dt_raw is not a number or below 2^-40.
+__device__ __forceinline__ bool level_of(double dt_raw, int kmin, int &level)
+{
+    if (isnan(dt_raw) || dt_raw < 0x1p-40) return false;
+    int k;
+    if (isinf(dt_raw)) {
+        k = kmin;
+    } else {
+        const long long bits = __double_as_longlong(dt_raw);
+        k = 1023 - (int)((bits >> 52) & 0x7FF);
+        if (k < kmin) k = kmin;
+    }
+    level = k;
+    return true;
+}
+
+// Halve at once; double by one level only when the new time is a multiple of
+// the doubled step; never above the largest step.
+__device__ __forceinline__ int next_level(int k_old, int k_q, long long t_new, int kmin)
+{
+    if (k_q > k_old) return k_q;
+    if (k_q < k_old && k_old > kmin) {
+        const long long twice_old = 1LL << (kTickBits - k_old + 1);
+        if (t_new % twice_old == 0) return k_old - 1;
+    }
+    return k_old;
+}
+
+// Start-up step eta_init |a| / |k|; +infinity when the jerk vanishes.
+__device__ __forceinline__ double initial_dt(const double a[3], const double k[3], double eta_init)
+{
+    const double nk = norm3(k[0], k[1], k[2]);
+    return nk == 0.0 ? (double)INFINITY : __ddiv_rn(__dmul_rn(eta_init, norm3(a[0], a[1], a[2])), nk);
+}
+
+// Hermite corrector and Aarseth step for particle i of `s` (Section 2).  In
+// the paper's notation a, k are the old values (in s) and a_p, k_p the new:
+//   a3 = 2 (a - a_p) + (k + k_p) dt,   a2 = -3 (a - a_p) - (2 k + k_p) dt,
+//   x = x_p + (a2/12 + a3/20) dt^2,    v = v_p + (a2/3 + a3/4) dt.
+// Snap s0 = 2 a2 / dt^2, crackle c = 6 a3 / dt^3, s1 = s0 + c dt, and
+//   dt_new = sqrt(eta (|a_p| |s1| + |k_p|^2) / (|k_p| |c| + |s1|^2)),
+// quantised by level_of and next_level (level_fixed > 0 keeps that level).
+// x_p, v_p are recomputed with predict1, bit for bit the values the force
+// saw.  Returns false when the new step fell below 2^-40.
+__device__ __forceinline__ bool correct_particle(const State &s, long long i, long long stride,
+                                                 long long tn, const double ap[3], const double kp[3],
+                                                 double eta, int level_min, int level_fixed)
+{
+    const double dt = ticks_to_time(tn - s.t[i]);
+    double a2[3], a3[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long e = c * stride + i;
+        const double x = s.x[e], v = s.v[e], a = s.a[e], k = s.k[e];
+        double xp, vp;
+        predict1(x, v, a, k, dt, xp, vp);
+        const double d = __dsub_rn(a, ap[c]);
+        a3[c] = __dadd_rn(__dmul_rn(2.0, d), __dmul_rn(__dadd_rn(k, kp[c]), dt));
+        a2[c] = __dsub_rn(__dmul_rn(-3.0, d), __dmul_rn(__dadd_rn(__dmul_rn(2.0, k), kp[c]), dt));
+        s.x[e] = __dadd_rn(xp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[c], 12.0), __ddiv_rn(a3[c], 20.0)),
+                                         __dmul_rn(dt, dt)));
+        s.v[e] = __dadd_rn(vp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[c], 3.0), __ddiv_rn(a3[c], 4.0)), dt));
+        s.a[e] = ap[c];
+        s.k[e] = kp[c];
+    }
+    s.t[i] = tn;
+    if (level_fixed > 0) {
+        s.lev[i] = level_fixed;
+        return true;
+    }
+    const double dt2 = __dmul_rn(dt, dt);
+    const double dt3 = __dmul_rn(dt2, dt);
+    double s1[3], cr[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double s0 = __ddiv_rn(__dmul_rn(2.0, a2[c]), dt2);
+        cr[c] = __ddiv_rn(__dmul_rn(6.0, a3[c]), dt3);
+        s1[c] = __dadd_rn(s0, __dmul_rn(cr[c], dt));
+    }
+    const double na = norm3(ap[0], ap[1], ap[2]);
+    const double nk = norm3(kp[0], kp[1], kp[2]);
+    const double ns = norm3(s1[0], s1[1], s1[2]);
+    const double nc = norm3(cr[0], cr[1], cr[2]);
+    const double num = __dadd_rn(__dmul_rn(na, ns), __dmul_rn(nk, nk));
+    const double den = __dadd_rn(__dmul_rn(nk, nc), __dmul_rn(ns, ns));
+    const double dt_raw = den == 0.0 ? (double)INFINITY : __dsqrt_rn(__ddiv_rn(__dmul_rn(eta, num), den));
+    int kq;
+    const bool ok = level_of(dt_raw, level_min, kq);
+    if (!ok) kq = kTickBits;
+    s.lev[i] = next_level(s.lev[i], kq, tn, level_min);
+    return ok;
+}
+
+// One FP32 pair interaction on double-single positions (Eq. 1 with the
+// attractive sign; pair terms of the Appendix A kernel), dx = x_j - x_i formed
+// as (x_j,hi - x_i,hi) + (x_j,lo - x_i,lo).  SOFT = false drops pairs at
+// r = 0; GUARD drops the pair j == i.
+template <bool SOFT, bool GUARD>
+__device__ __forceinline__ void pair_ds(const float4 &p, const float4 &l, const float4 &w,
+                                        const float xh[3], const float xl[3], const float vi[3],
+                                        float eps2, float acc[3], float jk[3], float &pot,
+                                        int j = 0, int i = 1)
+{
+    const float dx = (p.x - xh[0]) + (l.x - xl[0]);
+    const float dy = (p.y - xh[1]) + (l.y - xl[1]);
+    const float dz = (p.z - xh[2]) + (l.z - xl[2]);
+    const float ux = w.x - vi[0];
+    const float uy = w.y - vi[1];
+    const float uz = w.z - vi[2];
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+    const float rv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+    float rinv = rsqrt_sfu(r2);
+    if (!SOFT) rinv = (r2 > 0.0f) ? rinv : 0.0f;
+    if (GUARD) rinv = (j == i) ? 0.0f : rinv;
+    const float rinv2 = rinv * rinv;
+    const float mr = p.w * rinv;           // m_j / r
+    const float mr3 = mr * rinv2;          // m_j / r^3
+    const float b = -3.0f * rv * rinv2;    // -3 (dx . dv) / r^2
+    acc[0] = fmaf(mr3, dx, acc[0]);
+    acc[1] = fmaf(mr3, dy, acc[1]);
+    acc[2] = fmaf(mr3, dz, acc[2]);
+    const float qx = fmaf(b, dx, ux);
+    const float qy = fmaf(b, dy, uy);
+    const float qz = fmaf(b, dz, uz);
+    jk[0] = fmaf(mr3, qx, jk[0]);
+    jk[1] = fmaf(mr3, qy, jk[1]);
+    jk[2] = fmaf(mr3, qz, jk[2]);
+    pot -= mr;
+}
+
+}  // namespace dev
+}  // namespace nbk
