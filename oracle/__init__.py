@@ -20,6 +20,11 @@ import numpy as np
 from . import build as _build
 
 TICK_BITS = 40
+# Summation of the force (same numbers as the library's NB_SUM_* options):
+SUM_FP64 = 0           # the FP64 definition (orc_force)
+SUM_FIXED = 1          # single-precision pair terms, 64-bit fixed-point sums (GRAPE-style)
+SUM_FP32 = 2           # single-precision pair terms, FP32 running sum in index order
+SUM_FP32_SORTED = 3    # the same, smallest pair force first
 TICKS_PER_UNIT = 1 << TICK_BITS
 ESTEP = -4
 
@@ -28,6 +33,7 @@ _lib = None
 _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_f32p = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
 _i64 = ctypes.c_int64
 _int = ctypes.c_int
 _dbl = ctypes.c_double
@@ -59,17 +65,17 @@ def lib():
         L.orc_next_level.argtypes = [_int, _int, _i64, _int]
         L.orc_next_level.restype = _int
         L.orc_init.argtypes = [_i64, _f64p, _f64p, _f64p, _dbl, _dbl, _int, _int, _f64p, _f64p,
-                               _f64p, _i64p, _i32p, _int]
+                               _f64p, _i64p, _i32p, _int, _int]
         L.orc_init.restype = _int
         L.orc_next_time.argtypes = [_i64, _i64p, _i32p]
         L.orc_next_time.restype = _i64
         L.orc_step.argtypes = [_i64, _f64p, _dbl, _dbl, _int, _int, _i64, _f64p, _f64p, _f64p,
                                _f64p, _i64p, _i32p, _i32p, ctypes.POINTER(_i64), ctypes.c_void_p,
-                               _int]
+                               _int, _int]
         L.orc_step.restype = _i64
         L.orc_run.argtypes = [_i64, _f64p, _dbl, _dbl, _int, _int, _i64, _i64, _f64p, _f64p,
                               _f64p, _f64p, _i64p, _i32p, ctypes.c_void_p, ctypes.POINTER(_i64),
-                              _int]
+                              _int, _int]
         L.orc_run.restype = _i64
         L.orc_force_vjp.argtypes = [_i64, _f64p, _f64p, _f64p, _dbl, _f64p, _f64p, _f64p, _f64p,
                                     _f64p]
@@ -77,6 +83,14 @@ def lib():
         L.orc_traj_vjp.argtypes = [_i64, _f64p, _f64p, _f64p, _dbl, _dbl, _i64, _f64p, _f64p, _f64p,
                                    _f64p, _f64p]
         L.orc_traj_vjp.restype = _int
+        L.orc_force_summed.argtypes = [_int, _i64, _f64p, _f64p, _f64p, _dbl, _i64, _i32p, _f64p,
+                                       _f64p, _f64p, _int]
+        L.orc_force_summed.restype = _int
+        L.orc_fixed_scales.argtypes = [_i64, _f64p, _f64p, _dbl, _i32p]
+        L.orc_fixed_scales.restype = _int
+        L.orc_pair_terms32.argtypes = [_i64, _f64p, _f64p, _f64p, _dbl, _i64, _int, _f32p, _f32p,
+                                       _i32p]
+        L.orc_pair_terms32.restype = _int
         L.orc_max_threads.argtypes = []
         L.orc_max_threads.restype = _int
         _lib = L
@@ -102,6 +116,46 @@ def force(m, x, v, eps, idx=None, nthreads=1):
     pot = np.zeros(na)
     lib().orc_force(n, m, x, v, float(eps), na, idx, acc, jerk, pot, int(nthreads))
     return acc, jerk, pot
+
+
+def force_summed(m, x, v, eps, idx=None, mode=SUM_FIXED, nthreads=1):
+    """acc, jerk, pot on the listed i with a summation variant (SUM_FIXED,
+    SUM_FP32 or SUM_FP32_SORTED) of the single-precision pair terms."""
+    m, x, v = _c(m), _c(x), _c(v)
+    n = m.shape[0]
+    idx = np.arange(n, dtype=np.int32) if idx is None else _c(idx, np.int32)
+    na = idx.shape[0]
+    acc = np.zeros((na, 3))
+    jerk = np.zeros((na, 3))
+    pot = np.zeros(na)
+    rc = lib().orc_force_summed(int(mode), n, m, x, v, float(eps), na, idx, acc, jerk, pot,
+                                int(nthreads))
+    if rc != 0:
+        raise ValueError("summation variant %d rejected the input (%d)" % (mode, rc))
+    return acc, jerk, pot
+
+
+def fixed_scales(m, v, eps):
+    """(s_acc, s_jerk, s_pot): fixed-point units 2^-s of the GRAPE-style sums."""
+    s = np.zeros(3, dtype=np.int32)
+    rc = lib().orc_fixed_scales(_c(m).shape[0], _c(m), _c(v), float(eps), s)
+    if rc != 0:
+        raise ValueError("no fixed-point scales for this input (%d)" % rc)
+    return tuple(int(q) for q in s)
+
+
+def pair_terms32(m, x, v, eps, i, scaled=False):
+    """Single-precision pair terms of every j on particle i: (t[n][7] float32,
+    key[n] float32, ok[n] bool); scaled=True applies the fixed-point scales."""
+    m, x, v = _c(m), _c(x), _c(v)
+    n = m.shape[0]
+    t = np.zeros((n, 7), dtype=np.float32)
+    key = np.zeros(n, dtype=np.float32)
+    ok = np.zeros(n, dtype=np.int32)
+    rc = lib().orc_pair_terms32(n, m, x, v, float(eps), int(i), int(bool(scaled)), t, key, ok)
+    if rc != 0:
+        raise ValueError("no fixed-point scales for this input (%d)" % rc)
+    return t, key, ok.astype(bool)
 
 
 def energy(m, x, v, eps, nthreads=1):
@@ -185,20 +239,23 @@ def time_to_ticks(t: float) -> int:
 class Integrator:
     """FP64 Hermite block-step integrator state (the oracle's step loop)."""
 
-    def __init__(self, m, x, v, eps, eta=0.01, eta_init=0.01, kmin=3, kfix=0, nthreads=1):
+    def __init__(self, m, x, v, eps, eta=0.01, eta_init=0.01, kmin=3, kfix=0, nthreads=1,
+                 summation=SUM_FP64):
         self.m = _c(m).copy()
         self.x = _c(x).copy()
         self.v = _c(v).copy()
         self.n = self.m.shape[0]
         self.eps, self.eta, self.eta_init = float(eps), float(eta), float(eta_init)
         self.kmin, self.kfix, self.nthreads = int(kmin), int(kfix), int(nthreads)
+        self.summation = int(summation)
         self.a = np.zeros((self.n, 3))
         self.k = np.zeros((self.n, 3))
         self.pot = np.zeros(self.n)
         self.t = np.zeros(self.n, dtype=np.int64)
         self.lev = np.zeros(self.n, dtype=np.int32)
         rc = lib().orc_init(self.n, self.m, self.x, self.v, self.eps, self.eta_init, self.kmin,
-                            self.kfix, self.a, self.k, self.pot, self.t, self.lev, self.nthreads)
+                            self.kfix, self.a, self.k, self.pot, self.t, self.lev, self.nthreads,
+                            self.summation)
         if rc != 0:
             raise RuntimeError("oracle init failed: %d" % rc)
         self._act = np.zeros(self.n, dtype=np.int32)
@@ -210,7 +267,8 @@ class Integrator:
         pot = np.zeros(self.n)
         na = lib().orc_step(self.n, self.m, self.eps, self.eta, self.kmin, self.kfix, t_end,
                             self.x, self.v, self.a, self.k, self.t, self.lev, self._act,
-                            ctypes.byref(tn), pot.ctypes.data_as(ctypes.c_void_p), self.nthreads)
+                            ctypes.byref(tn), pot.ctypes.data_as(ctypes.c_void_p), self.nthreads,
+                            self.summation)
         if na < 0:
             raise RuntimeError("oracle step failed: %d" % na)
         act = self._act[:na].copy()
@@ -226,7 +284,7 @@ class Integrator:
         steps = lib().orc_run(self.n, self.m, self.eps, self.eta, self.kmin, self.kfix,
                               t_end_ticks, cap, self.x, self.v, self.a, self.k, self.t, self.lev,
                               hist.ctypes.data_as(ctypes.c_void_p), ctypes.byref(inter),
-                              self.nthreads)
+                              self.nthreads, self.summation)
         if steps < 0:
             raise RuntimeError("oracle run failed: %d" % steps)
         return int(steps), int(inter.value), hist[:steps].copy()

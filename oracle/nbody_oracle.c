@@ -30,6 +30,13 @@
  *  - Initial step: eta_init * |a| / |k| quantised like every other step.
  *  - A step may halve as often as needed, but double only once per step and
  *    only when the new time is a multiple of the doubled step.
+ *
+ * The end of the file adds the summation variants of Section 6 (GRAPE-6's
+ * 64-bit fixed-point sums; FP32 sums in index order and smallest force
+ * first).  They are defined on single-precision pair terms, whose every
+ * operation is spelled out there, so that a GPU evaluating the same IEEE
+ * operations gives the same bits; the integrator takes the summation as an
+ * argument (0 = the FP64 definition above).
  */
 #include <math.h>
 #include <stdint.h>
@@ -254,20 +261,28 @@ int orc_next_level(int k_old, int k_q, int64_t t_new, int kmin)
     return k_old;
 }
 
+/* Force with the summation the integrator was asked for (see the summation
+ * variants at the end of this file); mode 0 is orc_force itself. */
+static void orc_force_mode(int mode, int64_t n, const double *m, const double *x, const double *v,
+                           double eps, int64_t n_act, const int32_t *idx, double *acc,
+                           double *jerk, double *pot, int nthreads);
+
 /*
  * Start-up: full force at t = 0 on every particle, then the initial step.
- * With kfix > 0 every particle gets the shared level kfix instead.
+ * With kfix > 0 every particle gets the shared level kfix instead.  sum_mode
+ * selects the force's summation (0: FP64, otherwise a summation variant).
  * Arrays are [n][3] (x, v, a, k), [n] ticks t and levels lev.
  */
 int orc_init(int64_t n, const double *m, const double *x, const double *v, double eps,
              double eta_init, int kmin, int kfix, double *a, double *k, double *pot,
-             int64_t *t, int32_t *lev, int nthreads)
+             int64_t *t, int32_t *lev, int nthreads, int sum_mode)
 {
     if (n < 1 || eps < 0.0 || kmin < 0 || kmin > ORC_TICK_BITS) return ORC_EINVAL;
+    if (sum_mode < 0 || sum_mode > 3) return ORC_EINVAL;
     int32_t *all = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     if (!all) return ORC_ENOMEM;
     for (int64_t i = 0; i < n; i++) all[i] = (int32_t)i;
-    orc_force(n, m, x, v, eps, n, all, a, k, pot, nthreads);
+    orc_force_mode(sum_mode, n, m, x, v, eps, n, all, a, k, pot, nthreads);
     free(all);
     int rc = ORC_OK;
     for (int64_t i = 0; i < n; i++) {
@@ -310,7 +325,7 @@ int64_t orc_next_time(int64_t n, const int64_t *t, const int32_t *lev)
 int64_t orc_step(int64_t n, const double *m, double eps, double eta, int kmin, int kfix,
                  int64_t t_end, double *x, double *v, double *a, double *k,
                  int64_t *t, int32_t *lev, int32_t *act, int64_t *t_next_out,
-                 double *pot_out, int nthreads)
+                 double *pot_out, int nthreads, int sum_mode)
 {
     int64_t tn = orc_next_time(n, t, lev);
     *t_next_out = tn;
@@ -333,7 +348,7 @@ int64_t orc_step(int64_t n, const double *m, double eps, double eta, int kmin, i
         orc_predict_one(x + 3 * j, v + 3 * j, a + 3 * j, k + 3 * j,
                         orc_ticks_to_time(tn - t[j]), xp + 3 * j, vp + 3 * j);
 
-    orc_force(n, m, xp, vp, eps, na, act, anew, knew, pnew, nthreads);
+    orc_force_mode(sum_mode, n, m, xp, vp, eps, na, act, anew, knew, pnew, nthreads);
 
     int64_t rc = na;
     for (int64_t s = 0; s < na; s++) {
@@ -368,7 +383,8 @@ int64_t orc_step(int64_t n, const double *m, double eps, double eta, int kmin, i
  */
 int64_t orc_run(int64_t n, const double *m, double eps, double eta, int kmin, int kfix,
                 int64_t t_end, int64_t max_steps, double *x, double *v, double *a, double *k,
-                int64_t *t, int32_t *lev, int32_t *hist_nact, int64_t *interactions, int nthreads)
+                int64_t *t, int32_t *lev, int32_t *hist_nact, int64_t *interactions, int nthreads,
+                int sum_mode)
 {
     int32_t *act = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     if (!act) return ORC_ENOMEM;
@@ -376,7 +392,7 @@ int64_t orc_run(int64_t n, const double *m, double eps, double eta, int kmin, in
     while (steps < max_steps) {
         int64_t tn;
         int64_t na = orc_step(n, m, eps, eta, kmin, kfix, t_end, x, v, a, k, t, lev, act, &tn,
-                              NULL, nthreads);
+                              NULL, nthreads, sum_mode);
         if (na < 0) { free(act); return na; }
         if (na == 0) break;
         if (hist_nact) hist_nact[steps] = (int32_t)na;
@@ -549,4 +565,278 @@ int orc_traj_vjp(int64_t n, const double *m, double *x, double *v, double eps, d
     free(st); free(xp); free(vp); free(a1); free(k1); free(pot); free(ab); free(kb);
     free(a1b); free(k1b); free(xg); free(vg); free(mg); free(all);
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * Summation variants (Section 6 on accuracy).  The paper notes that the
+ * GRAPE-6 accumulates the pair forces in 64-bit fixed point while the GPU
+ * sums in single precision, and that summing the smallest forces first would
+ * make the GPU's sums more accurate.  Three summations of the same
+ * single-precision pair terms are defined here:
+ *   ORC_SUM_FIXED       every term rounded to 64-bit fixed point and summed
+ *                       exactly (GRAPE-style; independent of the order of j);
+ *   ORC_SUM_FP32        FP32 running sum in increasing j;
+ *   ORC_SUM_FP32_SORTED FP32 running sum, smallest pair force first.
+ *
+ * The terms are those of the Appendix A kernel evaluated on the single-
+ * precision record of every particle: position as hi = fl32(x),
+ * lo = fl32(x - hi); velocity fl32(v); mass fl32(m); softening
+ * eps2 = fl32(eps * eps).  Each operation below is one IEEE single-precision
+ * operation rounded to nearest, in the order written (this file is compiled
+ * without contraction), so any IEEE implementation of the same sequence gives
+ * the same bits:
+ *   dx   = (xj_hi - xi_hi) + (xj_lo - xi_lo),   u = vj - vi       (per axis)
+ *   d2   = (dx0 dx0 + dx1 dx1) + dx2 dx2,        r2 = d2 + eps2
+ *   rv   = (dx0 u0 + dx1 u1) + dx2 u2
+ *   rinv = 1 / sqrt(r2),  rinv2 = rinv rinv,  mr = mj rinv,  mr3 = mr rinv2
+ *   b    = (-3 rv) rinv2
+ *   acc  = (mr3 Sa) dx,   jerk = (mr3 Sk) (u + b dx),   pot = -(mr Sp)
+ *   key  = min(mr3 sqrt(d2), FLT_MAX)        (the pair force |m_j dx / r^3|)
+ * with Sa = Sk = Sp = 1 for the FP32 sums and powers of two for fixed point.
+ * A pair contributes nothing when j = i or r2 = 0 (eps = 0 and coincident
+ * particles).
+ */
+#include <float.h>
+
+#define ORC_SUM_FP64 0
+#define ORC_SUM_FIXED 1
+#define ORC_SUM_FP32 2
+#define ORC_SUM_FP32_SORTED 3
+
+typedef struct {
+    float hi[3], lo[3], v[3], m;
+} orc_rec32;
+
+static void orc_rec32_of(const double *x, const double *v, double m, orc_rec32 *r)
+{
+    for (int c = 0; c < 3; c++) {
+        r->hi[c] = (float)x[c];
+        r->lo[c] = (float)(x[c] - (double)r->hi[c]);
+        r->v[c] = (float)v[c];
+    }
+    r->m = (float)m;
+}
+
+/* The pair terms t[0..6] (acc xyz, jerk xyz, pot) of j on i and the pair's
+ * key; returns 0 for a pair that contributes nothing (r2 = 0). */
+static int orc_pair32(const orc_rec32 *pi, const orc_rec32 *pj, float eps2, const float sc[3],
+                      float t[7], float *key)
+{
+    float dx[3], u[3];
+    for (int c = 0; c < 3; c++) {
+        dx[c] = (pj->hi[c] - pi->hi[c]) + (pj->lo[c] - pi->lo[c]);
+        u[c] = pj->v[c] - pi->v[c];
+    }
+    float d2 = (dx[0] * dx[0] + dx[1] * dx[1]) + dx[2] * dx[2];
+    float r2 = d2 + eps2;
+    if (r2 == 0.0f) return 0;
+    float rv = (dx[0] * u[0] + dx[1] * u[1]) + dx[2] * u[2];
+    float rinv = 1.0f / sqrtf(r2);
+    float rinv2 = rinv * rinv;
+    float mr = pj->m * rinv;
+    float mr3 = mr * rinv2;
+    float b = (-3.0f * rv) * rinv2;
+    float fa = mr3 * sc[0], fk = mr3 * sc[1], fp = mr * sc[2];
+    for (int c = 0; c < 3; c++) {
+        t[c] = fa * dx[c];
+        t[3 + c] = fk * (u[c] + b * dx[c]);
+    }
+    t[6] = -fp;
+    if (key) *key = fminf(mr3 * sqrtf(d2), FLT_MAX);
+    return 1;
+}
+
+/* Smallest e with x < 2^e for a float x >= 0, read from its exponent field
+ * (-126 for zero and subnormals). */
+static int orc_exp_above(float x)
+{
+    uint32_t b;
+    memcpy(&b, &x, sizeof b);
+    int be = (int)((b >> 23) & 0xFF);
+    return be == 0 ? -126 : be - 126;
+}
+
+static int orc_floor_half(int a) { return a >= 0 ? a / 2 : -((1 - a) / 2); }
+
+/*
+ * Fixed-point scales 2^s (s[0] acc, s[1] jerk, s[2] pot) for the system
+ * m[n], v[n][3], eps.  Every term must stay below 2^56 in fixed-point units,
+ * so that 64 of them sum without overflow in 64 bits.  With
+ *   eps2 >= 2^F (F from eps2's exponent field; eps2 must be a normal float),
+ *   m_j < 2^Em, |vx| + |vy| + |vz| < 2^Ev for every particle (fl32 values;
+ *   Em, Ev at least -64),
+ * the terms obey |acc| <= m_j / r^2 < 2^(Em - F), |pot| = m_j / r <
+ * 2^(Em - floor(F/2)) and |jerk| <= 4 m_j |dv| / r^3 < 2^(3 + Em + Ev -
+ * floor(3F/2)) (|dv| <= 2 max |v|, r >= eps), up to single-precision
+ * rounding, which the factor 2 between 2^56 and 2^57 absorbs.  Then
+ * s = 56 - e, at most 126.  Returns ORC_EINVAL when eps2 is zero, subnormal
+ * or infinite, or a scale falls below -126.
+ */
+int orc_fixed_scales(int64_t n, const double *m, const double *v, double eps, int s[3])
+{
+    float eps2 = (float)(eps * eps);
+    uint32_t eb;
+    memcpy(&eb, &eps2, sizeof eb);
+    int be = (int)((eb >> 23) & 0xFF);
+    if (be == 0 || be == 255) return ORC_EINVAL;
+    int F = be - 127;
+    float mmax = 0.0f, vmax = 0.0f;
+    for (int64_t j = 0; j < n; j++) {
+        float mf = (float)m[j];
+        float v1 = (fabsf((float)v[3 * j]) + fabsf((float)v[3 * j + 1])) + fabsf((float)v[3 * j + 2]);
+        if (mf > mmax) mmax = mf;
+        if (v1 > vmax) vmax = v1;
+    }
+    int Em = orc_exp_above(mmax), Ev = orc_exp_above(vmax);
+    if (Em < -64) Em = -64;
+    if (Ev < -64) Ev = -64;
+    int e[3] = {Em - F, 3 + Em + Ev - orc_floor_half(3 * F), Em - orc_floor_half(F)};
+    for (int q = 0; q < 3; q++) {
+        s[q] = 56 - e[q];
+        if (s[q] > 126) s[q] = 126;
+        if (s[q] < -126) return ORC_EINVAL;
+    }
+    return ORC_OK;
+}
+
+/* An exact integer as a double: |y| = H 2^64 + L, then fl64(fl64(H) 2^64 +
+ * fl64(L)) with y's sign.  (gcc's 128-bit integers hold the exact sums.) */
+static double orc_i128_to_double(__int128 y)
+{
+    int neg = y < 0;
+    unsigned __int128 u = neg ? -(unsigned __int128)y : (unsigned __int128)y;
+    uint64_t H = (uint64_t)(u >> 64), L = (uint64_t)u;
+    double d = (double)H * 0x1p64 + (double)L;
+    return neg ? -d : d;
+}
+
+typedef struct {
+    uint32_t key;  /* bits of the non-negative key: their order is the keys' order */
+    int32_t j;
+} orc_keyed;
+
+static int orc_keyed_cmp(const void *pa, const void *pb)
+{
+    const orc_keyed *a = (const orc_keyed *)pa, *b = (const orc_keyed *)pb;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return a->j < b->j ? -1 : (a->j > b->j);
+}
+
+/*
+ * acc, jerk, pot on the listed i with one of the summation variants above
+ * (mode ORC_SUM_FIXED, ORC_SUM_FP32 or ORC_SUM_FP32_SORTED).
+ *   fixed:  Y_q = sum_j round_half_even(t_q,j) exactly, with the scales of
+ *           orc_fixed_scales over all n particles; result Y_q 2^-s_q.
+ *   fp32:   S = 0; S = fl32(S + t_j) for j = 0, 1, ..., n - 1.
+ *   sorted: the same running sum over j in increasing key, ties in
+ *           increasing j.
+ * Returns ORC_EINVAL for a bad mode or (fixed) unusable scales.
+ */
+int orc_force_summed(int mode, int64_t n, const double *m, const double *x, const double *v,
+                     double eps, int64_t n_act, const int32_t *idx, double *acc, double *jerk,
+                     double *pot, int nthreads)
+{
+    if (mode != ORC_SUM_FIXED && mode != ORC_SUM_FP32 && mode != ORC_SUM_FP32_SORTED)
+        return ORC_EINVAL;
+    int s[3] = {0, 0, 0};
+    if (mode == ORC_SUM_FIXED && orc_fixed_scales(n, m, v, eps, s) != ORC_OK) return ORC_EINVAL;
+    float sc[3] = {1.0f, 1.0f, 1.0f};
+    for (int q = 0; q < 3; q++) sc[q] = ldexpf(1.0f, s[q]);
+    const float eps2 = (float)(eps * eps);
+    orc_rec32 *rec = (orc_rec32 *)malloc(sizeof(orc_rec32) * (size_t)(n > 0 ? n : 1));
+    if (!rec) return ORC_ENOMEM;
+    for (int64_t j = 0; j < n; j++) orc_rec32_of(x + 3 * j, v + 3 * j, m[j], &rec[j]);
+    int failed = 0;
+    orc_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t a = 0; a < n_act; a++) {
+        int64_t i = idx[a];
+        float t[7];
+        double out[7];
+        if (mode == ORC_SUM_FIXED) {
+            __int128 Y[7] = {0, 0, 0, 0, 0, 0, 0};
+            for (int64_t j = 0; j < n; j++) {
+                if (j == i || !orc_pair32(&rec[i], &rec[j], eps2, sc, t, NULL)) continue;
+                for (int q = 0; q < 7; q++) Y[q] += (__int128)llrintf(t[q]);
+            }
+            for (int q = 0; q < 7; q++)
+                out[q] = orc_i128_to_double(Y[q]) * ldexp(1.0, -s[q < 3 ? 0 : (q < 6 ? 1 : 2)]);
+        } else {
+            float S[7] = {0, 0, 0, 0, 0, 0, 0};
+            if (mode == ORC_SUM_FP32) {
+                for (int64_t j = 0; j < n; j++) {
+                    if (j == i || !orc_pair32(&rec[i], &rec[j], eps2, sc, t, NULL)) continue;
+                    for (int q = 0; q < 7; q++) S[q] = S[q] + t[q];
+                }
+            } else {
+                orc_keyed *ord = (orc_keyed *)malloc(sizeof(orc_keyed) * (size_t)(n > 0 ? n : 1));
+                if (!ord) {
+#pragma omp atomic write
+                    failed = 1;
+                    continue;
+                }
+                int64_t cnt = 0;
+                for (int64_t j = 0; j < n; j++) {
+                    float key;
+                    if (j == i || !orc_pair32(&rec[i], &rec[j], eps2, sc, t, &key)) continue;
+                    memcpy(&ord[cnt].key, &key, sizeof key);
+                    ord[cnt].j = (int32_t)j;
+                    cnt++;
+                }
+                qsort(ord, (size_t)cnt, sizeof(orc_keyed), orc_keyed_cmp);
+                for (int64_t q2 = 0; q2 < cnt; q2++) {
+                    orc_pair32(&rec[i], &rec[ord[q2].j], eps2, sc, t, NULL);
+                    for (int q = 0; q < 7; q++) S[q] = S[q] + t[q];
+                }
+                free(ord);
+            }
+            for (int q = 0; q < 7; q++) out[q] = (double)S[q];
+        }
+        for (int c = 0; c < 3; c++) {
+            acc[3 * a + c] = out[c];
+            jerk[3 * a + c] = out[3 + c];
+        }
+        pot[a] = out[6];
+    }
+    free(rec);
+    return failed ? ORC_ENOMEM : ORC_OK;
+}
+
+/* The pair terms (scaled as the fixed-point sum scales them when `scaled`)
+ * and keys of every j on particle i: t[n][7], key[n], ok[n] (0 for j = i and
+ * pairs that contribute nothing).  Exposed so that tests can redo the
+ * summations independently. */
+int orc_pair_terms32(int64_t n, const double *m, const double *x, const double *v, double eps,
+                     int64_t i, int scaled, float *t, float *key, int32_t *ok)
+{
+    int s[3] = {0, 0, 0};
+    if (scaled && orc_fixed_scales(n, m, v, eps, s) != ORC_OK) return ORC_EINVAL;
+    float sc[3];
+    for (int q = 0; q < 3; q++) sc[q] = ldexpf(1.0f, s[q]);
+    const float eps2 = (float)(eps * eps);
+    orc_rec32 ri, rj;
+    orc_rec32_of(x + 3 * i, v + 3 * i, m[i], &ri);
+    for (int64_t j = 0; j < n; j++) {
+        orc_rec32_of(x + 3 * j, v + 3 * j, m[j], &rj);
+        ok[j] = j != i && orc_pair32(&ri, &rj, eps2, sc, t + 7 * j, key + j);
+        if (!ok[j]) {
+            for (int q = 0; q < 7; q++) t[7 * j + q] = 0.0f;
+            key[j] = 0.0f;
+        }
+    }
+    return ORC_OK;
+}
+
+static void orc_force_mode(int mode, int64_t n, const double *m, const double *x, const double *v,
+                           double eps, int64_t n_act, const int32_t *idx, double *acc,
+                           double *jerk, double *pot, int nthreads)
+{
+    if (mode == ORC_SUM_FP64) {
+        orc_force(n, m, x, v, eps, n_act, idx, acc, jerk, pot, nthreads);
+    } else if (orc_force_summed(mode, n, m, x, v, eps, n_act, idx, acc, jerk, pot, nthreads) != ORC_OK) {
+        for (int64_t a = 0; a < n_act; a++) {  /* unusable input: NaN results */
+            for (int c = 0; c < 3; c++) acc[3 * a + c] = jerk[3 * a + c] = NAN;
+            pot[a] = NAN;
+        }
+    }
 }

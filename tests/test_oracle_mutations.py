@@ -16,6 +16,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "nbody_oracle.c")
 PINS = ["tests/test_oracle_force.py", "tests/test_oracle_hermite.py", "tests/test_oracle_adjoint.py"]
+# mistakes in the summation variants only touch that code: their own pins suffice
+SUMMATION_PINS = ["tests/test_oracle_summation.py"]
+SUMMATION_PREFIXES = ("pair32_", "fixed_", "sorted_", "integrator_ignores_summation")
 
 MUTATIONS = {
     "force_sign_repulsive": ("dx[c] = x[3 * j + c] - x[3 * i + c];", "dx[c] = x[3 * i + c] - x[3 * j + c];"),
@@ -49,6 +52,23 @@ MUTATIONS = {
     "traj_corrector_coeff": ("double a3b = xbar[c] * dt * dt / 20.0", "double a3b = xbar[c] * dt * dt / 12.0"),
     "traj_k1b_sign": ("k1b[c] = kb[c] + a3b * dt - a2b * dt;", "k1b[c] = kb[c] + a3b * dt + a2b * dt;"),
     "traj_no_initial_force_vjp": ("        xbar[c] += xg[c];\n        vbar[c] += vg[c];\n", ""),
+    "pair32_lo_dropped": ("dx[c] = (pj->hi[c] - pi->hi[c]) + (pj->lo[c] - pi->lo[c]);",
+                          "dx[c] = pj->hi[c] - pi->hi[c];"),
+    "pair32_jerk_sign": ("t[3 + c] = fk * (u[c] + b * dx[c]);", "t[3 + c] = fk * (u[c] - b * dx[c]);"),
+    "pair32_b_coeff": ("float b = (-3.0f * rv) * rinv2;", "float b = (-2.0f * rv) * rinv2;"),
+    "pair32_no_softening": ("float r2 = d2 + eps2;", "float r2 = d2;"),
+    "pair32_key_softened_inverse_square": ("*key = fminf(mr3 * sqrtf(d2), FLT_MAX);",
+                                           "*key = fminf(mr * rinv, FLT_MAX);"),
+    "fixed_truncates": ("Y[q] += (__int128)llrintf(t[q]);", "Y[q] += (__int128)(long long)t[q];"),
+    "fixed_scale_off_by_one": ("s[q] = 56 - e[q];", "s[q] = 57 - e[q];"),
+    "fixed_jerk_floor_truncated": ("3 + Em + Ev - orc_floor_half(3 * F)", "3 + Em + Ev - (3 * F) / 2"),
+    "fixed_conversion_drops_sign": ("return neg ? -d : d;", "return d;"),
+    "fixed_pot_uses_jerk_scale": ("ldexp(1.0, -s[q < 3 ? 0 : (q < 6 ? 1 : 2)])", "ldexp(1.0, -s[q < 3 ? 0 : 1])"),
+    "sorted_descending": ("if (a->key != b->key) return a->key < b->key ? -1 : 1;",
+                          "if (a->key != b->key) return a->key > b->key ? -1 : 1;"),
+    "sorted_ties_reversed": ("return a->j < b->j ? -1 : (a->j > b->j);", "return a->j > b->j ? -1 : (a->j < b->j);"),
+    "integrator_ignores_summation": ("if (mode == ORC_SUM_FP64) {\n        orc_force(",
+                                     "if (1) {\n        orc_force("),
 }
 
 
@@ -62,7 +82,8 @@ def _run(name, tmpdir):
     subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
                     "-shared", "-o", lib, path, "-lm"], check=True)
     env = dict(os.environ, NBODY_ORACLE_LIB=lib, OMP_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
+    pins = SUMMATION_PINS if name.startswith(SUMMATION_PREFIXES) else PINS
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *pins],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return r.returncode
 
