@@ -59,7 +59,8 @@ def parse_args():
     p.add_argument("--impl", default="mine", choices=["mine", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT)
     p.add_argument("--no-extras", action="store_true", help="skip ladder, FP64 arm, e2e, CPU baseline")
-    p.add_argument("--workload", default="full_active_step", choices=["full_active_step", "blockstep", "adjoint", "ensemble", "replay"],
+    p.add_argument("--workload", default="full_active_step",
+                   choices=["full_active_step", "blockstep", "adjoint", "ensemble", "replay", "summation"],
                    help="blockstep: individual block steps of a Plummer run (Section 2 step loop)")
     p.add_argument("--t-end", type=float, default=0.25, help="blockstep: end time (multiple of dt_max)")
     p.add_argument("--eps", type=float, default=None, help="blockstep: softening (default 1/256)")
@@ -168,21 +169,22 @@ def fp32_peak_tflops(sms, mhz):
 
 
 FORCE_SOURCES = ("k_force.cu", "nb_device.cuh", "nb_internal.cuh")
+FIXED_SOURCES = ("k_sum.cu", "nb_device.cuh", "nb_internal.cuh")
 
 
-def force_sources_sha256():
-    """sha256 over the force kernel's sources, concatenated in FORCE_SOURCES order."""
+def force_sources_sha256(sources=FORCE_SOURCES):
+    """sha256 over a kernel's sources, concatenated in the order given."""
     h = hashlib.sha256()
-    for name in FORCE_SOURCES:
+    for name in sources:
         with open(os.path.join(ROOT, "paper_cs_0702135_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
 
 
-def force_traffic_per_launch(n):
+def force_traffic_per_launch(n, profile="k_force_ipar_ds.md", sources=FORCE_SOURCES):
     """DRAM bytes per full-N force launch from the committed ncu summary, or
     None when the kernel's sources changed since that capture."""
-    path = os.path.join(ROOT, "profiles", "k_force_ipar_ds.md")
+    path = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -190,7 +192,7 @@ def force_traffic_per_launch(n):
     mb = re.search(r"dram bytes per launch at N=(\d+):\s*([0-9.eE+]+)", text)
     if not mh or not mb:
         return None
-    if force_sources_sha256() != mh.group(1):
+    if force_sources_sha256(sources) != mh.group(1):
         return None
     # With the j records resident in L2 the kernel's DRAM traffic is O(N)
     # (records, block outputs), so a smaller capture scales linearly.
@@ -198,9 +200,10 @@ def force_traffic_per_launch(n):
     return b * n / n_cap
 
 
-def cpu_oracle_rate(m, x, v, eps, budget_s=10.0, seed=SEED):
+def cpu_oracle_rate(m, x, v, eps, budget_s=10.0, seed=SEED, summation=0):
     """Oracle direct-sum force (OpenMP over i) on a growing sample of active i
-    against all N j until one timing takes at least budget_s seconds."""
+    against all N j until one timing takes at least budget_s seconds
+    (summation > 0: the oracle's summation variant of that number)."""
     import oracle
     from synth import sample_active
     threads = os.cpu_count() or 1
@@ -210,7 +213,10 @@ def cpu_oracle_rate(m, x, v, eps, budget_s=10.0, seed=SEED):
     while True:
         idx = sample_active(n, na, seed + na)
         t0 = time.perf_counter()
-        oracle.force(m, x, v, eps, idx, nthreads=threads)
+        if summation:
+            oracle.force_summed(m, x, v, eps, idx, mode=summation, nthreads=threads)
+        else:
+            oracle.force(m, x, v, eps, idx, nthreads=threads)
         dt = time.perf_counter() - t0
         if dt >= budget_s or na >= n:
             break
@@ -398,8 +404,21 @@ def run_extras(args, nb, ctx, m, x, v, stream, dev, torch, sample_active):
     out["fp64_gpu"] = {"value": r64, "unit": UNIT, "sample": "%d active i against all %d j" % (na, n),
                        "ds_over_fp64": (rds / r64) if rds else None}
 
-    # End to end through the host-buffer API: per step nb_predict, nb_force with
-    # pinned host index/output arrays, nb_correct; copies inside the timed region.
+    out["e2e"] = e2e_host_api(ctx, nb, n, max(2, min(args.steps, 3)), torch, dev)
+
+    # The CPU oracle on a bounded sample of the same workload.
+    if int(os.environ.get("WORLD_SIZE", "1")) == 1:
+        rate, threads, na_s, secs = cpu_oracle_rate(m, x, v, EPS)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": "oracle direct-sum force (FP64, OpenMP) on %d of the %d "
+                                         "active i against all j, %.1f s" % (na_s, n, secs)}
+    return out
+
+
+def e2e_host_api(ctx, nb, n, k_e2e, torch, dev):
+    """End to end through the host-buffer API: per full-active step nb_predict,
+    nb_force with pinned host index/output arrays, nb_correct; the copies are
+    inside the timed region."""
     st0 = ctx.nb_get_state()
     t_cur = int(st0["t"].max())
     dt = 1 << (40 - LEVEL)
@@ -407,7 +426,6 @@ def run_extras(args, nb, ctx, m, x, v, stream, dev, torch, sample_active):
     acc_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
     jerk_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
     pot_h = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
-    k_e2e = max(2, min(args.steps, 3))
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for s in range(k_e2e):
@@ -417,17 +435,9 @@ def run_extras(args, nb, ctx, m, x, v, stream, dev, torch, sample_active):
         ctx.nb_correct(idx_h, t_cur / nb.TICKS_PER_UNIT)
     torch.cuda.synchronize(dev)
     el = time.perf_counter() - t0
-    out["e2e"] = {"value": k_e2e * n * (n - 1) / el, "unit": UNIT,
-                  "h2d_bytes_per_step": 2 * 4 * n, "d2h_bytes_per_step": (3 + 3 + 1) * 8 * n,
-                  "steps": k_e2e, "api": "nb_predict + nb_force (host arrays) + nb_correct"}
-
-    # The CPU oracle on a bounded sample of the same workload.
-    if int(os.environ.get("WORLD_SIZE", "1")) == 1:
-        rate, threads, na_s, secs = cpu_oracle_rate(m, x, v, EPS)
-        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-                               "sample": "oracle direct-sum force (FP64, OpenMP) on %d of the %d "
-                                         "active i against all j, %.1f s" % (na_s, n, secs)}
-    return out
+    return {"value": k_e2e * n * (n - 1) / el, "unit": UNIT,
+            "h2d_bytes_per_step": 2 * 4 * n, "d2h_bytes_per_step": (3 + 3 + 1) * 8 * n,
+            "steps": k_e2e, "api": "nb_predict + nb_force (host arrays) + nb_correct"}
 
 
 def run_blockstep(args):
@@ -750,6 +760,167 @@ def run_replay(args):
     print(json.dumps({"workload": "paper_tab_results_replay", "eps": 1.0 / 256, "rows": rows}), flush=True)
 
 
+SUMMATIONS = (("compensated", 0), ("fixed", 1), ("fp32", 2), ("fp32_sorted", 3))
+ACCURACY_SAMPLE = 256
+
+
+def _rel_err_stats(got, ref):
+    out = {}
+    for name, g, r in zip(("acc", "jerk", "pot"), got, ref):
+        g, r = np.asarray(g).reshape(len(r), -1), np.asarray(r).reshape(len(r), -1)
+        e = np.linalg.norm(g - r, axis=1) / np.linalg.norm(r, axis=1)
+        out[name] = {"median": float(np.median(e)), "p99": float(np.percentile(e, 99)),
+                     "max": float(e.max())}
+    return out
+
+
+def run_summation(args):
+    """Summation variants (Section 6).  The timed step is the full-active block
+    step of the default workload with GRAPE-style 64-bit fixed-point sums of
+    the single-precision pair terms; beside it, every variant's force time and
+    accuracy against the FP64 oracle on sampled particles, and the property
+    that fixed point buys: bit-identical forces under a permutation of the
+    particles and another j slicing."""
+    import torch
+    import oracle
+    import paper_cs_0702135_gb300 as nb
+    from synth import plummer, sample_active
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    n = args.n
+    inter_per_step = n * (n - 1)
+
+    m, x, v = plummer(n, SEED + rank)
+    ctx = nb.Context(m, x, v, EPS, level_fixed=LEVEL, stream=stream.cuda_stream,
+                     summation=nb.NB_SUM_FIXED)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    e0 = sum(ctx.nb_energy())
+    for _ in range(args.warmup):
+        flush.zero_()
+        ctx.nb_step(wait=False)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(nvsmi_index(local))
+    ctx.nb_get_stats(reset=True)
+    ctx.nb_set_profiling(True)
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()
+        ctx.nb_step(wait=False)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    stats = ctx.nb_get_stats(reset=True)
+    ctx.nb_set_profiling(False)
+    if world > 1:
+        elapsed = max_over_ranks(elapsed, dev)
+        torch.distributed.barrier()
+    e1 = sum(ctx.nb_energy())
+    value = whole_job_rate(world, args.steps, inter_per_step, elapsed)
+
+    force_s = stats["force_ms"] / 1e3 / max(1, stats["force_launches"])
+    peak = fp32_peak_tflops(sms, MAX_SM_MHZ_FALLBACK)
+    achieved = FLOP_PER_INTERACTION * inter_per_step / force_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "traffic": force_traffic_per_launch(n, "k_force_fixed.md", FIXED_SOURCES),
+                "kernel": "k_force_fixed (full-N launch inside the step, with the bounds "
+                          "reduction and combine around it)",
+                "peak_note": "FP32 FMA peak 2 x 128 lanes x %d SMs x 2070 MHz (max SM clock); "
+                             "achieved counts 60 flop per interaction although the variant issues "
+                             "about 130 instructions per pair" % sms}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_measured_clock"] = achieved / fp32_peak_tflops(sms, clocks["sm_mhz"])
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        # every variant: force time on its own sample, accuracy on a common one
+        idx_acc = sample_active(n, min(ACCURACY_SAMPLE, n), SEED + 17)
+        ref = oracle.force(m, x, v, EPS, idx_acc, nthreads=os.cpu_count() or 1)
+        variants, fixed_acc = {}, None
+        for name, mode in SUMMATIONS:
+            c = nb.Context(m, x, v, EPS, flags=nb.NB_INIT_NO_FORCE, stream=stream.cuda_stream,
+                           summation=mode)
+            na = {0: n, 1: n, 2: min(n, 4096), 3: min(n, 256)}[mode]
+            idx = torch.from_numpy(sample_active(n, na, SEED + na)).to(dev)
+            acc = torch.empty((na, 3), dtype=torch.float64, device=dev)
+            jerk, pot = torch.empty_like(acc), torch.empty(na, dtype=torch.float64, device=dev)
+            c.nb_force_dev(idx, na, acc, jerk, pot)
+            c.nb_get_stats(reset=True)
+            c.nb_set_profiling(True)
+            for _ in range(2):
+                c.nb_force_dev(idx, na, acc, jerk, pot)
+            st = c.nb_get_stats(reset=True)
+            fs = st["force_ms"] / 1e3 / max(1, st["force_launches"])
+            got = c.nb_force(idx_acc)
+            if mode == 1:
+                fixed_acc = got
+            c.nb_free()
+            variants[name] = {"force_ms": fs * 1e3, "n_active": na,
+                              "interactions_per_s": na * (n - 1) / fs,
+                              "rel_err_vs_fp64": _rel_err_stats(got, ref)}
+        # fixed point: the same bits for a permuted system sliced another way
+        perm = np.random.default_rng(SEED).permutation(n)
+        inv = np.argsort(perm).astype(np.int32)
+        c = nb.Context(m[perm], x[perm], v[perm], EPS, flags=nb.NB_INIT_NO_FORCE,
+                       stream=stream.cuda_stream, summation=nb.NB_SUM_FIXED, split_j=7)
+        got_p = c.nb_force(inv[idx_acc])
+        c.nb_free()
+        same = all(np.array_equal(a, b) for a, b in zip(got_p, fixed_acc))
+        extras["summation_variants"] = variants
+        extras["fixed_bit_identical_under_permutation_and_split"] = bool(same)
+        extras["accuracy_sample"] = "%d i drawn uniformly (seed %d) against all %d j, vs the FP64 oracle" % (
+            len(idx_acc), SEED + 17, n)
+        extras["e2e"] = e2e_host_api(ctx, nb, n, max(2, min(args.steps, 3)), torch, dev)
+        if world == 1:
+            rate, threads, na_s, secs = cpu_oracle_rate(m, x, v, EPS, summation=oracle.SUM_FIXED)
+            extras["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                      "sample": "oracle fixed-point summation variant (OpenMP) on %d "
+                                                "of the %d active i against all j, %.1f s" % (na_s, n, secs)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "plummer_N%d_eps1/1024_full_active_block_step_fixed_point_sums" % n,
+                   "N": n, "eps": EPS, "seed": SEED, "n_active": n, "shared_level": LEVEL,
+                   "summation": "NB_SUM_FIXED: IEEE single-precision pair terms on double-single "
+                                "positions, 64-bit fixed-point rounding, exact 128-bit sums",
+                   "l2": "inputs larger than L2 and a 256 MiB memset between steps inside the "
+                         "timed region",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "gflops": value * FLOP_PER_INTERACTION / 1e9,
+        "pct_fp32_peak": 100.0 * value * FLOP_PER_INTERACTION / 1e12 / peak,
+        "energy": {"rel_err": abs(e1 - e0) / abs(e0), "steps": args.warmup + args.steps,
+                   "dt": 2.0 ** -LEVEL},
+        "roofline": roofline,
+        "gpu_launches": stats["kernel_launches"],
+        "clocks": clocks,
+        "device": {"name": props.name, "sms": sms},
+    }
+    line.update(extras)
+    ctx.nb_free()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -762,6 +933,8 @@ def main():
         run_ensemble(args)
     elif args.workload == "replay":
         run_replay(args)
+    elif args.workload == "summation":
+        run_summation(args)
     else:
         run_mine(args)
 

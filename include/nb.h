@@ -46,6 +46,37 @@ extern "C" {
                           * small-block variant, one i per thread, serves n_active <= 192) */
 #define NB_FORCE_JPAR 2  /* j across threads, warp-shuffle tree reduction (small n_active) */
 
+/*
+ * Summation of the force (nb_opts.summation; precision NB_DS only).  Section
+ * 6 compares GRAPE-6, which accumulates pair forces in 64-bit fixed point,
+ * with the GPU's single-precision sums, and suggests adding the smallest
+ * forces first.  The variants other than the default evaluate every pair term
+ * in single precision with IEEE round-to-nearest operations in a fixed order
+ * (no fused multiply-add, correctly rounded square root and reciprocal), so
+ * their results are reproducible bit for bit on any IEEE machine:
+ *   NB_SUM_COMPENSATED  default: FP32 pair terms (approximate 1/sqrt) summed
+ *                       in double-single with compensated additions; fastest.
+ *   NB_SUM_FIXED        each term rounded to 64-bit fixed point and summed
+ *                       exactly (GRAPE-style).  Results do not depend on the
+ *                       order of the particles, the j slicing or the kernel,
+ *                       and momentum is conserved exactly for equal masses.
+ *                       The fixed-point units are powers of two set from the
+ *                       largest mass, the largest |vx|+|vy|+|vz| and eps, so
+ *                       that no term or sum can overflow; requires eps^2 to be
+ *                       a normal single-precision number (eps >~ 1.1e-19).
+ *   NB_SUM_FP32         FP32 running sum over j in index order, one thread per
+ *                       active particle (a single-precision GPU summation).
+ *   NB_SUM_FP32_SORTED  FP32 running sum with the smallest pair force
+ *                       |m_j dx / r^3| first (ties in index order), after a
+ *                       per-particle sort; memory: 16 n bytes per resident CTA.
+ * force_mode and split_j only apply to NB_SUM_COMPENSATED and NB_SUM_FIXED
+ * (whose results split_j does not change).
+ */
+#define NB_SUM_COMPENSATED 0
+#define NB_SUM_FIXED 1
+#define NB_SUM_FP32 2
+#define NB_SUM_FP32_SORTED 3
+
 #define NB_TICK_BITS 40
 
 #define NB_INIT_NO_FORCE 1  /* nb_opts.flags: skip the t = 0 force sweep and initial steps */
@@ -61,6 +92,7 @@ typedef struct nb_opts {
     int force_mode;    /* NB_FORCE_AUTO (default), NB_FORCE_IPAR or NB_FORCE_JPAR */
     int split_j;       /* i-parallel kernel: number of j slices, 0 = automatic */
     int flags;         /* NB_INIT_NO_FORCE or 0 (default): see nb_init */
+    int summation;     /* NB_SUM_COMPENSATED (default), NB_SUM_FIXED, NB_SUM_FP32, NB_SUM_FP32_SORTED */
     void *stream;      /* cudaStream_t to run on; NULL = a non-blocking stream the context creates */
 } nb_opts;
 
@@ -76,7 +108,9 @@ void nb_default_opts(nb_opts *opts);
  * acceleration and jerk start at zero and every level at level_min, for
  * callers that only use nb_force or that load a state with nb_set_state.
  * Errors: NB_EINVAL (n < 1 or n > 2^31 - 1, eps < 0, non-finite input, bad
- * opts), NB_ENOMEM, NB_ECUDA, NB_ESTEP.  On error *ctx is NULL.
+ * opts, among them a summation other than NB_SUM_COMPENSATED with NB_FP64, or
+ * NB_SUM_FIXED with eps^2 not a normal single-precision number), NB_ENOMEM,
+ * NB_ECUDA, NB_ESTEP.  On error *ctx is NULL.
  */
 int nb_init(nb_ctx **ctx, int64_t n, const double *m, const double *x, const double *v,
             double eps, const nb_opts *opts);
@@ -101,8 +135,10 @@ int nb_predict(nb_ctx *ctx, double t);
  * evaluated at the state of the last nb_predict (or nb_init).  Outputs are
  * host arrays acc[n_active][3], jerk[n_active][3], pot[n_active] (any may be
  * NULL), in the order of active_idx.  The results are also kept for
- * nb_correct.  Errors: NB_EINVAL (n_active out of [0, n], index out of range
- * or repeated), NB_ECUDA.
+ * nb_correct.  The summation is the context's nb_opts.summation.  Errors:
+ * NB_EINVAL (n_active out of [0, n], index out of range or repeated; with
+ * NB_SUM_FIXED, masses, velocities and eps so extreme that the fixed-point
+ * units leave the single-precision range), NB_ECUDA.
  */
 int nb_force(nb_ctx *ctx, const int32_t *active_idx, int32_t n_active, double *acc,
              double *jerk, double *pot);

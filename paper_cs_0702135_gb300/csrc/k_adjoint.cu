@@ -30,8 +30,6 @@ using namespace dev;
 
 constexpr int kVNT = 128;  // threads per CTA = partners per tile
 
-__device__ __forceinline__ int clamp_index(int i, int n) { return min(max(i, 0), n - 1); }
-
 // One particle's VJP record: (predicted) position and velocity, mass and the
 // cotangents of its acc and jerk, in the layout of the context's precision.
 __device__ __forceinline__ void write_vjp_record(int i, const double x[3], const double v[3], double m,

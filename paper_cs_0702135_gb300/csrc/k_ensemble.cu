@@ -506,6 +506,8 @@ int ens_init_impl(nb_ens *e, int32_t C, const int64_t *off, const double *m, con
     if (!std::isfinite(eps) || eps < 0.0) return efail(e, NB_EINVAL, "eps must be finite and >= 0");
     if (o.level_min < 0 || o.level_min > kTickBits || o.level_fixed != 0 || o.precision != NB_DS)
         return efail(e, NB_EINVAL, "ensembles use DS precision and individual block steps");
+    if (o.summation != NB_SUM_COMPENSATED)
+        return efail(e, NB_EINVAL, "ensembles use the compensated summation");
     if (!(o.eta > 0.0) || !(o.eta_init > 0.0)) return efail(e, NB_EINVAL, "eta must be positive");
     if (off[0] != 0) return efail(e, NB_EINVAL, "offsets must start at 0");
     std::vector<std::pair<long long, int>> sizes;

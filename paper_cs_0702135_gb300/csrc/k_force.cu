@@ -35,26 +35,6 @@ namespace {
 
 using namespace dev;
 
-__device__ __forceinline__ int read_na(const ForceArgs &fa)
-{
-    return fa.na_dev ? *fa.na_dev : fa.na_host;
-}
-
-__device__ __forceinline__ void store_result(const ForceOut &o, int a, const double r[kComp])
-{
-    if (o.acc) {
-        o.acc[3 * (long long)a + 0] = r[0];
-        o.acc[3 * (long long)a + 1] = r[1];
-        o.acc[3 * (long long)a + 2] = r[2];
-    }
-    if (o.jerk) {
-        o.jerk[3 * (long long)a + 0] = r[3];
-        o.jerk[3 * (long long)a + 1] = r[4];
-        o.jerk[3 * (long long)a + 2] = r[5];
-    }
-    if (o.pot) o.pot[a] = r[6];
-}
-
 // One FP64 pair interaction.
 template <bool SOFT>
 __device__ __forceinline__ void pair_f64(const double4_32a &p, const double4_32a &w, const double xi[3],
@@ -85,7 +65,6 @@ __device__ __forceinline__ void pair_f64(const double4_32a &p, const double4_32a
     pot -= mr;
 }
 
-__device__ __forceinline__ int clamp_index(int i, int n) { return min(max(i, 0), n - 1); }
 
 // ----------------------------------------------------------------------------
 // DS, i-parallel.
@@ -427,18 +406,6 @@ __global__ void __launch_bounds__(NT) k_force_jpar_f64(ForceArgs fa, JF64 J)
 
 // ----------------------------------------------------------------------------
 // Slice combine: out = sum over slices in a fixed order (FP64).
-
-__device__ __forceinline__ void write_combined(const ForceOut &o, int c, int a, double s)
-{
-    if (c < 3) {
-        if (o.acc) o.acc[3 * (long long)a + c] = s;
-    } else if (c < 6) {
-        if (o.jerk) o.jerk[3 * (long long)a + (c - 3)] = s;
-    } else if (o.pot) {
-        o.pot[a] = s;
-    }
-}
-
 
 template <int IR, int IR64>
 __global__ void k_force_combine(ForceArgs fa, int precision)

@@ -44,6 +44,9 @@ struct nb_ctx {
     double *d_stage = nullptr;      // [7n] staging for host I/O
 
     int slots_ipar = 0, slots_jpar = 0, slots_small = 0, jpar_max = 0, small_max = 0;
+    SumArgs sum{};                  // summation variant (NB_SUM_COMPENSATED: unused)
+    unsigned *d_bounds = nullptr;   // fixed point: mass and velocity bounds
+    unsigned long long *d_sort = nullptr;  // sorted: keyed items, 2n per resident CTA
     long long t_pred = 0;           // ticks of the last host-driven prediction
     bool force_valid = false;       // results in d_res usable by nb_correct
     int force_na = 0;
@@ -146,6 +149,9 @@ int sync_ctrl(nb_ctx *c)
         CK(cudaStreamSynchronize(c->st));
         if (e == NB_ESTEP) return fail(c, NB_ESTEP, "a new time step fell below 2^-40");
         if (e == NB_EINVAL) return fail(c, NB_EINVAL, "invalid particle index (device check)");
+        if (e == kErrFixedScale)
+            return fail(c, NB_EINVAL, "fixed-point summation: masses, velocities or eps put the "
+                                      "fixed-point units outside the single-precision range");
         return fail(c, e, "device error %d", e);
     }
     return NB_OK;
@@ -207,6 +213,9 @@ void enqueue_force(nb_ctx *c, const int *act, int na_host, const int *na_dev, Fo
             gi = p.items < c->slots_ipar ? p.items : c->slots_ipar;
         }
     }
+    const bool summed = c->o.summation != NB_SUM_COMPENSATED;
+    const int gsum = summed ? grid_summed(fa, c->sum) : 0;
+    if (summed && gsum <= 0) return;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     const bool timed = c->profiling && !c->capturing;
     if (timed) {
@@ -220,11 +229,15 @@ void enqueue_force(nb_ctx *c, const int *act, int na_host, const int *na_dev, Fo
         }
         if (ev[0] && ev[1]) cudaEventRecord(ev[0], c->st);
     }
-    if (f64)
+    if (summed) {
+        c->launches += launch_force_summed(fa, c->jds, c->sum, gsum, c->st);
+    } else if (f64) {
         launch_force_f64(fa, c->jf, c->eps > 0.0, gi, gj, c->st);
-    else
+        c->launches += (gi > 0) + (gj > 0) + 1;
+    } else {
         launch_force_ds(fa, c->jds, c->eps > 0.0, gi, gj, gs, c->st);
-    c->launches += (gi > 0) + (gj > 0) + (gs > 0) + 1;
+        c->launches += (gi > 0) + (gj > 0) + (gs > 0) + 1;
+    }
     if (timed) {
         if (ev[0] && ev[1]) {
             cudaEventRecord(ev[1], c->st);
@@ -285,7 +298,7 @@ void release(nb_ctx *c)
                     c->d_act, c->d_idx, c->d_all, c->d_bitmap, c->d_ctrl, c->d_blockmin,
                     c->d_blockcnt, c->d_epart, c->d_stage, c->d_ck, c->d_seg, c->d_fin, c->d_tfin,
                     c->d_cot, c->vrec.ph, c->vrec.pl, c->vrec.v, c->vrec.ab, c->vrec.kb,
-                    c->vrec64.x, c->vrec64.v, c->vrec64.ab, c->vrec64.kb};
+                    c->vrec64.x, c->vrec64.v, c->vrec64.ab, c->vrec64.kb, c->d_bounds, c->d_sort};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
@@ -383,6 +396,7 @@ void nb_default_opts(nb_opts *o)
     o->force_mode = NB_FORCE_AUTO;
     o->split_j = 0;
     o->flags = 0;
+    o->summation = NB_SUM_COMPENSATED;
     o->stream = nullptr;
 }
 
@@ -423,6 +437,15 @@ static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, con
         return fail(c, NB_EINVAL, "bad force_mode");
     if (o.split_j < 0 || (o.flags & ~NB_INIT_NO_FORCE) != 0)
         return fail(c, NB_EINVAL, "bad split_j or flags");
+    if (o.summation < NB_SUM_COMPENSATED || o.summation > NB_SUM_FP32_SORTED)
+        return fail(c, NB_EINVAL, "bad summation");
+    if (o.summation != NB_SUM_COMPENSATED && o.precision != NB_DS)
+        return fail(c, NB_EINVAL, "summation variants need precision NB_DS");
+    if (o.summation == NB_SUM_FIXED) {
+        const float e2 = (float)(eps * eps);
+        if (!(e2 >= 0x1p-126f) || std::isinf(e2))
+            return fail(c, NB_EINVAL, "NB_SUM_FIXED needs eps^2 to be a normal single-precision number");
+    }
     if (!finite_all(m, n) || !finite_all(x, 3 * n) || !finite_all(v, 3 * n))
         return fail(c, NB_EINVAL, "non-finite input");
     for (int64_t i = 0; i < n; ++i)
@@ -452,6 +475,17 @@ static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, con
                   : o.force_mode == NB_FORCE_JPAR ? INT_MAX
                                                   : kJparMaxActive;
     c->small_max = f64 || o.force_mode == NB_FORCE_JPAR ? 0 : kSmallMaxActive;
+    if (o.summation != NB_SUM_COMPENSATED) {
+        int bsum = 0;
+        if (occupancy_sum(o.summation, &bsum)) return fail(c, NB_ECUDA, "occupancy query failed");
+        c->sum.mode = o.summation;
+        c->sum.slots = c->sms * (bsum > 0 ? bsum : 1);
+        if (o.summation == NB_SUM_FP32_SORTED) {
+            // keyed items: 16 n bytes per resident CTA, at most 4 GiB in all
+            const long long per = 16LL * n, cap = (4LL << 30) / per;
+            if (cap < c->sum.slots) c->sum.slots = (int)(cap > 0 ? cap : 1);
+        }
+    }
     const long long iblk = kIparNT * (f64 ? kIparR64 : kIparR);
     // Partials: up to 16 slots' worth of i-blocks, and four slices of all n.
     long long cap = 16LL * c->slots_ipar * iblk;
@@ -473,6 +507,13 @@ static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, con
         (rc = dalloc(c, &c->d_epart, 2LL * energy_blocks(c->n))) ||
         (rc = dalloc(c, &c->d_stage, 7 * N)))
         return rc;
+    if (o.summation == NB_SUM_FIXED) {
+        if ((rc = dalloc(c, &c->d_bounds, 2))) return rc;
+        c->sum.bounds = c->d_bounds;
+    } else if (o.summation == NB_SUM_FP32_SORTED) {
+        if ((rc = dalloc(c, &c->d_sort, 2LL * N * c->sum.slots))) return rc;
+        c->sum.scratch = c->d_sort;
+    }
     if (f64) {
         if ((rc = dalloc(c, &c->jf.pos, N)) || (rc = dalloc(c, &c->jf.vel, N))) return rc;
     } else {
@@ -569,7 +610,7 @@ int nb_force(nb_ctx *c, const int32_t *idx, int32_t na, double *acc, double *jer
         CK(cudaGetLastError());
         if ((rc = copy_results_out(c, na, acc, jerk, pot, cudaMemcpyDeviceToHost))) return rc;
     }
-    CK(cudaStreamSynchronize(c->st));
+    if ((rc = sync_ctrl(c))) return rc;
     c->force_valid = true;
     c->force_na = na;
     c->force_t = c->t_pred;

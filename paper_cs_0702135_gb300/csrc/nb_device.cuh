@@ -203,5 +203,42 @@ __device__ __forceinline__ void pair_ds(const float4 &p, const float4 &l, const 
     pot -= mr;
 }
 
+// Block size of a force launch: read on the device when the host does not know it.
+__device__ __forceinline__ int read_na(const ForceArgs &fa)
+{
+    return fa.na_dev ? *fa.na_dev : fa.na_host;
+}
+
+// Index loads of padding lanes are clamped into [0, n).
+__device__ __forceinline__ int clamp_index(int i, int n) { return min(max(i, 0), n - 1); }
+
+// One particle's acc, jerk, pot into the public output layout.
+__device__ __forceinline__ void store_result(const ForceOut &o, int a, const double r[kComp])
+{
+    if (o.acc) {
+        o.acc[3 * (long long)a + 0] = r[0];
+        o.acc[3 * (long long)a + 1] = r[1];
+        o.acc[3 * (long long)a + 2] = r[2];
+    }
+    if (o.jerk) {
+        o.jerk[3 * (long long)a + 0] = r[3];
+        o.jerk[3 * (long long)a + 1] = r[4];
+        o.jerk[3 * (long long)a + 2] = r[5];
+    }
+    if (o.pot) o.pot[a] = r[6];
+}
+
+// Component c (0-2 acc, 3-5 jerk, 6 pot) of output a.
+__device__ __forceinline__ void write_combined(const ForceOut &o, int c, int a, double s)
+{
+    if (c < 3) {
+        if (o.acc) o.acc[3 * (long long)a + c] = s;
+    } else if (c < 6) {
+        if (o.jerk) o.jerk[3 * (long long)a + (c - 3)] = s;
+    } else if (o.pot) {
+        o.pot[a] = s;
+    }
+}
+
 }  // namespace dev
 }  // namespace nbk

@@ -195,6 +195,32 @@ struct ForceArgs {
     int *err;                 // device error word
 };
 
+// Summation variants (k_sum.cu): the force with single-precision pair terms in
+// IEEE round-to-nearest arithmetic, summed in 64-bit fixed point (GRAPE-style,
+// independent of summation order), or in FP32 in index order, or in FP32
+// smallest pair force first.
+struct SumArgs {
+    int mode;                       // NB_SUM_FIXED, NB_SUM_FP32 or NB_SUM_FP32_SORTED
+    unsigned *bounds;               // [2] fixed point: largest fl32 mass, largest fl32 |vx|+|vy|+|vz| (bits)
+    unsigned long long *scratch;    // sorted: 2 n keyed items per resident CTA
+    int slots;                      // resident CTAs of the mode's force kernel
+};
+#ifndef NB_FIX_NT
+#define NB_FIX_NT 64
+#endif
+#ifndef NB_FIX_R
+#define NB_FIX_R 1
+#endif
+#ifndef NB_FIX_UNROLL
+#define NB_FIX_UNROLL 4
+#endif
+constexpr int kFixNT = NB_FIX_NT;   // fixed point: threads per CTA (= j per tile)
+constexpr int kFixR = NB_FIX_R;     // fixed point: i per thread
+constexpr int kFixUnroll = NB_FIX_UNROLL;  // fixed point: j unrolling of the inner loop
+constexpr int kSeqNT = 128;         // FP32 index order: threads per CTA, one i each
+constexpr int kSortNT = 1024;       // FP32 sorted: one CTA per i
+constexpr int kErrFixedScale = 64;  // device error word: fixed-point scales out of range
+
 // Reverse mode (k_adjoint.cu).  Force-VJP records: DS (x_hi, y_hi, z_hi, m),
 // (x_lo, y_lo, z_lo, 0), (vx, vy, vz, 0), (abar, 0), (kbar, 0); FP64 (x, y,
 // z, m), (v, 0), (abar, 0), (kbar, 0).
@@ -228,6 +254,12 @@ void launch_force_ds(const ForceArgs &fa, const JDS &j, bool softened, int grid_
 void launch_force_f64(const ForceArgs &fa, const JF64 &j, bool softened, int grid_ipar,
                       int grid_jpar, cudaStream_t st);
 int occupancy_force(int precision, int regime, int *blocks_per_sm);
+
+// k_sum.cu
+int occupancy_sum(int mode, int *blocks_per_sm);
+int grid_summed(const ForceArgs &fa, const SumArgs &sa);
+int launch_force_summed(const ForceArgs &fa, const JDS &j, const SumArgs &sa, int grid,
+                        cudaStream_t st);
 
 // k_step.cu
 void launch_predict(const State &s, long long t_val, const long long *t_ptr, const int *gate,

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_PKG, "libnb_gb300.so")
 NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ESTEP, NB_ETIMEOUT, NB_ESTATE = 0, -1, -2, -3, -4, -5, -6
 NB_DS, NB_FP64 = 0, 1
 NB_FORCE_AUTO, NB_FORCE_IPAR, NB_FORCE_JPAR = 0, 1, 2
+NB_SUM_COMPENSATED, NB_SUM_FIXED, NB_SUM_FP32, NB_SUM_FP32_SORTED = 0, 1, 2, 3
 NB_TICK_BITS = 40
 NB_INIT_NO_FORCE = 1
 NB_NOALLOC_MAX_ACTIVE = 64
@@ -43,7 +44,7 @@ class nb_opts(ctypes.Structure):
                 ("level_min", ctypes.c_int), ("level_fixed", ctypes.c_int),
                 ("precision", ctypes.c_int), ("force_mode", ctypes.c_int),
                 ("split_j", ctypes.c_int), ("flags", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("summation", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class nb_stats(ctypes.Structure):
@@ -142,7 +143,10 @@ def _check(ctx, rc):
 def nb_default_opts(**overrides) -> nb_opts:
     o = nb_opts()
     lib().nb_default_opts(ctypes.byref(o))
+    names = {f[0] for f in nb_opts._fields_}
     for k, v in overrides.items():
+        if k not in names:
+            raise TypeError("nb_opts has no field %r" % k)
         setattr(o, k, v)
     return o
 

@@ -73,6 +73,10 @@ def test_init_rejects_bad_arguments_before_touching_a_device(built):
         dict(opts=nb.nb_default_opts(level_fixed=2)),
         dict(opts=nb.nb_default_opts(precision=7)),
         dict(opts=nb.nb_default_opts(force_mode=9)),
+        dict(opts=nb.nb_default_opts(summation=4)),
+        dict(opts=nb.nb_default_opts(summation=nb.NB_SUM_FIXED, precision=nb.NB_FP64)),
+        dict(opts=nb.nb_default_opts(summation=nb.NB_SUM_FIXED), eps=0.0),
+        dict(opts=nb.nb_default_opts(summation=nb.NB_SUM_FIXED), eps=1e-30),
     ]
     for case in bad:
         args = dict(m=m, x=x, v=v, eps=0.1, opts=None)
@@ -89,3 +93,31 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.lower(), f
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    # offsets and sizes of nb_opts and nb_stats as the C compiler lays them out
+    import ctypes
+    import paper_cs_0702135_gb300 as nb
+    prog = tmp_path / "layout.c"
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "nb.h"', 'int main(void) {']
+    for st in (nb.nb.nb_opts, nb.nb.nb_stats):
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (st.__name__, st.__name__))
+        for name, _ in st._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (st.__name__, name, st.__name__, name))
+    lines += ['return 0;', '}']
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(prog)], check=True)
+    c_layout = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                             check=True).stdout.splitlines())
+    for st in (nb.nb.nb_opts, nb.nb.nb_stats):
+        assert int(c_layout[st.__name__]) == ctypes.sizeof(st)
+        for name, _ in st._fields_:
+            assert int(c_layout["%s.%s" % (st.__name__, name)]) == getattr(st, name).offset, name
+
+
+def test_default_opts_rejects_unknown_fields(built):
+    import paper_cs_0702135_gb300 as nb
+    with pytest.raises(TypeError):
+        nb.nb_default_opts(sumation=1)
