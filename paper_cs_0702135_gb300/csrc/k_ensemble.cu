@@ -1,25 +1,30 @@
 // k_ensemble.cu -- many independent clusters advanced together: every
 // ensemble block step advances every unfinished cluster by its own next block
-// step (Section 2 step loop: select the block, predict, force, correct), in two
-// launches replayed from one CUDA graph:
-//   A. a CTA per cluster (taken largest first from a work counter): block time
-//      t_next = min over the cluster of t_i + dt_i, every particle predicted to
-//      t_next (FP64, the single-system predictor's arithmetic) into global
-//      double-single j records, the block compacted in ascending order (ballot
-//      + prefix sums), and one work item per chunk of up to `threads` active
-//      particles appended to a queue;
-//   B. persistent CTAs take queue items: the cluster's j records stream through
-//      shared-memory tiles, g consecutive lanes share one active particle and
-//      split its j loop when the chunk is small (g = the largest power of two
-//      with g * chunk <= threads, capped at gmax), FP32 pair arithmetic on
-//      double-single positions with TwoSum-promoted partials and a shuffle
-//      reduction in the lane group; the group's first lane corrects its
-//      particle (FP64 corrector and Aarseth step, the single-system
-//      corrector's arithmetic).  The force reads only the j records, so
-//      correcting while other items still sum is safe.
-// A block of thousands of particles in one cluster is thus spread over many
-// SMs.  Every item is computed by one CTA in a fixed order, so results do not
-// depend on which CTA takes it.
+// step (Section 2 step loop: select the block, predict, force, correct) in one
+// persistent cooperative launch, replayed from a CUDA graph.  Its CTAs work in
+// two phases:
+//   A. clusters, largest first, from a work counter: block time t_next = min
+//      over the cluster of t_i + dt_i, every particle predicted to t_next (FP64,
+//      the single-system predictor's arithmetic) into global double-single j
+//      records, the block compacted in ascending order (ballot + prefix sums),
+//      and one work item per chunk of up to `threads` active particles
+//      published to a queue (the item's cluster index is written last and
+//      marks it ready);
+//   B. once every cluster is claimed, queue items in order: the cluster's j
+//      records stream through shared-memory tiles, g consecutive lanes share one
+//      active particle and split its j loop when the chunk is small (g = the
+//      largest power of two with g * chunk <= threads, capped at gmax), FP32
+//      pair arithmetic on double-single positions with TwoSum-promoted partials
+//      and a shuffle reduction in the lane group; the group's first lane
+//      corrects its particle (FP64 corrector and Aarseth step, the
+//      single-system corrector's arithmetic).  The force reads only the j
+//      records, so correcting while other items still sum is safe.
+// An item waits only for its own cluster's phase A, so the large clusters'
+// items run while small clusters are still being predicted.  A CTA waiting for
+// an item spins with a time limit (error NB_ETIMEOUT past it); the cooperative
+// launch keeps every CTA resident, and every cluster is claimed before any CTA
+// waits, so the wait always ends.  Every item is computed by one CTA in a fixed
+// order, so results do not depend on which CTA takes it.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -50,10 +55,11 @@ struct EnsArgs {
     long long t_end;
     int gmax;                 // largest lane group per active particle
     int chunk;                // active particles per work item (= launch B threads)
-    int *work;                // launch A: cluster counter; launch B: item counter
-    int *work_b;
-    int *qlen;                // queue length (items appended by launch A)
-    int *qc, *qk;             // queue: cluster and chunk of each item
+    int *work;                // phase A: cluster counter
+    int *work_b;              // phase B: item counter
+    int *qlen;                // queue length (items reserved in phase A)
+    int *a_done;              // clusters whose phase A finished
+    int *qc, *qk;             // queue: cluster (-1 = not ready) and chunk of each item
     float4 *jph, *jpl, *jv;   // [P] predicted double-single records
     int *act;                 // [P] active particles of each cluster (local indices)
     int *na;                  // [C] block sizes
@@ -86,180 +92,238 @@ struct MinLL {
 
 enum EnsMode { kEnsStep = 0, kEnsForce = 1, kEnsInit = 2 };
 
-// Launch A: schedule, predict, compact, enqueue.
+// Phase A for the cluster of rank q: schedule, predict, compact, publish.
 template <int NT, int MODE>
-__global__ void __launch_bounds__(NT) k_ens_a(EnsArgs ea)
+__device__ __forceinline__ void ens_a_cluster(const EnsArgs &ea, int q, long long *s_red, int *s_wtot)
 {
-    __shared__ long long s_red[NT / 32];
-    __shared__ int s_wtot[NT / 32];
-    __shared__ int s_cluster;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const State &S = ea.s;
     const long long P = S.n;
-    for (;;) {
-        if (tid == 0) s_cluster = atomicAdd(ea.work, 1);
+    const int c = ea.order[q];
+    const long long o = ea.off[c];
+    const int n = (int)(ea.off[c + 1] - o);
+    if (MODE == kEnsStep && ea.done[c]) return;
+    long long tn = 0;
+    if (MODE == kEnsStep) {
+        long long mn = LLONG_MAX;
+        for (int i = tid; i < n; i += NT)
+            mn = min(mn, S.t[o + i] + (1LL << (kTickBits - S.lev[o + i])));
+        tn = cta_reduce(mn, MinLL(), s_red);
+        if (tn > ea.t_end) {
+            if (tid == 0) ea.done[c] = 1;
+            return;
+        }
+    }
+    int running = 0;
+    for (int base = 0; base < n; base += NT) {
+        const int i = base + tid;
+        bool f = false;
+        if (i < n) {
+            const long long gi = o + i;
+            const double dt = MODE == kEnsStep ? ticks_to_time(tn - S.t[gi]) : 0.0;
+            double xp[3], vp[3];
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc)
+                predict1(S.x[cc * P + gi], S.v[cc * P + gi], S.a[cc * P + gi], S.k[cc * P + gi],
+                         dt, xp[cc], vp[cc]);
+            float hi[3], lo[3];
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) split_ds(xp[cc], hi[cc], lo[cc]);
+            ea.jph[gi] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(S.m[gi]));
+            ea.jpl[gi] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+            ea.jv[gi] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
+                                    __double2float_rn(vp[2]), 0.0f);
+            f = MODE == kEnsStep ? (S.t[gi] + (1LL << (kTickBits - S.lev[gi])) == tn) : true;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) s_wtot[warp] = __popc(bal);
         __syncthreads();
-        const int q = s_cluster;
+        int woff = 0, tot = 0;
+        for (int w = 0; w < NT / 32; ++w) {
+            woff += w < warp ? s_wtot[w] : 0;
+            tot += s_wtot[w];
+        }
+        if (f) ea.act[o + running + woff + __popc(bal & ((1u << lane) - 1u))] = i;
+        running += tot;
         __syncthreads();
-        if (q >= ea.C) break;
-        const int c = ea.order[q];
-        const long long o = ea.off[c];
-        const int n = (int)(ea.off[c + 1] - o);
-        if (MODE == kEnsStep && ea.done[c]) continue;
-        long long tn = 0;
+    }
+    // every thread's records and active indices are written before tid 0 publishes
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const int na = running;
+        ea.na[c] = na;
+        ea.tnext[c] = tn;
         if (MODE == kEnsStep) {
-            long long mn = LLONG_MAX;
-            for (int i = tid; i < n; i += NT)
-                mn = min(mn, S.t[o + i] + (1LL << (kTickBits - S.lev[o + i])));
-            tn = cta_reduce(mn, MinLL(), s_red);
-            if (tn > ea.t_end) {
-                if (tid == 0) ea.done[c] = 1;
-                continue;
-            }
+            ea.steps[c] += 1;
+            ea.inter[c] += (long long)na * (n - 1);
         }
-        int running = 0;
-        for (int base = 0; base < n; base += NT) {
-            const int i = base + tid;
-            bool f = false;
-            if (i < n) {
-                const long long gi = o + i;
-                const double dt = MODE == kEnsStep ? ticks_to_time(tn - S.t[gi]) : 0.0;
-                double xp[3], vp[3];
-#pragma unroll
-                for (int cc = 0; cc < 3; ++cc)
-                    predict1(S.x[cc * P + gi], S.v[cc * P + gi], S.a[cc * P + gi], S.k[cc * P + gi],
-                             dt, xp[cc], vp[cc]);
-                float hi[3], lo[3];
-#pragma unroll
-                for (int cc = 0; cc < 3; ++cc) split_ds(xp[cc], hi[cc], lo[cc]);
-                ea.jph[gi] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(S.m[gi]));
-                ea.jpl[gi] = make_float4(lo[0], lo[1], lo[2], 0.0f);
-                ea.jv[gi] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
-                                        __double2float_rn(vp[2]), 0.0f);
-                f = MODE == kEnsStep ? (S.t[gi] + (1LL << (kTickBits - S.lev[gi])) == tn) : true;
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, f);
-            if (lane == 0) s_wtot[warp] = __popc(bal);
-            __syncthreads();
-            int woff = 0, tot = 0;
-            for (int w = 0; w < NT / 32; ++w) {
-                woff += w < warp ? s_wtot[w] : 0;
-                tot += s_wtot[w];
-            }
-            if (f) ea.act[o + running + woff + __popc(bal & ((1u << lane) - 1u))] = i;
-            running += tot;
-            __syncthreads();
-        }
-        if (tid == 0) {
-            const int na = running;
-            ea.na[c] = na;
-            ea.tnext[c] = tn;
-            if (MODE == kEnsStep) {
-                ea.steps[c] += 1;
-                ea.inter[c] += (long long)na * (n - 1);
-            }
-            const int items = (na + ea.chunk - 1) / ea.chunk;
-            const int base = atomicAdd(ea.qlen, items);
-            for (int k = 0; k < items; ++k) {
-                ea.qc[base + k] = c;
-                ea.qk[base + k] = k;
-            }
-        }
+        const int items = (na + ea.chunk - 1) / ea.chunk;
+        const int base = atomicAdd(ea.qlen, items);
+        for (int k = 0; k < items; ++k) ea.qk[base + k] = k;
+        __threadfence();
+        for (int k = 0; k < items; ++k) atomicExch(&ea.qc[base + k], c);
     }
 }
 
-// Launch B: force on one chunk of a cluster's block, then correction (or the
-// start-up levels, or plain output).
-template <int NT, int MODE>
-__global__ void __launch_bounds__(NT) k_ens_b(EnsArgs ea)
+// Queue item `it` for phase B: true with (c, k) once it is published; false
+// when there is no such item (every cluster's phase A finished and the queue
+// is shorter) or the wait ran past its limit (error NB_ETIMEOUT).  Consuming
+// an item marks it not ready again for the next launch.
+constexpr long long kEnsSpinCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+__device__ __forceinline__ bool ens_take_item(const EnsArgs &ea, int it, int &c, int &k)
 {
-    __shared__ float4 s_ph[NT], s_pl[NT], s_v[NT];
-    __shared__ int s_item;
+    volatile int *qc = ea.qc;
+    volatile int *adone = ea.a_done;
+    volatile int *qlen = ea.qlen;
+    const long long t0 = clock64();
+    for (;;) {
+        const int cc = qc[it];
+        if (cc >= 0) {
+            __threadfence();
+            c = cc;
+            k = __ldcg(&ea.qk[it]);
+            qc[it] = -1;
+            return true;
+        }
+        if (*adone >= ea.C) {
+            __threadfence();
+            if (it >= *qlen) return false;
+            continue;  // published before the last cluster finished: visible next read
+        }
+        if (clock64() - t0 > kEnsSpinCycles) {
+            atomicCAS(ea.err, 0, NB_ETIMEOUT);
+            return false;
+        }
+        __nanosleep(64);
+    }
+}
+
+// Phase B for item (c, k): force on one chunk of the cluster's block, then the
+// correction (or the start-up levels, or plain output).
+template <int NT, int MODE>
+__device__ __forceinline__ void ens_b_item(const EnsArgs &ea, int c, int k, float4 *s_ph, float4 *s_pl,
+                                           float4 *s_v)
+{
     const int tid = threadIdx.x;
     const State &S = ea.s;
     const long long P = S.n;
-    const int qlen = *ea.qlen;
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(ea.work_b, 1);
+    const long long o = ea.off[c];
+    const int n = (int)(ea.off[c + 1] - o);
+    // Everything phase A wrote in this launch is read past L1 (__ldcg): L1 is
+    // not coherent across SMs, and a line read earlier for a neighbouring
+    // cluster could hold this cluster's records from before they were written.
+    const int s0 = k * ea.chunk;
+    const int cnt = min(ea.chunk, __ldcg(&ea.na[c]) - s0);
+    int g = 1;
+    while (g < ea.gmax && g * 2 * cnt <= NT) g <<= 1;
+    const int grp = tid / g, lig = tid % g;
+    const bool valid = grp < cnt;
+    const int i = __ldcg(&ea.act[o + s0 + (valid ? grp : 0)]);
+    const float4 ip = __ldcg(&ea.jph[o + i]), il = __ldcg(&ea.jpl[o + i]), iv = __ldcg(&ea.jv[o + i]);
+    const float xh[3] = {ip.x, ip.y, ip.z}, xl[3] = {il.x, il.y, il.z}, vi[3] = {iv.x, iv.y, iv.z};
+    float hi[7] = {0, 0, 0, 0, 0, 0, 0}, lo[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int jt = 0; jt < n; jt += NT) {
         __syncthreads();
-        const int it = s_item;
+        const int j = jt + tid;
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        s_ph[tid] = j < n ? __ldcg(&ea.jph[o + j]) : z;
+        s_pl[tid] = j < n ? __ldcg(&ea.jpl[o + j]) : z;
+        s_v[tid] = j < n ? __ldcg(&ea.jv[o + j]) : z;
         __syncthreads();
-        if (it >= qlen) break;
-        const int c = ea.qc[it], k = ea.qk[it];
-        const long long o = ea.off[c];
-        const int n = (int)(ea.off[c + 1] - o);
-        const int s0 = k * ea.chunk;
-        const int cnt = min(ea.chunk, ea.na[c] - s0);
-        int g = 1;
-        while (g < ea.gmax && g * 2 * cnt <= NT) g <<= 1;
-        const int grp = tid / g, lig = tid % g;
-        const bool valid = grp < cnt;
-        const int i = ea.act[o + s0 + (valid ? grp : 0)];
-        const float4 ip = ea.jph[o + i], il = ea.jpl[o + i], iv = ea.jv[o + i];
-        const float xh[3] = {ip.x, ip.y, ip.z}, xl[3] = {il.x, il.y, il.z}, vi[3] = {iv.x, iv.y, iv.z};
-        float hi[7] = {0, 0, 0, 0, 0, 0, 0}, lo[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int jt = 0; jt < n; jt += NT) {
-            __syncthreads();
-            const int j = jt + tid;
-            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            s_ph[tid] = j < n ? ea.jph[o + j] : z;
-            s_pl[tid] = j < n ? ea.jpl[o + j] : z;
-            s_v[tid] = j < n ? ea.jv[o + j] : z;
-            __syncthreads();
-            const int jc = min(NT, n - jt);
-            // FP32 partials over at most 64 pairs per lane, then TwoSum promotion
-            for (int jb = 0; jb < jc; jb += 64 * g) {
-                const int je = min(jc, jb + 64 * g);
-                float ta[3] = {0, 0, 0}, tk[3] = {0, 0, 0}, tp = 0.0f;
-                for (int jj = jb + lig; jj < je; jj += g)
-                    pair_ds<false, true>(s_ph[jj], s_pl[jj], s_v[jj], xh, xl, vi, ea.eps2, ta, tk, tp,
-                                         jt + jj, i);
-                const float t7[7] = {ta[0], ta[1], ta[2], tk[0], tk[1], tk[2], tp};
+        const int jc = min(NT, n - jt);
+        // FP32 partials over at most 64 pairs per lane, then TwoSum promotion
+        for (int jb = 0; jb < jc; jb += 64 * g) {
+            const int je = min(jc, jb + 64 * g);
+            float ta[3] = {0, 0, 0}, tk[3] = {0, 0, 0}, tp = 0.0f;
+            for (int jj = jb + lig; jj < je; jj += g)
+                pair_ds<false, true>(s_ph[jj], s_pl[jj], s_v[jj], xh, xl, vi, ea.eps2, ta, tk, tp,
+                                     jt + jj, i);
+            const float t7[7] = {ta[0], ta[1], ta[2], tk[0], tk[1], tk[2], tp};
 #pragma unroll
-                for (int cc = 0; cc < 7; ++cc) two_sum_acc(hi[cc], lo[cc], t7[cc]);
-            }
+            for (int cc = 0; cc < 7; ++cc) two_sum_acc(hi[cc], lo[cc], t7[cc]);
         }
-        for (int sh = 1; sh < g; sh <<= 1) {
+    }
+    for (int sh = 1; sh < g; sh <<= 1) {
 #pragma unroll
-            for (int cc = 0; cc < 7; ++cc) {
-                const float h2 = __shfl_xor_sync(0xffffffffu, hi[cc], sh);
-                const float l2 = __shfl_xor_sync(0xffffffffu, lo[cc], sh);
-                ds_add(hi[cc], lo[cc], h2, l2);
-            }
+        for (int cc = 0; cc < 7; ++cc) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi[cc], sh);
+            const float l2 = __shfl_xor_sync(0xffffffffu, lo[cc], sh);
+            ds_add(hi[cc], lo[cc], h2, l2);
         }
-        if (!valid || lig != 0) continue;
-        double res[7];
+    }
+    if (!valid || lig != 0) return;
+    double res[7];
 #pragma unroll
-        for (int cc = 0; cc < 7; ++cc) res[cc] = (double)hi[cc] + (double)lo[cc];
-        const long long gi = o + i;
-        if (MODE == kEnsForce) {
+    for (int cc = 0; cc < 7; ++cc) res[cc] = (double)hi[cc] + (double)lo[cc];
+    const long long gi = o + i;
+    if (MODE == kEnsForce) {
 #pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                ea.out_acc[3 * gi + cc] = res[cc];
-                ea.out_jerk[3 * gi + cc] = res[3 + cc];
-            }
-            ea.out_pot[gi] = res[6];
-            continue;
+        for (int cc = 0; cc < 3; ++cc) {
+            ea.out_acc[3 * gi + cc] = res[cc];
+            ea.out_jerk[3 * gi + cc] = res[3 + cc];
         }
-        if (MODE == kEnsInit) {
+        ea.out_pot[gi] = res[6];
+        return;
+    }
+    if (MODE == kEnsInit) {
 #pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                S.a[cc * P + gi] = res[cc];
-                S.k[cc * P + gi] = res[3 + cc];
-            }
-            S.t[gi] = 0;
-            int lv;
-            if (!level_of(initial_dt(res, res + 3, ea.eta_init), ea.level_min, lv)) {
-                atomicCAS(ea.err, 0, NB_ESTEP);
-                lv = kTickBits;
-            }
-            S.lev[gi] = lv;
-            continue;
+        for (int cc = 0; cc < 3; ++cc) {
+            S.a[cc * P + gi] = res[cc];
+            S.k[cc * P + gi] = res[3 + cc];
         }
-        // corrector and new step (the single-system corrector's arithmetic)
-        const double ap[3] = {res[0], res[1], res[2]}, kp[3] = {res[3], res[4], res[5]};
-        if (!correct_particle(S, gi, P, ea.tnext[c], ap, kp, ea.eta, ea.level_min, 0))
+        S.t[gi] = 0;
+        int lv;
+        if (!level_of(initial_dt(res, res + 3, ea.eta_init), ea.level_min, lv)) {
             atomicCAS(ea.err, 0, NB_ESTEP);
+            lv = kTickBits;
+        }
+        S.lev[gi] = lv;
+        return;
+    }
+    // corrector and new step (the single-system corrector's arithmetic)
+    const double ap[3] = {res[0], res[1], res[2]}, kp[3] = {res[3], res[4], res[5]};
+    if (!correct_particle(S, gi, P, __ldcg(&ea.tnext[c]), ap, kp, ea.eta, ea.level_min, 0))
+        atomicCAS(ea.err, 0, NB_ESTEP);
+}
+
+// One ensemble block step (or start-up, or force-only pass): phase A over the
+// clusters, then phase B over the queue.
+template <int NT, int MODE>
+__global__ void __launch_bounds__(NT) k_ens_step(EnsArgs ea)
+{
+    __shared__ long long s_red[NT / 32];
+    __shared__ int s_wtot[NT / 32];
+    __shared__ float4 s_ph[NT], s_pl[NT], s_v[NT];
+    __shared__ int s_q, s_c, s_k;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) s_q = atomicAdd(ea.work, 1);
+        __syncthreads();
+        const int q = s_q;
+        __syncthreads();
+        if (q >= ea.C) break;
+        ens_a_cluster<NT, MODE>(ea, q, s_red, s_wtot);
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(ea.a_done, 1);
+        }
+    }
+    for (;;) {
+        if (tid == 0) {
+            int c = -1, k = 0;
+            const int it = atomicAdd(ea.work_b, 1);
+            if (!ens_take_item(ea, it, c, k)) c = -1;
+            s_c = c;
+            s_k = k;
+        }
+        __syncthreads();
+        const int c = s_c, k = s_k;
+        __syncthreads();
+        if (c < 0) break;
+        ens_b_item<NT, MODE>(ea, c, k, s_ph, s_pl, s_v);
     }
 }
 
@@ -343,7 +407,7 @@ struct nb_ens {
     double *d_x = nullptr, *d_v = nullptr, *d_a = nullptr, *d_k = nullptr, *d_m = nullptr;
     long long *d_t = nullptr;
     int *d_lev = nullptr;
-    int *d_work = nullptr, *d_done = nullptr, *d_err = nullptr;  // d_work: [3] counters A, B, queue
+    int *d_work = nullptr, *d_done = nullptr, *d_err = nullptr;  // d_work: [4] counters A, B, queue, A done
     float4 *d_jph = nullptr, *d_jpl = nullptr, *d_jv = nullptr;
     int *d_act = nullptr, *d_na = nullptr, *d_qc = nullptr, *d_qk = nullptr;
     long long *d_tnext = nullptr;
@@ -404,6 +468,7 @@ EnsArgs ens_args(nb_ens *e)
     a.work = e->d_work;
     a.work_b = e->d_work + 1;
     a.qlen = e->d_work + 2;
+    a.a_done = e->d_work + 3;
     a.qc = e->d_qc;
     a.qk = e->d_qk;
     a.jph = e->d_jph;
@@ -419,29 +484,48 @@ EnsArgs ens_args(nb_ens *e)
     return a;
 }
 
-constexpr int kNTA = 256;  // launch A threads
-
+// Resident CTAs per SM of the fused kernel for this configuration.
 template <int NT, int MODE>
-void launch_b_t(nb_ens *e, const EnsArgs &a)
+int ens_blocks_per_sm()
 {
     static int bps = 0;
-    if (bps == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_ens_b<NT, MODE>, NT, 0) != cudaSuccess)
+    if (bps == 0 &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_ens_step<NT, MODE>, NT, 0) != cudaSuccess)
         bps = 1;
-    k_ens_b<NT, MODE><<<e->sms * (bps > 0 ? bps : 1), NT, 0, e->st>>>(a);
+    return bps > 0 ? bps : 1;
 }
 
-// One pass of the two launches (counters zeroed first).
+// One cooperative launch over all resident CTAs (CTAs wait on each other's
+// phase A, so they must all be resident).
+template <int NT, int MODE>
+cudaError_t launch_step_t(nb_ens *e, const EnsArgs &a)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.gridDim = dim3(e->sms * ens_blocks_per_sm<NT, MODE>());
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = e->st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_ens_step<NT, MODE>, a);
+}
+
+// One pass: counters zeroed, then the fused launch.
 template <int MODE>
 int enqueue_ens(nb_ens *e, const EnsArgs &a)
 {
-    ECK(cudaMemsetAsync(e->d_work, 0, 3 * sizeof(int), e->st));
-    k_ens_a<kNTA, MODE><<<e->sms * 4, kNTA, 0, e->st>>>(a);
+    ECK(cudaMemsetAsync(e->d_work, 0, 4 * sizeof(int), e->st));
+    cudaError_t ce;
     switch (e->nt) {
-    case 128: launch_b_t<128, MODE>(e, a); break;
-    case 512: launch_b_t<512, MODE>(e, a); break;
-    default: launch_b_t<256, MODE>(e, a); break;
+    case 128: ce = launch_step_t<128, MODE>(e, a); break;
+    case 512: ce = launch_step_t<512, MODE>(e, a); break;
+    default: ce = launch_step_t<256, MODE>(e, a); break;
     }
-    e->launches += 2;
+    if (ce != cudaSuccess) return efail(e, NB_ECUDA, "ensemble launch: %s", cudaGetErrorString(ce));
+    e->launches += 1;
     return NB_OK;
 }
 
@@ -455,8 +539,12 @@ int ens_sync(nb_ens *e)
     ECK(cudaStreamSynchronize(e->st));
     ECK(cudaGetLastError());
     if (h_err) {
+        // an aborted launch may leave items unconsumed: mark every item not ready
+        ECK(cudaMemsetAsync(e->d_qc, 0xff, sizeof(int) * (e->P + e->C), e->st));
         ECK(cudaMemsetAsync(e->d_err, 0, sizeof(int), e->st));
         ECK(cudaStreamSynchronize(e->st));
+        if (h_err == NB_ETIMEOUT)
+            return efail(e, NB_ETIMEOUT, "an ensemble launch waited too long for a cluster's block");
         return efail(e, h_err, "a new time step fell below 2^-40 in some cluster");
     }
     return NB_OK;
@@ -545,7 +633,7 @@ int ens_init_impl(nb_ens *e, int32_t C, const int64_t *off, const double *m, con
         (rc = ealloc(e, &e->d_x, 3 * P)) || (rc = ealloc(e, &e->d_v, 3 * P)) ||
         (rc = ealloc(e, &e->d_a, 3 * P)) || (rc = ealloc(e, &e->d_k, 3 * P)) ||
         (rc = ealloc(e, &e->d_m, P)) || (rc = ealloc(e, &e->d_t, P)) || (rc = ealloc(e, &e->d_lev, P)) ||
-        (rc = ealloc(e, &e->d_work, 3)) || (rc = ealloc(e, &e->d_done, C)) || (rc = ealloc(e, &e->d_err, 1)) ||
+        (rc = ealloc(e, &e->d_work, 4)) || (rc = ealloc(e, &e->d_done, C)) || (rc = ealloc(e, &e->d_err, 1)) ||
         (rc = ealloc(e, &e->d_steps, C)) || (rc = ealloc(e, &e->d_inter, C)) ||
         (rc = ealloc(e, &e->d_stage, 7 * P)) || (rc = ealloc(e, &e->d_jph, P)) ||
         (rc = ealloc(e, &e->d_jpl, P)) || (rc = ealloc(e, &e->d_jv, P)) ||
@@ -576,6 +664,7 @@ int ens_init_impl(nb_ens *e, int32_t C, const int64_t *off, const double *m, con
     ECK(cudaMemsetAsync(e->d_err, 0, sizeof(int), e->st));
     ECK(cudaMemsetAsync(e->d_steps, 0, sizeof(long long) * C, e->st));
     ECK(cudaMemsetAsync(e->d_inter, 0, sizeof(long long) * C, e->st));
+    ECK(cudaMemsetAsync(e->d_qc, 0xff, sizeof(int) * (P + C), e->st));  // no item ready
     // start-up: force on every particle of every cluster, initial steps
     if ((rc = enqueue_ens<kEnsInit>(e, ens_args(e)))) return rc;
     ECK(cudaGetLastError());
