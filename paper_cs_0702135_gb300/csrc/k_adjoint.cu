@@ -269,10 +269,9 @@ __global__ void k_adj_pre(State st, double dt, const double *xb, const double *v
     const int n = st.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double xp[3], vp[3], a1b[3], k1b[3];
+        predict3(st, i, n, dt, xp, vp);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            predict1(st.x[c * n + i], st.v[c * n + i], st.a[c * n + i], st.k[c * n + i], dt, xp[c],
-                     vp[c]);
             const long long q = 3LL * i + c;
             const double a2b = xb[q] * dt * dt / 12.0 + vb[q] * dt / 3.0;
             const double a3b = xb[q] * dt * dt / 20.0 + vb[q] * dt / 4.0;

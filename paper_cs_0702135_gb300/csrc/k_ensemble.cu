@@ -4,13 +4,16 @@
 // persistent cooperative launch, replayed from a CUDA graph.  Its CTAs work in
 // two phases:
 //   A. clusters, largest first, from a work counter: block time t_next = min
-//      over the cluster of t_i + dt_i, every particle predicted to t_next (FP64,
-//      the single-system predictor's arithmetic) into global double-single j
-//      records, the block compacted in ascending order (ballot + prefix sums),
-//      and one work item per chunk of up to `threads` active particles
-//      published to a queue (the item's cluster index is written last and
-//      marks it ready);
-//   B. once every cluster is claimed, queue items in order: the cluster's j
+//      over the cluster of t_i + dt_i, the block compacted in ascending order
+//      (ballot + prefix sums), every particle predicted to t_next (FP64, the
+//      single-system predictor's arithmetic) into global double-single j
+//      records, and one work item per chunk of up to threads / gmax active
+//      particles published to a queue (the item's cluster index is written
+//      last and marks it ready).  A cluster above 512 particles is not
+//      predicted here: its prediction goes to the queue as chunks of 512,
+//      ahead of its force items, so several CTAs share the FP64 work;
+//   B. once every cluster is claimed, queue items in order: prediction chunks;
+//      force items (which first wait for their cluster's prediction): the j
 //      records stream through shared-memory tiles, g consecutive lanes share one
 //      active particle and split its j loop when the chunk is small (g = the
 //      largest power of two with g * chunk <= threads, capped at gmax), FP32
@@ -43,6 +46,7 @@ namespace {
 using namespace dev;
 
 constexpr int kEnsMaxN = 4096;       // largest cluster
+constexpr int kEnsPredChunk = 512;   // larger clusters are predicted in chunks by several CTAs
 
 struct EnsArgs {
     int C;                    // clusters
@@ -54,12 +58,15 @@ struct EnsArgs {
     int level_min;
     long long t_end;
     int gmax;                 // largest lane group per active particle
-    int chunk;                // active particles per work item (= launch B threads)
+    int chunk;                // active particles per work item (threads / gmax)
     int *work;                // phase A: cluster counter
     int *work_b;              // phase B: item counter
     int *qlen;                // queue length (items reserved in phase A)
     int *a_done;              // clusters whose phase A finished
-    int *qc, *qk;             // queue: cluster (-1 = not ready) and chunk of each item
+    int *qc, *qk;             // queue: cluster (-1 = not ready); force chunk k >= 0 or
+                              // prediction chunk -1 - k of each item
+    int qcap;                 // queue capacity: P + C (at most n_c + 1 items per cluster)
+    int *pred_left;           // [C] prediction chunks of the cluster not yet done
     float4 *jph, *jpl, *jv;   // [P] predicted double-single records
     int *act;                 // [P] active particles of each cluster (local indices)
     int *na;                  // [C] block sizes
@@ -114,18 +121,16 @@ __device__ __forceinline__ void ens_a_cluster(const EnsArgs &ea, int q, long lon
             return;
         }
     }
+    const bool split = n > kEnsPredChunk;  // prediction left to queue items
     int running = 0;
     for (int base = 0; base < n; base += NT) {
         const int i = base + tid;
         bool f = false;
-        if (i < n) {
+        if (i < n && !split) {
             const long long gi = o + i;
             const double dt = MODE == kEnsStep ? ticks_to_time(tn - S.t[gi]) : 0.0;
             double xp[3], vp[3];
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc)
-                predict1(S.x[cc * P + gi], S.v[cc * P + gi], S.a[cc * P + gi], S.k[cc * P + gi],
-                         dt, xp[cc], vp[cc]);
+            predict3(S, gi, P, dt, xp, vp);
             float hi[3], lo[3];
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc) split_ds(xp[cc], hi[cc], lo[cc]);
@@ -133,6 +138,9 @@ __device__ __forceinline__ void ens_a_cluster(const EnsArgs &ea, int q, long lon
             ea.jpl[gi] = make_float4(lo[0], lo[1], lo[2], 0.0f);
             ea.jv[gi] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
                                     __double2float_rn(vp[2]), 0.0f);
+        }
+        if (i < n) {
+            const long long gi = o + i;
             f = MODE == kEnsStep ? (S.t[gi] + (1LL << (kTickBits - S.lev[gi])) == tn) : true;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, f);
@@ -158,11 +166,14 @@ __device__ __forceinline__ void ens_a_cluster(const EnsArgs &ea, int q, long lon
             ea.steps[c] += 1;
             ea.inter[c] += (long long)na * (n - 1);
         }
-        const int items = (na + ea.chunk - 1) / ea.chunk;
-        const int base = atomicAdd(ea.qlen, items);
-        for (int k = 0; k < items; ++k) ea.qk[base + k] = k;
+        const int npred = split ? (n + kEnsPredChunk - 1) / kEnsPredChunk : 0;
+        const int nforce = (na + ea.chunk - 1) / ea.chunk;
+        ea.pred_left[c] = npred;
+        const int base = atomicAdd(ea.qlen, npred + nforce);
+        for (int k = 0; k < npred; ++k) ea.qk[base + k] = -1 - k;  // ahead of the force items
+        for (int k = 0; k < nforce; ++k) ea.qk[base + npred + k] = k;
         __threadfence();
-        for (int k = 0; k < items; ++k) atomicExch(&ea.qc[base + k], c);
+        for (int k = 0; k < npred + nforce; ++k) atomicExch(&ea.qc[base + k], c);
     }
 }
 
@@ -174,6 +185,9 @@ constexpr long long kEnsSpinCycles = 4000000000LL;  // about 2 s at 2 GHz
 
 __device__ __forceinline__ bool ens_take_item(const EnsArgs &ea, int it, int &c, int &k)
 {
+    // Every CTA takes one index past the last item before it stops, so indices
+    // run up to (items + CTAs - 1): those at or past the capacity hold no item.
+    if (it >= ea.qcap) return false;
     volatile int *qc = ea.qc;
     volatile int *adone = ea.a_done;
     volatile int *qlen = ea.qlen;
@@ -200,17 +214,68 @@ __device__ __forceinline__ bool ens_take_item(const EnsArgs &ea, int it, int &c,
     }
 }
 
-// Phase B for item (c, k): force on one chunk of the cluster's block, then the
-// correction (or the start-up levels, or plain output).
+// Phase B, prediction item: particles [512 p, 512 (p + 1)) of cluster c to its
+// block time; the last CTA to finish a cluster's chunks releases its force items.
 template <int NT, int MODE>
-__device__ __forceinline__ void ens_b_item(const EnsArgs &ea, int c, int k, float4 *s_ph, float4 *s_pl,
-                                           float4 *s_v)
+__device__ __forceinline__ void ens_predict_chunk(const EnsArgs &ea, int c, int p)
 {
     const int tid = threadIdx.x;
     const State &S = ea.s;
     const long long P = S.n;
     const long long o = ea.off[c];
     const int n = (int)(ea.off[c + 1] - o);
+    const long long tn = __ldcg(&ea.tnext[c]);
+    const int i1 = min(n, (p + 1) * kEnsPredChunk);
+    for (int i = p * kEnsPredChunk + tid; i < i1; i += NT) {
+        const long long gi = o + i;
+        const double dt = MODE == kEnsStep ? ticks_to_time(tn - S.t[gi]) : 0.0;
+        double xp[3], vp[3];
+        predict3(S, gi, P, dt, xp, vp);
+        float hi[3], lo[3];
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) split_ds(xp[cc], hi[cc], lo[cc]);
+        ea.jph[gi] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(S.m[gi]));
+        ea.jpl[gi] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+        ea.jv[gi] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
+                                __double2float_rn(vp[2]), 0.0f);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) atomicSub(&ea.pred_left[c], 1);
+}
+
+// Waits (thread 0) until cluster c's prediction chunks are done; false past
+// the time limit (error NB_ETIMEOUT).  The chunks precede the cluster's force
+// items in the queue, so CTAs already hold them and finish them without waiting.
+__device__ __forceinline__ bool ens_wait_predicted(const EnsArgs &ea, int c)
+{
+    volatile int *left = ea.pred_left;
+    const long long t0 = clock64();
+    while (left[c] > 0) {
+        if (clock64() - t0 > kEnsSpinCycles) {
+            atomicCAS(ea.err, 0, NB_ETIMEOUT);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    __threadfence();
+    return true;
+}
+
+// Phase B, force item (c, k): force on one chunk of the cluster's block, then the
+// correction (or the start-up levels, or plain output).
+template <int NT, int MODE>
+__device__ __forceinline__ void ens_b_item(const EnsArgs &ea, int c, int k, float4 *s_ph, float4 *s_pl,
+                                           float4 *s_v, int *s_ok)
+{
+    const int tid = threadIdx.x;
+    const State &S = ea.s;
+    const long long P = S.n;
+    const long long o = ea.off[c];
+    const int n = (int)(ea.off[c + 1] - o);
+    if (tid == 0) *s_ok = ens_wait_predicted(ea, c);
+    __syncthreads();
+    if (!*s_ok) return;
     // Everything phase A wrote in this launch is read past L1 (__ldcg): L1 is
     // not coherent across SMs, and a line read earlier for a neighbouring
     // cluster could hold this cluster's records from before they were written.
@@ -296,7 +361,7 @@ __global__ void __launch_bounds__(NT) k_ens_step(EnsArgs ea)
     __shared__ long long s_red[NT / 32];
     __shared__ int s_wtot[NT / 32];
     __shared__ float4 s_ph[NT], s_pl[NT], s_v[NT];
-    __shared__ int s_q, s_c, s_k;
+    __shared__ int s_q, s_c, s_k, s_ok;
     const int tid = threadIdx.x;
     for (;;) {
         if (tid == 0) s_q = atomicAdd(ea.work, 1);
@@ -323,7 +388,10 @@ __global__ void __launch_bounds__(NT) k_ens_step(EnsArgs ea)
         const int c = s_c, k = s_k;
         __syncthreads();
         if (c < 0) break;
-        ens_b_item<NT, MODE>(ea, c, k, s_ph, s_pl, s_v);
+        if (k < 0)
+            ens_predict_chunk<NT, MODE>(ea, c, -1 - k);
+        else
+            ens_b_item<NT, MODE>(ea, c, k, s_ph, s_pl, s_v, &s_ok);
     }
 }
 
@@ -409,7 +477,7 @@ struct nb_ens {
     int *d_lev = nullptr;
     int *d_work = nullptr, *d_done = nullptr, *d_err = nullptr;  // d_work: [4] counters A, B, queue, A done
     float4 *d_jph = nullptr, *d_jpl = nullptr, *d_jv = nullptr;
-    int *d_act = nullptr, *d_na = nullptr, *d_qc = nullptr, *d_qk = nullptr;
+    int *d_act = nullptr, *d_na = nullptr, *d_qc = nullptr, *d_qk = nullptr, *d_pred = nullptr;
     long long *d_tnext = nullptr;
     long long qcap = 0;
     long long *d_steps = nullptr, *d_inter = nullptr;
@@ -417,7 +485,7 @@ struct nb_ens {
     double *d_backup = nullptr;  // state copy for tuning
     long long *d_tbak = nullptr;
     int *d_lbak = nullptr;
-    int nt = 256, gmax = 8;      // launch B threads (= chunk) and lane-group cap (tunable)
+    int nt = 256, gmax = 8;      // threads per CTA and lane-group cap (tunable); items of nt / gmax
     long long t_end = LLONG_MAX;
     cudaGraphExec_t graph = nullptr;
     int graph_nt = 0, graph_gmax = 0;
@@ -464,12 +532,14 @@ EnsArgs ens_args(nb_ens *e)
     a.level_min = e->o.level_min;
     a.t_end = e->t_end;
     a.gmax = e->gmax;
-    a.chunk = e->nt;
+    a.chunk = e->nt / e->gmax;  // every full item uses gmax lanes per particle
     a.work = e->d_work;
     a.work_b = e->d_work + 1;
     a.qlen = e->d_work + 2;
     a.a_done = e->d_work + 3;
+    a.pred_left = e->d_pred;
     a.qc = e->d_qc;
+    a.qcap = (int)(e->P + e->C);
     a.qk = e->d_qk;
     a.jph = e->d_jph;
     a.jpl = e->d_jpl;
@@ -569,7 +639,7 @@ void ens_release(nb_ens *e)
     void *ptrs[] = {e->d_off, e->d_order, e->d_x, e->d_v, e->d_a, e->d_k, e->d_m, e->d_t,
                     e->d_lev, e->d_work, e->d_done, e->d_err, e->d_steps, e->d_inter,
                     e->d_stage, e->d_backup, e->d_tbak, e->d_lbak, e->d_jph, e->d_jpl, e->d_jv,
-                    e->d_act, e->d_na, e->d_qc, e->d_qk, e->d_tnext};
+                    e->d_act, e->d_na, e->d_qc, e->d_qk, e->d_tnext, e->d_pred};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (e->own_stream && e->st) cudaStreamDestroy(e->st);
@@ -639,7 +709,7 @@ int ens_init_impl(nb_ens *e, int32_t C, const int64_t *off, const double *m, con
         (rc = ealloc(e, &e->d_jpl, P)) || (rc = ealloc(e, &e->d_jv, P)) ||
         (rc = ealloc(e, &e->d_act, P)) || (rc = ealloc(e, &e->d_na, C)) ||
         (rc = ealloc(e, &e->d_tnext, C)) || (rc = ealloc(e, &e->d_qc, P + C)) ||
-        (rc = ealloc(e, &e->d_qk, P + C)))
+        (rc = ealloc(e, &e->d_qk, P + C)) || (rc = ealloc(e, &e->d_pred, C)))
         return rc;
     e->S.x = e->d_x;
     e->S.v = e->d_v;
@@ -665,6 +735,7 @@ int ens_init_impl(nb_ens *e, int32_t C, const int64_t *off, const double *m, con
     ECK(cudaMemsetAsync(e->d_steps, 0, sizeof(long long) * C, e->st));
     ECK(cudaMemsetAsync(e->d_inter, 0, sizeof(long long) * C, e->st));
     ECK(cudaMemsetAsync(e->d_qc, 0xff, sizeof(int) * (P + C), e->st));  // no item ready
+    ECK(cudaMemsetAsync(e->d_pred, 0, sizeof(int) * C, e->st));
     // start-up: force on every particle of every cluster, initial steps
     if ((rc = enqueue_ens<kEnsInit>(e, ens_args(e)))) return rc;
     ECK(cudaGetLastError());

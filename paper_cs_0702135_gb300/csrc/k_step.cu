@@ -33,10 +33,7 @@ __global__ void k_predict(State s, long long t_val, const long long *t_ptr, cons
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double dt = ticks_to_time(tn - s.t[i]);
         double xp[3], vp[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            predict1(s.x[c * n + i], s.v[c * n + i], s.a[c * n + i], s.k[c * n + i], dt, xp[c],
-                     vp[c]);
+        predict3(s, i, n, dt, xp, vp);
         const double m = s.m[i];
         if (precision == NB_FP64) {
             jf.pos[i] = make_double4_32a(xp[0], xp[1], xp[2], m);
@@ -227,13 +224,10 @@ __global__ void k_energy_partial(State s, const long long *t_ptr, const double *
     double ke = 0.0, pe = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double dt = ticks_to_time(tn - s.t[i]);
-        double v2 = 0.0;
+        double xp[3], vp[3], v2 = 0.0;
+        predict3(s, i, n, dt, xp, vp);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            double xp, vp;
-            predict1(s.x[c * n + i], s.v[c * n + i], s.a[c * n + i], s.k[c * n + i], dt, xp, vp);
-            v2 += vp * vp;
-        }
+        for (int c = 0; c < 3; ++c) v2 += vp[c] * vp[c];
         ke += 0.5 * s.m[i] * v2;
         pe += 0.5 * s.m[i] * pot[i];
     }

@@ -50,13 +50,31 @@ __device__ __forceinline__ void ds_add(float &h, float &l, float h2, float l2)
 
 // Hermite predictor (Section 2), round-to-nearest in the formula's order:
 //   x_p = x + (v + (dt/2)(a + (dt/3) k)) dt,   v_p = v + (a + (dt/2) k) dt.
+// dt/2 is taken as dt * 0.5, the same number (halving is exact for every dt on
+// the tick grid), which saves an FP64 division on the GB300's small FP64 pipe.
+// With h = dt/2 and q = dt/3 given (one division per particle, not per axis):
+__device__ __forceinline__ void predict1hq(double x, double v, double a, double k, double dt,
+                                           double h, double q, double &xp, double &vp)
+{
+    xp = __dadd_rn(x, __dmul_rn(__dadd_rn(v, __dmul_rn(h, __dadd_rn(a, __dmul_rn(q, k)))), dt));
+    vp = __dadd_rn(v, __dmul_rn(__dadd_rn(a, __dmul_rn(h, k)), dt));
+}
+
 __device__ __forceinline__ void predict1(double x, double v, double a, double k, double dt,
                                          double &xp, double &vp)
 {
-    const double h = __ddiv_rn(dt, 2.0);
-    const double q = __ddiv_rn(dt, 3.0);
-    xp = __dadd_rn(x, __dmul_rn(__dadd_rn(v, __dmul_rn(h, __dadd_rn(a, __dmul_rn(q, k)))), dt));
-    vp = __dadd_rn(v, __dmul_rn(__dadd_rn(a, __dmul_rn(h, k)), dt));
+    predict1hq(x, v, a, k, dt, __dmul_rn(dt, 0.5), __ddiv_rn(dt, 3.0), xp, vp);
+}
+
+// All three axes of particle i of `s` (component-major, stride n).
+__device__ __forceinline__ void predict3(const State &s, long long i, long long n, double dt,
+                                         double xp[3], double vp[3])
+{
+    const double h = __dmul_rn(dt, 0.5), q = __ddiv_rn(dt, 3.0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        predict1hq(s.x[c * n + i], s.v[c * n + i], s.a[c * n + i], s.k[c * n + i], dt, h, q, xp[c],
+                   vp[c]);
 }
 
 // A predicted FP64 position split into double-single: x = hi + lo to 2^-48.
@@ -122,13 +140,14 @@ __device__ __forceinline__ bool correct_particle(const State &s, long long i, lo
                                                  double eta, int level_min, int level_fixed)
 {
     const double dt = ticks_to_time(tn - s.t[i]);
+    const double h = __dmul_rn(dt, 0.5), q = __ddiv_rn(dt, 3.0);
     double a2[3], a3[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const long long e = c * stride + i;
         const double x = s.x[e], v = s.v[e], a = s.a[e], k = s.k[e];
         double xp, vp;
-        predict1(x, v, a, k, dt, xp, vp);
+        predict1hq(x, v, a, k, dt, h, q, xp, vp);
         const double d = __dsub_rn(a, ap[c]);
         a3[c] = __dadd_rn(__dmul_rn(2.0, d), __dmul_rn(__dadd_rn(k, kp[c]), dt));
         a2[c] = __dsub_rn(__dmul_rn(-3.0, d), __dmul_rn(__dadd_rn(__dmul_rn(2.0, k), kp[c]), dt));
