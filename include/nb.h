@@ -80,6 +80,7 @@ extern "C" {
 #define NB_TICK_BITS 40
 
 #define NB_INIT_NO_FORCE 1  /* nb_opts.flags: skip the t = 0 force sweep and initial steps */
+#define NB_RUN_GRAPH 2      /* nb_opts.flags: nb_run always replays the per-stage step graph */
 
 typedef struct nb_ctx nb_ctx;
 
@@ -179,9 +180,16 @@ int nb_step(nb_ctx *ctx, double *t_out, int32_t *n_active_out);
 /*
  * Block steps until every particle has reached t_end (which must be a multiple
  * of the largest step so that all particles meet there), or max_steps steps.
- * Steps are replayed from a captured CUDA graph with no host synchronisation
- * between them.  Outputs (may be NULL): steps taken, interactions
- * (sum of n_active (n - 1)).  Errors: NB_EINVAL, NB_ESTEP, NB_ECUDA.
+ * For n <= 16384 with precision NB_DS and summation NB_SUM_COMPENSATED or
+ * NB_SUM_FIXED the whole loop runs in one persistent launch (one CTA per 32
+ * to 256 particles, grid barriers between the stages of a step, no host
+ * synchronisation); otherwise, or with nb_opts.flags & NB_RUN_GRAPH, each step
+ * is replayed from a captured CUDA graph of the per-stage kernels.  The two
+ * forms take the same steps with the same arithmetic except the order in
+ * which the compensated sums add their partials (fixed-point sums are exact:
+ * both forms give the same bits).  Outputs (may be NULL): steps taken,
+ * interactions (sum of n_active (n - 1)).  Errors: NB_EINVAL, NB_ESTEP,
+ * NB_ETIMEOUT (a grid barrier of the persistent launch waited ~2 s), NB_ECUDA.
  */
 int nb_run(nb_ctx *ctx, double t_end, int64_t max_steps, int64_t *steps_out,
            int64_t *interactions_out);

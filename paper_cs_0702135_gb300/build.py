@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libnb_gb300.so")
 
 SOURCES = ["k_force.cu", "k_step.cu", "nb_api.cu", "k_noalloc.cu", "k_adjoint.cu", "k_ensemble.cu",
-           "k_sum.cu"]
+           "k_sum.cu", "k_run.cu"]
 HEADERS = [os.path.join(CSRC, "nb_internal.cuh"), os.path.join(CSRC, "nb_device.cuh"),
            os.path.join(INCLUDE, "nb.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -39,90 +39,6 @@ using namespace dev;
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// ---------------------------------------------------------------------------
-// Pair terms
-
-// The seven single-precision terms of j on i, each scaled as stated above;
-// false when r2 = 0 (the terms are then not numbers and must be skipped).
-__device__ __forceinline__ bool pair_rn(const float4 &p, const float4 &l, const float4 &w,
-                                        const float xh[3], const float xl[3], const float vi[3],
-                                        float eps2, float sa, float sk, float sp, float t[7],
-                                        float *key = nullptr)
-{
-    const float dx0 = __fadd_rn(__fsub_rn(p.x, xh[0]), __fsub_rn(l.x, xl[0]));
-    const float dx1 = __fadd_rn(__fsub_rn(p.y, xh[1]), __fsub_rn(l.y, xl[1]));
-    const float dx2 = __fadd_rn(__fsub_rn(p.z, xh[2]), __fsub_rn(l.z, xl[2]));
-    const float u0 = __fsub_rn(w.x, vi[0]);
-    const float u1 = __fsub_rn(w.y, vi[1]);
-    const float u2 = __fsub_rn(w.z, vi[2]);
-    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx0, dx0), __fmul_rn(dx1, dx1)), __fmul_rn(dx2, dx2));
-    const float r2 = __fadd_rn(d2, eps2);
-    const float rv = __fadd_rn(__fadd_rn(__fmul_rn(dx0, u0), __fmul_rn(dx1, u1)), __fmul_rn(dx2, u2));
-    const float rinv = __frcp_rn(__fsqrt_rn(r2));
-    const float rinv2 = __fmul_rn(rinv, rinv);
-    const float mr = __fmul_rn(p.w, rinv);
-    const float mr3 = __fmul_rn(mr, rinv2);
-    const float b = __fmul_rn(__fmul_rn(-3.0f, rv), rinv2);
-    const float fa = __fmul_rn(mr3, sa), fk = __fmul_rn(mr3, sk), fp = __fmul_rn(mr, sp);
-    t[0] = __fmul_rn(fa, dx0);
-    t[1] = __fmul_rn(fa, dx1);
-    t[2] = __fmul_rn(fa, dx2);
-    t[3] = __fmul_rn(fk, __fadd_rn(u0, __fmul_rn(b, dx0)));
-    t[4] = __fmul_rn(fk, __fadd_rn(u1, __fmul_rn(b, dx1)));
-    t[5] = __fmul_rn(fk, __fadd_rn(u2, __fmul_rn(b, dx2)));
-    t[6] = -fp;
-    if (key) *key = fminf(__fmul_rn(mr3, __fsqrt_rn(d2)), FLT_MAX);
-    return r2 != 0.0f;
-}
-
-__device__ __forceinline__ void load_i(const JDS &J, int i, float xh[3], float xl[3], float vi[3])
-{
-    const float4 p = J.pos_hi[i], l = J.pos_lo[i], v = J.vel[i];
-    xh[0] = p.x; xh[1] = p.y; xh[2] = p.z;
-    xl[0] = l.x; xl[1] = l.y; xl[2] = l.z;
-    vi[0] = v.x; vi[1] = v.y; vi[2] = v.z;
-}
-
-// ---------------------------------------------------------------------------
-// Fixed point
-
-struct Scale {
-    float sc[3];    // 2^s: acc, jerk, pot
-    double inv[3];  // 2^-s
-};
-
-__device__ __forceinline__ int exp_above(unsigned bits)
-{
-    const int be = (int)((bits >> 23) & 0xFF);
-    return be == 0 ? -126 : be - 126;
-}
-
-__device__ __forceinline__ int floor_half(int a) { return a >= 0 ? a / 2 : -((1 - a) / 2); }
-
-// Scales from the bounds.  With eps2 >= 2^F, every mass < 2^Em and every
-// |vx| + |vy| + |vz| < 2^Ev (Em, Ev at least -64), the terms obey
-//   |acc| <= mj / r^2 < 2^(Em - F),   |pot| = mj / r < 2^(Em - floor(F/2)),
-//   |jerk| <= 4 mj |dv| / r^3 < 2^(3 + Em + Ev - floor(3F/2))
-// up to single-precision rounding, which the factor 2 between 2^56 and 2^57
-// absorbs; s = min(56 - e, 126).  False when eps2 is not a normal float or a
-// scale falls below -126.
-__device__ __forceinline__ bool fixed_scale(const unsigned *bounds, float eps2, Scale &S)
-{
-    const int be = (int)((__float_as_uint(eps2) >> 23) & 0xFF);
-    if (be == 0 || be == 255) return false;
-    const int F = be - 127;
-    const int Em = max(exp_above(bounds[0]), -64), Ev = max(exp_above(bounds[1]), -64);
-    const int e[3] = {Em - F, 3 + Em + Ev - floor_half(3 * F), Em - floor_half(F)};
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const int s = min(56 - e[q], 126);
-        if (s < -126) return false;
-        S.sc[q] = __int_as_float((s + 127) << 23);
-        S.inv[q] = __longlong_as_double((long long)(1023 - s) << 52);
-    }
-    return true;
-}
-
 // The largest single-precision mass and |vx| + |vy| + |vz| over all j, as
 // float bits (non-negative floats order like their bits); bounds[] must be
 // zero on entry.
@@ -141,61 +57,6 @@ __global__ void k_fixed_bounds(JDS J, int n, unsigned *bounds)
         atomicMax(&bounds[0], mb);
         atomicMax(&bounds[1], vb);
     }
-}
-
-// Exact integer rounding of a term |t| < 2^57 - 2^34 on the FP32 pipe.  For
-// C = 1.5 * 2^(23+g), s = fl(t + C) stays in C's binade while |t| < 2^(22+g),
-// so s - C is t rounded to a multiple of 2^g and bits(s) - bits(C) is that
-// multiple's count.  With g = 35, 13 and 0:
-//   s1 = fl(t + C1),  r  = t - (s1 - C1)      |r|  <= 2^34, exact
-//   s2 = fl(r + C2),  r2 = r - (s2 - C2)      |r2| <= 2^12, exact
-//   s3 = fl(r2 + C3)                          r2 rounded half to even
-// and round_half_even(t) = a1 2^35 + a2 2^13 + a3 with a_k = bits(s_k) -
-// bits(C_k) (the first two parts are even, so the tie rule carries over).  A
-// tile adds the raw bit patterns in 32 bits (mod 2^32) and subtracts the
-// constants once: the true sums stay below 2^28 in magnitude.
-constexpr float kC1 = 0x1.8p58f, kC2 = 0x1.8p36f, kC3 = 0x1.8p23f;
-
-__device__ __forceinline__ void split_add(float t, unsigned &a1, unsigned &a2, unsigned &a3)
-{
-    const float s1 = __fadd_rn(t, kC1);
-    const float r = __fsub_rn(t, __fsub_rn(s1, kC1));
-    const float s2 = __fadd_rn(r, kC2);
-    const float r2 = __fsub_rn(r, __fsub_rn(s2, kC2));
-    const float s3 = __fadd_rn(r2, kC3);
-    a1 += __float_as_uint(s1);
-    a2 += __float_as_uint(s2);
-    a3 += __float_as_uint(s3);
-}
-
-// The integer sum of a tile of `cnt` split terms.
-__device__ __forceinline__ long long tile_sum(unsigned a1, unsigned a2, unsigned a3, unsigned cnt)
-{
-    const int q1 = (int)(a1 - cnt * __float_as_uint(kC1));
-    const int q2 = (int)(a2 - cnt * __float_as_uint(kC2));
-    const int q3 = (int)(a3 - cnt * __float_as_uint(kC3));
-    return ((long long)q1 << 35) + ((long long)q2 << 13) + (long long)q3;
-}
-
-// (hi, lo) += x, a 128-bit two's-complement sum.
-__device__ __forceinline__ void add128(long long &hi, unsigned long long &lo, long long x)
-{
-    const unsigned long long l2 = lo + (unsigned long long)x;
-    hi += (x >> 63) + (l2 < lo ? 1 : 0);
-    lo = l2;
-}
-
-// |Y| = H 2^64 + L  ->  fl64(fl64(H) 2^64 + fl64(L)), with Y's sign.
-__device__ __forceinline__ double i128_to_double(long long hi, unsigned long long lo)
-{
-    const bool neg = hi < 0;
-    if (neg) {
-        lo = ~lo + 1ULL;
-        hi = ~hi + (lo == 0ULL ? 1 : 0);
-    }
-    const double d = __dadd_rn(__dmul_rn(__ull2double_rn((unsigned long long)hi), 0x1p64),
-                               __ull2double_rn(lo));
-    return neg ? -d : d;
 }
 
 __device__ __forceinline__ Plan plan_fixed(int na, const ForceArgs &fa, const SumArgs &sa)

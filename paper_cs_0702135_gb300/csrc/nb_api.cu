@@ -45,6 +45,13 @@ struct nb_ctx {
 
     int slots_ipar = 0, slots_jpar = 0, slots_small = 0, jpar_max = 0, small_max = 0;
     SumArgs sum{};                  // summation variant (NB_SUM_COMPENSATED: unused)
+    // persistent nb_run (k_run.cu), allocated on first use
+    double *d_run_part = nullptr;
+    long long *d_run_mins = nullptr;
+    int *d_run_counts = nullptr;
+    unsigned *d_run_maxs = nullptr;
+    unsigned long long *d_run_bar = nullptr;
+    int run_ncta = 0, run_per = 0;
     unsigned *d_bounds = nullptr;   // fixed point: mass and velocity bounds
     unsigned long long *d_sort = nullptr;  // sorted: keyed items, 2n per resident CTA
     long long t_pred = 0;           // ticks of the last host-driven prediction
@@ -149,6 +156,8 @@ int sync_ctrl(nb_ctx *c)
         CK(cudaStreamSynchronize(c->st));
         if (e == NB_ESTEP) return fail(c, NB_ESTEP, "a new time step fell below 2^-40");
         if (e == NB_EINVAL) return fail(c, NB_EINVAL, "invalid particle index (device check)");
+        if (e == NB_ETIMEOUT)
+            return fail(c, NB_ETIMEOUT, "a grid barrier of the persistent run waited too long");
         if (e == kErrFixedScale)
             return fail(c, NB_EINVAL, "fixed-point summation: masses, velocities or eps put the "
                                       "fixed-point units outside the single-precision range");
@@ -298,7 +307,8 @@ void release(nb_ctx *c)
                     c->d_act, c->d_idx, c->d_all, c->d_bitmap, c->d_ctrl, c->d_blockmin,
                     c->d_blockcnt, c->d_epart, c->d_stage, c->d_ck, c->d_seg, c->d_fin, c->d_tfin,
                     c->d_cot, c->vrec.ph, c->vrec.pl, c->vrec.v, c->vrec.ab, c->vrec.kb,
-                    c->vrec64.x, c->vrec64.v, c->vrec64.ab, c->vrec64.kb, c->d_bounds, c->d_sort};
+                    c->vrec64.x, c->vrec64.v, c->vrec64.ab, c->vrec64.kb, c->d_bounds, c->d_sort,
+                    c->d_run_part, c->d_run_mins, c->d_run_counts, c->d_run_maxs, c->d_run_bar};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
@@ -380,6 +390,54 @@ int copy_results_out(nb_ctx *c, int na, double *acc, double *jerk, double *pot, 
     return NB_OK;
 }
 
+// nb_run in one persistent launch (k_run.cu) when the system is small enough:
+// NB_OK or an error code, or kRunNotUsed when this context uses the
+// per-stage graph instead.
+constexpr int kRunNotUsed = 1;
+
+int run_persistent(nb_ctx *c, long long te, long long max_steps)
+{
+    if (c->n > kRunMaxN || c->o.precision != NB_DS || (c->o.flags & NB_RUN_GRAPH) ||
+        (c->o.summation != NB_SUM_COMPENSATED && c->o.summation != NB_SUM_FIXED))
+        return kRunNotUsed;
+    if (!c->d_run_bar) {
+        int bps = 0;
+        if (occupancy_run(c->o.summation, &bps) ||
+            run_layout(c->n, c->sms, bps, &c->run_ncta, &c->run_per))
+            return kRunNotUsed;
+        const long long C = c->run_ncta, N = c->n;
+        int rc;
+        if ((rc = dalloc(c, &c->d_run_part, C * N * 2 * kComp)) || (rc = dalloc(c, &c->d_run_mins, C)) ||
+            (rc = dalloc(c, &c->d_run_counts, C)) || (rc = dalloc(c, &c->d_run_maxs, 2 * C)) ||
+            (rc = dalloc(c, &c->d_run_bar, 1)))
+            return rc;
+    }
+    RunArgs ra{};
+    ra.s = c->S;
+    ra.j = c->jds;
+    ra.ctrl = c->d_ctrl;
+    ra.n = c->n;
+    ra.ncta = c->run_ncta;
+    ra.per = c->run_per;
+    ra.eps2f = (float)(c->eps * c->eps);
+    ra.eta = c->o.eta;
+    ra.level_min = c->o.level_min;
+    ra.level_fixed = c->o.level_fixed;
+    ra.t_end = te;
+    ra.max_steps = max_steps;
+    ra.act = c->d_act;
+    ra.mins = c->d_run_mins;
+    ra.counts = c->d_run_counts;
+    ra.maxs = c->d_run_maxs;
+    ra.part = c->d_run_part;
+    ra.bar = c->d_run_bar;
+    CK(cudaMemsetAsync(c->d_run_bar, 0, sizeof(unsigned long long), c->st));
+    const cudaError_t e = launch_run(ra, c->o.summation, c->st);
+    if (e != cudaSuccess) return fail(c, NB_ECUDA, "persistent run launch: %s", cudaGetErrorString(e));
+    c->launches += 1;
+    return sync_ctrl(c);
+}
+
 }  // namespace
 
 extern "C" {
@@ -435,7 +493,7 @@ static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, con
         return fail(c, NB_EINVAL, "precision must be NB_DS or NB_FP64");
     if (o.force_mode < NB_FORCE_AUTO || o.force_mode > NB_FORCE_JPAR)
         return fail(c, NB_EINVAL, "bad force_mode");
-    if (o.split_j < 0 || (o.flags & ~NB_INIT_NO_FORCE) != 0)
+    if (o.split_j < 0 || (o.flags & ~(NB_INIT_NO_FORCE | NB_RUN_GRAPH)) != 0)
         return fail(c, NB_EINVAL, "bad split_j or flags");
     if (o.summation < NB_SUM_COMPENSATED || o.summation > NB_SUM_FP32_SORTED)
         return fail(c, NB_EINVAL, "bad summation");
@@ -709,6 +767,14 @@ int nb_run(nb_ctx *c, double t_end, int64_t max_steps, int64_t *steps_out, int64
     if (rc) return rc;
     if ((rc = sync_ctrl(c))) return rc;
     const long long steps0 = c->h_ctrl->steps, inter0 = c->h_ctrl->interactions;
+    c->force_valid = false;
+    rc = run_persistent(c, te, max_steps);
+    if (rc != kRunNotUsed) {
+        if (rc) return rc;
+        if (steps_out) *steps_out = c->h_ctrl->steps - steps0;
+        if (inter_out) *inter_out = c->h_ctrl->interactions - inter0;
+        return set_t_end(c, LLONG_MAX);
+    }
     if (!c->step_exec) {
         cudaGraph_t g;
         CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));

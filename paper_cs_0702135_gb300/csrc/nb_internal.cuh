@@ -221,6 +221,28 @@ constexpr int kSeqNT = 128;         // FP32 index order: threads per CTA, one i 
 constexpr int kSortNT = 1024;       // FP32 sorted: one CTA per i
 constexpr int kErrFixedScale = 64;  // device error word: fixed-point scales out of range
 
+// Persistent block-step loop (k_run.cu): nb_run in one cooperative launch for
+// systems of up to kRunMaxN particles, kRunNT threads per CTA, one CTA per
+// `per` particles.
+constexpr int kRunNT = 256;
+constexpr int kRunMaxN = 16384;
+struct RunArgs {
+    State s;
+    JDS j;
+    Ctrl *ctrl;
+    int n, ncta, per;            // particles, CTAs, particles per CTA (<= kRunNT)
+    float eps2f;                 // single-precision eps^2 of the pair terms
+    double eta;
+    int level_min, level_fixed;
+    long long t_end, max_steps;  // stop before a block time past t_end, or after max_steps steps
+    int *act;                    // [n] block list
+    long long *mins;             // [ncta] per-CTA minimum end time
+    int *counts;                 // [ncta] per-CTA block count
+    unsigned *maxs;              // [2 ncta] fixed point: per-CTA mass and |v|_1 bounds (float bits)
+    double *part;                // [ncta][n][7] partials (fixed point: pairs of int64)
+    unsigned long long *bar;     // grid-barrier arrivals (zero at launch)
+};
+
 // Reverse mode (k_adjoint.cu).  Force-VJP records: DS (x_hi, y_hi, z_hi, m),
 // (x_lo, y_lo, z_lo, 0), (vx, vy, vz, 0), (abar, 0), (kbar, 0); FP64 (x, y,
 // z, m), (v, 0), (abar, 0), (kbar, 0).
@@ -260,6 +282,11 @@ int occupancy_sum(int mode, int *blocks_per_sm);
 int grid_summed(const ForceArgs &fa, const SumArgs &sa);
 int launch_force_summed(const ForceArgs &fa, const JDS &j, const SumArgs &sa, int grid,
                         cudaStream_t st);
+
+// k_run.cu
+int run_layout(int n, int sms, int blocks_per_sm, int *ncta, int *per);
+int occupancy_run(int summation, int *blocks_per_sm);
+cudaError_t launch_run(const RunArgs &ra, int summation, cudaStream_t st);
 
 // k_step.cu
 void launch_predict(const State &s, long long t_val, const long long *t_ptr, const int *gate,

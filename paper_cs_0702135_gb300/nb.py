@@ -26,6 +26,7 @@ NB_FORCE_AUTO, NB_FORCE_IPAR, NB_FORCE_JPAR = 0, 1, 2
 NB_SUM_COMPENSATED, NB_SUM_FIXED, NB_SUM_FP32, NB_SUM_FP32_SORTED = 0, 1, 2, 3
 NB_TICK_BITS = 40
 NB_INIT_NO_FORCE = 1
+NB_RUN_GRAPH = 2
 NB_NOALLOC_MAX_ACTIVE = 64
 TICKS_PER_UNIT = 1 << NB_TICK_BITS
 

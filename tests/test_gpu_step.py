@@ -159,8 +159,9 @@ def test_energy_one_time_unit(nb, precision):
 
 
 def test_run_equals_step_loop_bitwise(nb):
+    # the graph-replayed nb_run and nb_step enqueue the same kernels
     m, x, v = plummer(700, 5)
-    ctx_a = nb.nb_init(m, x, v, EPS)
+    ctx_a = nb.nb_init(m, x, v, EPS, nb.nb_default_opts(flags=nb.NB_RUN_GRAPH))
     ctx_b = nb.nb_init(m, x, v, EPS)
     try:
         steps, _ = nb.nb_run(ctx_a, 0.125)
