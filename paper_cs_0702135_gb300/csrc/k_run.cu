@@ -23,7 +23,8 @@
 // wrote in the same launch is read past L1 (__ldcg).  Two summations: the
 // compensated double-single sums (TwoSum-promoted FP32 partials, FP64 across
 // CTAs) and the GRAPE-style fixed-point sums of k_sum.cu (exact, so the run is
-// bit-identical to the kernel-per-stage path and to the oracle).
+// bit-identical to the kernel-per-stage path and to any IEEE evaluation of the
+// same sums).
 #include <climits>
 
 #include "nb_device.cuh"
