@@ -3,7 +3,7 @@
 // systems small enough that a step is mostly launch latency on the
 // kernel-per-stage path.
 //
-// CTA r owns particles [r P, (r + 1) P).  One block step is three phases
+// CTA r owns particles [r P, (r + 1) P).  One block step is four phases
 // separated by grid barriers (a counter in global memory, added to with
 // release and read with acquire semantics; each wait ends after about 2 s
 // with NB_ETIMEOUT, and the cooperative launch keeps every CTA resident):
@@ -17,10 +17,11 @@
 //      |vx|+|vy|+|vz|);
 //   3. force partials: every CTA sums every block particle's pair terms over
 //      its own particles as j and writes them per (CTA, block particle);
-// then each CTA adds the partials of its own block particles in CTA order,
-// corrects them (FP64 corrector and Aarseth step) and starts the next step.
-// Nothing but the owner writes a particle's state, and everything other CTAs
-// wrote in the same launch is read past L1 (__ldcg).  Two summations: the
+//   4. block particle a is corrected by CTA a mod (CTAs): its partials added in
+//      CTA order, FP64 corrector and Aarseth step.  The corrector's FP64 chain
+//      is long, so spreading the block evenly keeps every CTA's share short.
+// Everything that other CTAs wrote in the same launch (state included, since
+// a particle may be corrected by any CTA) is read past L1 (__ldcg).  Two summations: the
 // compensated double-single sums (TwoSum-promoted FP32 partials, FP64 across
 // CTAs) and the GRAPE-style fixed-point sums of k_sum.cu (exact, so the run is
 // bit-identical to the kernel-per-stage path and to any IEEE evaluation of the
@@ -39,7 +40,7 @@ constexpr long long kRunSpinCycles = 4000000000LL;  // about 2 s at 2 GHz
 
 __device__ __forceinline__ long long end_time_of(const State &s, int i)
 {
-    return s.t[i] + (1LL << (kTickBits - s.lev[i]));
+    return __ldcg(&s.t[i]) + (1LL << (kTickBits - __ldcg(&s.lev[i])));
 }
 
 __device__ __forceinline__ void arrive_release(unsigned long long *p)
@@ -266,13 +267,12 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
         }
         na = cta_reduce_r(na, AddR(), s_red);
         off = cta_reduce_r(off, AddR(), s_red);
-        const int cnt = mn == tn ? cnt_min : 0;
         if (at_min && mn == tn) ra.act[off + woff + __popc(bal & ((1u << lane) - 1u))] = i0 + tid;
         unsigned mb = 0, vb = 0;
         if (tid < m) {
             const int i = i0 + tid;
             double xp[3], vp[3];
-            predict3(S, i, n, ticks_to_time(tn - S.t[i]), xp, vp);
+            predict3<true>(S, i, n, ticks_to_time(tn - __ldcg(&S.t[i])), xp, vp);
             float h[3], l[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) split_ds(xp[c], h[c], l[c]);
@@ -325,7 +325,8 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
         }
         if (!grid_barrier(ra, target, &s_ok)) return;
 
-        // 5. own block particles: partials in CTA order, corrector, new steps
+        // 5. block particles a = r, r + CTAs, ...: partials in CTA order,
+        // corrector, new steps
         Scale Sc;
         bool scale_ok = true;
         if (MODE == NB_SUM_FIXED) {
@@ -339,8 +340,8 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
             const unsigned bounds[2] = {bm, bv};
             scale_ok = fixed_scale(bounds, ra.eps2f, Sc);
         }
-        if (tid < cnt && scale_ok) {
-            const long long a = off + tid;
+        for (long long a = r + (long long)ra.ncta * tid; scale_ok && a < na;
+             a += (long long)ra.ncta * kRunNT) {
             double res[7];
             if (MODE == NB_SUM_FIXED) {
                 const long long *part = reinterpret_cast<const long long *>(ra.part);
@@ -367,7 +368,7 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
             }
             const double ap[3] = {res[0], res[1], res[2]}, kp[3] = {res[3], res[4], res[5]};
             const int i = (int)__ldcg(&ra.act[a]);
-            if (!correct_particle(S, i, n, tn, ap, kp, ra.eta, ra.level_min, ra.level_fixed))
+            if (!correct_particle<true>(S, i, n, tn, ap, kp, ra.eta, ra.level_min, ra.level_fixed))
                 atomicCAS(&ra.ctrl->err, 0, NB_ESTEP);
         }
         ++steps;
@@ -378,9 +379,8 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
             ra.ctrl->steps += 1;
             ra.ctrl->interactions += na * (long long)(n - 1);
         }
-        // the corrected t_i and levels were written by other threads of this
-        // CTA: phase 1 of the next step reads them
-        __syncthreads();
+        // the owners read the corrected state in the next step's phase 1
+        if (!grid_barrier(ra, target, &s_ok)) return;
     }
 }
 

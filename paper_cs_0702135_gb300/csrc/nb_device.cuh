@@ -68,15 +68,25 @@ __device__ __forceinline__ void predict1(double x, double v, double a, double k,
     predict1hq(x, v, a, k, dt, __dmul_rn(dt, 0.5), __ddiv_rn(dt, 3.0), xp, vp);
 }
 
+// State loads: plain, or past L1 (CG) for state that other SMs may have
+// written earlier in the same launch.
+template <bool CG, typename T>
+__device__ __forceinline__ T ldst(const T *p)
+{
+    if (CG) return __ldcg(p);
+    return *p;
+}
+
 // All three axes of particle i of `s` (component-major, stride n).
+template <bool CG = false>
 __device__ __forceinline__ void predict3(const State &s, long long i, long long n, double dt,
                                          double xp[3], double vp[3])
 {
     const double h = __dmul_rn(dt, 0.5), q = __ddiv_rn(dt, 3.0);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-        predict1hq(s.x[c * n + i], s.v[c * n + i], s.a[c * n + i], s.k[c * n + i], dt, h, q, xp[c],
-                   vp[c]);
+        predict1hq(ldst<CG>(&s.x[c * n + i]), ldst<CG>(&s.v[c * n + i]), ldst<CG>(&s.a[c * n + i]),
+                   ldst<CG>(&s.k[c * n + i]), dt, h, q, xp[c], vp[c]);
 }
 
 // A predicted FP64 position split into double-single: x = hi + lo to 2^-48.
@@ -137,17 +147,19 @@ __device__ __forceinline__ double initial_dt(const double a[3], const double k[3
 // quantised by level_of and next_level (level_fixed > 0 keeps that level).
 // x_p, v_p are recomputed with predict1, bit for bit the values the force
 // saw.  Returns false when the new step fell below 2^-40.
+template <bool CG = false>
 __device__ __forceinline__ bool correct_particle(const State &s, long long i, long long stride,
                                                  long long tn, const double ap[3], const double kp[3],
                                                  double eta, int level_min, int level_fixed)
 {
-    const double dt = ticks_to_time(tn - s.t[i]);
+    const double dt = ticks_to_time(tn - ldst<CG>(&s.t[i]));
     const double h = __dmul_rn(dt, 0.5), q = __ddiv_rn(dt, 3.0);
     double a2[3], a3[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const long long e = c * stride + i;
-        const double x = s.x[e], v = s.v[e], a = s.a[e], k = s.k[e];
+        const double x = ldst<CG>(&s.x[e]), v = ldst<CG>(&s.v[e]), a = ldst<CG>(&s.a[e]),
+                     k = ldst<CG>(&s.k[e]);
         double xp, vp;
         predict1hq(x, v, a, k, dt, h, q, xp, vp);
         const double d = __dsub_rn(a, ap[c]);
@@ -155,7 +167,8 @@ __device__ __forceinline__ bool correct_particle(const State &s, long long i, lo
         a2[c] = __dsub_rn(__dmul_rn(-3.0, d), __dmul_rn(__dadd_rn(__dmul_rn(2.0, k), kp[c]), dt));
         s.x[e] = __dadd_rn(xp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[c], 12.0), __ddiv_rn(a3[c], 20.0)),
                                          __dmul_rn(dt, dt)));
-        s.v[e] = __dadd_rn(vp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[c], 3.0), __ddiv_rn(a3[c], 4.0)), dt));
+        // a3 / 4 as a3 * 0.25: the same real number, so the same rounded result
+        s.v[e] = __dadd_rn(vp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[c], 3.0), __dmul_rn(a3[c], 0.25)), dt));
         s.a[e] = ap[c];
         s.k[e] = kp[c];
     }
@@ -166,11 +179,18 @@ __device__ __forceinline__ bool correct_particle(const State &s, long long i, lo
     }
     const double dt2 = __dmul_rn(dt, dt);
     const double dt3 = __dmul_rn(dt2, dt);
+    // A block step is a power of two: dividing by dt^2 and dt^3 is then the
+    // same real number as multiplying by their exact reciprocals (powers of
+    // two, from the exponent field), so the rounded results are identical and
+    // four FP64 divisions per axis leave the latency chain.
+    const bool pow2 = (__double_as_longlong(dt) & 0x000FFFFFFFFFFFFFLL) == 0 && dt > 0x1p-100;
+    const double r2 = pow2 ? __longlong_as_double((2046LL << 52) - (__double_as_longlong(dt2) & 0x7FF0000000000000LL)) : 0.0;
+    const double r3 = pow2 ? __longlong_as_double((2046LL << 52) - (__double_as_longlong(dt3) & 0x7FF0000000000000LL)) : 0.0;
     double s1[3], cr[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double s0 = __ddiv_rn(__dmul_rn(2.0, a2[c]), dt2);
-        cr[c] = __ddiv_rn(__dmul_rn(6.0, a3[c]), dt3);
+        const double s0 = pow2 ? __dmul_rn(__dmul_rn(2.0, a2[c]), r2) : __ddiv_rn(__dmul_rn(2.0, a2[c]), dt2);
+        cr[c] = pow2 ? __dmul_rn(__dmul_rn(6.0, a3[c]), r3) : __ddiv_rn(__dmul_rn(6.0, a3[c]), dt3);
         s1[c] = __dadd_rn(s0, __dmul_rn(cr[c], dt));
     }
     const double na = norm3(ap[0], ap[1], ap[2]);
@@ -183,7 +203,7 @@ __device__ __forceinline__ bool correct_particle(const State &s, long long i, lo
     int kq;
     const bool ok = level_of(dt_raw, level_min, kq);
     if (!ok) kq = kTickBits;
-    s.lev[i] = next_level(s.lev[i], kq, tn, level_min);
+    s.lev[i] = next_level(ldst<CG>(&s.lev[i]), kq, tn, level_min);
     return ok;
 }
 
