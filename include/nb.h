@@ -195,6 +195,17 @@ int nb_run(nb_ctx *ctx, double t_end, int64_t max_steps, int64_t *steps_out,
            int64_t *interactions_out);
 
 /*
+ * Self-test of failure detection (the paper has no counterpart): one device
+ * thread runs the bounded wait that the persistent nb_run's grid barriers use,
+ * on a counter that nothing increments, with a limit of about `ms`
+ * milliseconds of SM clock.  The wait runs out, the kernel raises NB_ETIMEOUT
+ * in the context's error word and returns, and the call reports it; the
+ * context stays usable.  Returns NB_ETIMEOUT when the wait ran out as it must.
+ * Errors: NB_EINVAL (ms outside [1, 2000]), NB_ECUDA.
+ */
+int nb_check_wait(nb_ctx *ctx, int32_t ms);
+
+/*
  * Total energy of the system predicted to the current system time (exact when
  * all particles are synchronised): *ekin = 1/2 sum m v^2 (FP64) and
  * *epot = 1/2 sum m_i pot_i from a full force sweep (the softened potential

@@ -38,6 +38,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "nb_device.cuh"
 
 namespace nbk {
@@ -498,6 +500,12 @@ namespace ens_impl {
 
 thread_local std::string g_ens_init_err;
 
+// An NVTX range over one entry point (no cost unless a tool is attached).
+struct EnsRange {
+    explicit EnsRange(const char *name) { nvtxRangePushA(name); }
+    ~EnsRange() { nvtxRangePop(); }
+};
+
 int efail(nb_ens *e, int code, const char *fmt, ...)
 {
     if (e) {
@@ -751,6 +759,7 @@ extern "C" {
 int nb_ens_init(nb_ens **ens, int32_t n_clusters, const int64_t *offsets, const double *m,
                 const double *x, const double *v, double eps, const nb_opts *opts)
 {
+    const EnsRange range_("nb_ens_init");
     g_ens_init_err.clear();
     if (!ens) return NB_EINVAL;
     *ens = nullptr;
@@ -794,6 +803,7 @@ int nb_ens_configure(nb_ens *e, int threads, int gmax)
 int nb_ens_run(nb_ens *e, double t_end, int64_t max_launches, int64_t *launches_out,
                int64_t *interactions_out)
 {
+    const EnsRange range_("nb_ens_run");
     if (!e) return NB_EINVAL;
     if (!std::isfinite(t_end) || t_end < 0.0 || t_end >= 0x1p22 || t_end * 0x1p40 != std::floor(t_end * 0x1p40))
         return efail(e, NB_EINVAL, "t_end is not on the 2^-40 grid");
@@ -860,6 +870,7 @@ int nb_ens_run(nb_ens *e, double t_end, int64_t max_launches, int64_t *launches_
 int nb_ens_tune(nb_ens *e, int launches_per_candidate, int *threads_out, int *gmax_out,
                 double *ms_out)
 {
+    const EnsRange range_("nb_ens_tune");
     if (!e) return NB_EINVAL;
     if (launches_per_candidate < 1) return efail(e, NB_EINVAL, "launches_per_candidate < 1");
     const long long P = e->P, C = e->C;
@@ -929,6 +940,7 @@ int nb_ens_tune(nb_ens *e, int launches_per_candidate, int *threads_out, int *gm
 
 int nb_ens_step(nb_ens *e)
 {
+    const EnsRange range_("nb_ens_step");
     if (!e) return NB_EINVAL;
     int rc = enqueue_ens_step(e);
     if (rc) return rc;
@@ -937,6 +949,7 @@ int nb_ens_step(nb_ens *e)
 
 int nb_ens_force(nb_ens *e, double *acc, double *jerk, double *pot)
 {
+    const EnsRange range_("nb_ens_force");
     if (!e) return NB_EINVAL;
     const long long P = e->P;
     EnsArgs a = ens_args(e);
@@ -953,6 +966,7 @@ int nb_ens_force(nb_ens *e, double *acc, double *jerk, double *pot)
 
 int nb_ens_energy(nb_ens *e, double *ekin, double *epot)
 {
+    const EnsRange range_("nb_ens_energy");
     if (!e) return NB_EINVAL;
     double *d = e->d_stage;
     k_ens_energy<256><<<std::max(1, std::min(e->C, 8 * e->sms)), 256, 0, e->st>>>(

@@ -55,32 +55,44 @@ __device__ __forceinline__ unsigned long long load_acquire(const unsigned long l
     return v;
 }
 
+// Bounded wait (one thread): until *p >= target, read with acquire semantics;
+// false after `limit` SM cycles.  Spins first, then sleeps between reads.
+__device__ __forceinline__ bool wait_counter(const unsigned long long *p, unsigned long long target,
+                                             long long limit)
+{
+    const long long t0 = clock64();
+    int spins = 0;
+    while (load_acquire(p) < target) {
+        if (++spins > 256) {
+            if (clock64() - t0 > limit) return false;
+            __nanosleep(64);
+        }
+    }
+    return true;
+}
+
 // Grid barrier: thread 0 of every CTA adds one arrival (release: the CTA's
 // writes, ordered before it by __syncthreads, become visible first) and waits
 // (acquire) until all CTAs' arrivals for this barrier are in.  False when the
-// wait ran out.
+// wait ran out (error NB_ETIMEOUT).
 __device__ __forceinline__ bool grid_barrier(const RunArgs &ra, unsigned long long &target, int *s_ok)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         target += (unsigned long long)ra.ncta;
         arrive_release(ra.bar);
-        const long long t0 = clock64();
-        int ok = 1, spins = 0;
-        while (load_acquire(ra.bar) < target) {
-            if (++spins > 256) {
-                if (clock64() - t0 > kRunSpinCycles) {
-                    atomicCAS(&ra.ctrl->err, 0, NB_ETIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
+        const bool ok = wait_counter(ra.bar, target, kRunSpinCycles);
+        if (!ok) atomicCAS(&ra.ctrl->err, 0, NB_ETIMEOUT);
         *s_ok = ok;
     }
     __syncthreads();
     return *s_ok != 0;
+}
+
+// The same wait on a counter that nothing increments, for nb_check_wait.
+__global__ void k_check_wait(const unsigned long long *counter, long long limit, Ctrl *ctrl)
+{
+    if (!wait_counter(counter, 1ULL, limit)) atomicCAS(&ctrl->err, 0, NB_ETIMEOUT);
 }
 
 template <typename T, typename Op>
@@ -406,6 +418,13 @@ int occupancy_run(int summation, int *blocks_per_sm)
             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_run<NB_SUM_FIXED>, kRunNT, 0)
             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_run<NB_SUM_COMPENSATED>, kRunNT, 0);
     return e == cudaSuccess ? 0 : -1;
+}
+
+cudaError_t launch_check_wait(const unsigned long long *counter, long long limit_cycles, Ctrl *ctrl,
+                              cudaStream_t st)
+{
+    k_check_wait<<<1, 1, 0, st>>>(counter, limit_cycles, ctrl);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_run(const RunArgs &ra, int summation, cudaStream_t st)

@@ -10,9 +10,19 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "nb_internal.cuh"
 
 using namespace nbk;
+
+namespace {
+// An NVTX range over one entry point (no cost unless a tool is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+}  // namespace
 
 struct nb_ctx {
     int n = 0;
@@ -157,7 +167,7 @@ int sync_ctrl(nb_ctx *c)
         if (e == NB_ESTEP) return fail(c, NB_ESTEP, "a new time step fell below 2^-40");
         if (e == NB_EINVAL) return fail(c, NB_EINVAL, "invalid particle index (device check)");
         if (e == NB_ETIMEOUT)
-            return fail(c, NB_ETIMEOUT, "a grid barrier of the persistent run waited too long");
+            return fail(c, NB_ETIMEOUT, "a bounded device wait ran out");
         if (e == kErrFixedScale)
             return fail(c, NB_EINVAL, "fixed-point summation: masses, velocities or eps put the "
                                       "fixed-point units outside the single-precision range");
@@ -623,6 +633,7 @@ static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, con
 int nb_init(nb_ctx **ctx, int64_t n, const double *m, const double *x, const double *v,
             double eps, const nb_opts *opts)
 {
+    const Range range_("nb_init");
     g_init_err.clear();
     if (!ctx) {
         g_init_err = "ctx is NULL";
@@ -646,6 +657,7 @@ int nb_init(nb_ctx **ctx, int64_t n, const double *m, const double *x, const dou
 
 int nb_predict(nb_ctx *c, double t)
 {
+    const Range range_("nb_predict");
     if (!c) return NB_EINVAL;
     long long ticks;
     if (!time_to_ticks(t, &ticks)) return fail(c, NB_EINVAL, "t=%.17g is not on the 2^-40 grid", t);
@@ -659,6 +671,7 @@ int nb_predict(nb_ctx *c, double t)
 
 int nb_force(nb_ctx *c, const int32_t *idx, int32_t na, double *acc, double *jerk, double *pot)
 {
+    const Range range_("nb_force");
     if (!c) return NB_EINVAL;
     int rc = check_indices_host(c, idx, na);
     if (rc) return rc;
@@ -678,6 +691,7 @@ int nb_force(nb_ctx *c, const int32_t *idx, int32_t na, double *acc, double *jer
 int nb_force_dev(nb_ctx *c, const int32_t *d_idx, int32_t na, double *d_acc, double *d_jerk,
                  double *d_pot)
 {
+    const Range range_("nb_force_dev");
     if (!c) return NB_EINVAL;
     if (na < 0 || na > c->n) return fail(c, NB_EINVAL, "n_active=%d outside [0, %d]", na, c->n);
     if (na > 0 && !d_idx) return fail(c, NB_EINVAL, "active_idx is NULL");
@@ -702,6 +716,7 @@ int nb_force_dev(nb_ctx *c, const int32_t *d_idx, int32_t na, double *d_acc, dou
 int nb_correct(nb_ctx *c, const int32_t *idx, int32_t na, double t, const double *acc,
                const double *jerk)
 {
+    const Range range_("nb_correct");
     if (!c) return NB_EINVAL;
     long long ticks;
     if (!time_to_ticks(t, &ticks)) return fail(c, NB_EINVAL, "t=%.17g is not on the 2^-40 grid", t);
@@ -743,6 +758,7 @@ int nb_correct(nb_ctx *c, const int32_t *idx, int32_t na, double t, const double
 
 int nb_step(nb_ctx *c, double *t_out, int32_t *na_out)
 {
+    const Range range_("nb_step");
     if (!c) return NB_EINVAL;
     int rc = set_t_end(c, LLONG_MAX);
     if (rc) return rc;
@@ -759,6 +775,7 @@ int nb_step(nb_ctx *c, double *t_out, int32_t *na_out)
 
 int nb_run(nb_ctx *c, double t_end, int64_t max_steps, int64_t *steps_out, int64_t *inter_out)
 {
+    const Range range_("nb_run");
     if (!c) return NB_EINVAL;
     long long te;
     if (!time_to_ticks(t_end, &te)) return fail(c, NB_EINVAL, "t_end is not on the 2^-40 grid");
@@ -811,8 +828,29 @@ int nb_run(nb_ctx *c, double t_end, int64_t max_steps, int64_t *steps_out, int64
     return set_t_end(c, LLONG_MAX);
 }
 
+int nb_check_wait(nb_ctx *c, int32_t ms)
+{
+    if (!c) return NB_EINVAL;
+    const Range range_("nb_check_wait");
+    if (ms < 1 || ms > 2000) return fail(c, NB_EINVAL, "ms=%d outside [1, 2000]", ms);
+    int dev = 0, khz = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    unsigned long long *counter = nullptr;
+    int rc;
+    if ((rc = dalloc(c, &counter, 1))) return rc;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), c->st);
+    if (e == cudaSuccess) e = launch_check_wait(counter, (long long)ms * (khz > 0 ? khz : 2000000), c->d_ctrl, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    cudaFree(counter);
+    if (e != cudaSuccess) return fail(c, NB_ECUDA, "wait check: %s", cudaGetErrorString(e));
+    c->launches += 1;
+    return sync_ctrl(c);
+}
+
 int nb_energy(nb_ctx *c, double *ekin, double *epot)
 {
+    const Range range_("nb_energy");
     if (!c) return NB_EINVAL;
     launch_predict(c->S, 0, &c->d_ctrl->t_now, nullptr, c->o.precision, c->jds, c->jf, c->st);
     enqueue_full_sweep(c);
@@ -829,6 +867,7 @@ int nb_energy(nb_ctx *c, double *ekin, double *epot)
 
 int nb_get_state(nb_ctx *c, double *x, double *v, double *a, double *k, int64_t *t, int32_t *lev)
 {
+    const Range range_("nb_get_state");
     if (!c) return NB_EINVAL;
     const long long N = c->n;
     launch_gather_state(c->S, c->d_stage, c->d_stage + 3 * N, nullptr, nullptr, c->st);
@@ -854,6 +893,7 @@ int nb_get_state(nb_ctx *c, double *x, double *v, double *a, double *k, int64_t 
 int nb_set_state(nb_ctx *c, const double *x, const double *v, const double *a, const double *k,
                  const int64_t *t, const int32_t *lev)
 {
+    const Range range_("nb_set_state");
     if (!c) return NB_EINVAL;
     if (!x || !v || !a || !k || !t || !lev) return fail(c, NB_EINVAL, "all state arrays are required");
     const long long N = c->n;
@@ -908,6 +948,7 @@ int nb_get_active(nb_ctx *c, int32_t *idx, int32_t cap, int32_t *na, int64_t *t_
 int nb_force_vjp(nb_ctx *c, const double *abar, const double *kbar, double *xbar, double *vbar,
                  double *mbar)
 {
+    const Range range_("nb_force_vjp");
     if (!c) return NB_EINVAL;
     if (!abar || !kbar) return fail(c, NB_EINVAL, "abar and kbar are required");
     const long long N = c->n;
@@ -930,6 +971,7 @@ int nb_force_vjp(nb_ctx *c, const double *abar, const double *kbar, double *xbar
 
 int nb_traj_forward(nb_ctx *c, int64_t steps, int64_t checkpoint_every)
 {
+    const Range range_("nb_traj_forward");
     if (!c) return NB_EINVAL;
     if (c->o.level_fixed <= 0)
         return fail(c, NB_ESTATE, "a trajectory needs the shared step (opts.level_fixed > 0)");
@@ -982,6 +1024,7 @@ int nb_traj_forward(nb_ctx *c, int64_t steps, int64_t checkpoint_every)
 int nb_traj_backward(nb_ctx *c, const double *xbar_T, const double *vbar_T, double *xbar0,
                      double *vbar0, double *mbar)
 {
+    const Range range_("nb_traj_backward");
     if (!c) return NB_EINVAL;
     if (!c->traj_valid) return fail(c, NB_ESTATE, "nb_traj_backward needs nb_traj_forward first");
     if (!xbar_T) return fail(c, NB_EINVAL, "xbar_T is required");

@@ -287,6 +287,8 @@ int launch_force_summed(const ForceArgs &fa, const JDS &j, const SumArgs &sa, in
 int run_layout(int n, int sms, int blocks_per_sm, int *ncta, int *per);
 int occupancy_run(int summation, int *blocks_per_sm);
 cudaError_t launch_run(const RunArgs &ra, int summation, cudaStream_t st);
+cudaError_t launch_check_wait(const unsigned long long *counter, long long limit_cycles, Ctrl *ctrl,
+                              cudaStream_t st);
 
 // k_step.cu
 void launch_predict(const State &s, long long t_val, const long long *t_ptr, const int *gate,

@@ -70,6 +70,7 @@ SIGNATURES = [
     ("nb_force_dev", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, _vp]),
     ("nb_correct", ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_double, _vp, _vp]),
     ("nb_step", ctypes.c_int, [_vp, _c_dp, _c_ip]),
+    ("nb_check_wait", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("nb_run", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int64, _c_lp, _c_lp]),
     ("nb_energy", ctypes.c_int, [_vp, _c_dp, _c_dp]),
     ("nb_get_state", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -218,6 +219,12 @@ def nb_run(ctx, t_end, max_steps=1 << 62):
     it = ctypes.c_int64()
     _check(ctx, lib().nb_run(ctx, float(t_end), int(max_steps), ctypes.byref(s), ctypes.byref(it)))
     return s.value, it.value
+
+
+def nb_check_wait(ctx, ms):
+    """Runs the bounded device wait on a counter nothing sets; raises NbError
+    with NB_ETIMEOUT when the wait ran out, as it must."""
+    _check(ctx, lib().nb_check_wait(ctx, int(ms)))
 
 
 def nb_energy(ctx):
@@ -467,6 +474,9 @@ class Context:
 
     def nb_energy(self):
         return nb_energy(self.ctx)
+
+    def nb_check_wait(self, ms):
+        return nb_check_wait(self.ctx, ms)
 
     def nb_get_state(self):
         return nb_get_state(self.ctx)

@@ -155,3 +155,31 @@ def test_sizes_at_the_edges(nb, n):
     finally:
         a.nb_free()
         b.nb_free()
+
+
+def test_bounded_wait_times_out_and_the_context_stays_usable(nb):
+    # failure detection without a fault: the persistent run's wait loop on a
+    # counter that nothing increments must give up after its limit, report
+    # NB_ETIMEOUT, and leave the context working
+    import time
+    m, x, v = plummer(600, 41)
+    a = nb.Context(m, x, v, EPS, summation=nb.NB_SUM_FIXED)
+    b = nb.Context(m, x, v, EPS, summation=nb.NB_SUM_FIXED)
+    try:
+        t0 = time.perf_counter()
+        with pytest.raises(nb.NbError) as ei:
+            a.nb_check_wait(100)
+        el = time.perf_counter() - t0
+        assert ei.value.code == nb.NB_ETIMEOUT
+        assert 0.05 < el < 3.0
+        with pytest.raises(nb.NbError) as ei:
+            a.nb_check_wait(0)
+        assert ei.value.code == nb.NB_EINVAL
+        a.nb_run(1.0 / 16)
+        b.nb_run(1.0 / 16)
+        ra, rb = a.nb_get_state(), b.nb_get_state()
+        for key in ra:
+            assert np.array_equal(ra[key], rb[key]), key
+    finally:
+        a.nb_free()
+        b.nb_free()
