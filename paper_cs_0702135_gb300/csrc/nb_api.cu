@@ -443,6 +443,11 @@ int run_persistent(nb_ctx *c, long long te, long long max_steps)
     ra.bar = c->d_run_bar;
     CK(cudaMemsetAsync(c->d_run_bar, 0, sizeof(unsigned long long), c->st));
     const cudaError_t e = launch_run(ra, c->o.summation, c->st);
+    if (e == cudaErrorCooperativeLaunchTooLarge) {
+        // not every CTA can be resident now (a shared GPU): use the graph
+        cudaGetLastError();
+        return kRunNotUsed;
+    }
     if (e != cudaSuccess) return fail(c, NB_ECUDA, "persistent run launch: %s", cudaGetErrorString(e));
     c->launches += 1;
     return sync_ctrl(c);
