@@ -419,8 +419,18 @@ int run_persistent(nb_ctx *c, long long te, long long max_steps)
         int rc;
         if ((rc = dalloc(c, &c->d_run_part, C * N * 2 * kComp)) || (rc = dalloc(c, &c->d_run_mins, C)) ||
             (rc = dalloc(c, &c->d_run_counts, C)) || (rc = dalloc(c, &c->d_run_maxs, 2 * C)) ||
-            (rc = dalloc(c, &c->d_run_bar, 1)))
+            (rc = dalloc(c, &c->d_run_bar, 1))) {
+            // all or nothing: a later call starts again from scratch
+            void *ps[] = {c->d_run_part, c->d_run_mins, c->d_run_counts, c->d_run_maxs, c->d_run_bar};
+            for (void *q : ps)
+                if (q) cudaFree(q);
+            c->d_run_part = nullptr;
+            c->d_run_mins = nullptr;
+            c->d_run_counts = nullptr;
+            c->d_run_maxs = nullptr;
+            c->d_run_bar = nullptr;
             return rc;
+        }
     }
     RunArgs ra{};
     ra.s = c->S;
