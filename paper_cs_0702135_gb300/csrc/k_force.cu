@@ -18,8 +18,10 @@
 // every thread reads by broadcast.  j-parallel kernels (small blocks): a CTA
 // owns up to four active i and one j slice, each thread takes every NT-th j,
 // and the CTA reduces with a warp-shuffle tree.  With several j slices the
-// slice partials go to a buffer and a combine kernel sums them in fixed slice
-// order, so results are deterministic and no atomics are used.
+// slice partials go to a buffer and are summed in fixed slice order (by a
+// combine kernel, or, in the DS j-parallel kernel, by the CTA that finishes a
+// chunk's last slice), so results are deterministic and no floating-point
+// atomics are used.
 //
 // The self term j = i is dropped inside the loop: a warp whose own i fall in
 // the current j tile runs a guarded copy of the inner loop that zeroes the
@@ -176,16 +178,58 @@ __global__ void __launch_bounds__(NT) k_force_ipar_ds(ForceArgs fa, JDS J)
 
 // ----------------------------------------------------------------------------
 // DS, j-parallel (small blocks).
+//
+// A CTA owns IC consecutive active i (IC = 1 for blocks of one or two
+// particles, kJparIC otherwise) and one j slice; each thread takes every NT-th
+// j of the slice.  The per-thread partials are reduced over the warp by a
+// reduce-scatter tree (each level halves the number of values a lane carries,
+// so the 7 values of an i cost 9 shuffle steps instead of 35), then over the warps in
+// shared memory.  The CTA that finishes the last slice of an i chunk (an
+// arrival counter per chunk, reset by that CTA) adds the chunk's slice
+// partials in slice order: the result depends only on the plan, and no
+// second launch is needed.
+
+// Lane l ends up holding, for value index e = l >> (5 - log2 P), the DS sum of
+// value e over all 32 lanes; P is a power of two <= 32.
+template <int P>
+__device__ __forceinline__ void warp_reduce_scatter(float (&h)[P], float (&lo)[P], int lane)
+{
+    int c = P;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        if (c > 1) {
+            const bool up = (lane & off) != 0;
+            const int half = c / 2;
+#pragma unroll
+            for (int k = 0; k < P / 2; ++k) {
+                if (k < half) {
+                    const float sh = up ? h[k] : h[k + half], sl = up ? lo[k] : lo[k + half];
+                    float kh = up ? h[k + half] : h[k], kl = up ? lo[k + half] : lo[k];
+                    const float rh = __shfl_xor_sync(0xffffffffu, sh, off);
+                    const float rl = __shfl_xor_sync(0xffffffffu, sl, off);
+                    ds_add(kh, kl, rh, rl);
+                    h[k] = kh;
+                    lo[k] = kl;
+                }
+            }
+            c = half;
+        } else {
+            const float rh = __shfl_xor_sync(0xffffffffu, h[0], off);
+            const float rl = __shfl_xor_sync(0xffffffffu, lo[0], off);
+            ds_add(h[0], lo[0], rh, rl);
+        }
+    }
+}
 
 template <int NT, int IC, bool SOFT>
-__global__ void __launch_bounds__(NT) k_force_jpar_ds(ForceArgs fa, JDS J)
+__device__ __forceinline__ void jpar_ds_items(const ForceArgs &fa, const JDS &J, int na)
 {
-    const int na = read_na(fa);
-    if (na <= 0 || !use_jpar(na, fa.jpar_max)) return;
     const Plan P = plan_jpar(na, fa.n, NT, IC, fa.slots_jpar, fa.part_cap);
     constexpr int NW = NT / 32;
     constexpr int NV = IC * kComp;
     __shared__ float s_h[NW][NV], s_l[NW][NV];
+    __shared__ int s_last;
+    constexpr int UNROLL = IC == 1 ? 4 : 2;   // j in flight per thread
     const float eps2 = (float)fa.eps2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -194,6 +238,7 @@ __global__ void __launch_bounds__(NT) k_force_jpar_ds(ForceArgs fa, JDS J)
         const int sl = w / P.n_iblk;
         const int j0 = sl * P.jslice;
         const int j1 = min(fa.n, j0 + P.jslice);
+        const int nq = min(IC, na - ch * IC);   // i of this chunk (uniform in the CTA)
 
         float xh[IC][3], xl[IC][3], vi[IC][3];
         int ii[IC];
@@ -214,53 +259,78 @@ __global__ void __launch_bounds__(NT) k_force_jpar_ds(ForceArgs fa, JDS J)
             vk[q][0] = vk[q][1] = vk[q][2] = 0.0f;
             vp[q] = 0.0f;
         }
-#pragma unroll 4
+#pragma unroll UNROLL
         for (int j = j0 + tid; j < j1; j += NT) {
             const float4 p = __ldg(&J.pos_hi[j]), l = __ldg(&J.pos_lo[j]), v = __ldg(&J.vel[j]);
 #pragma unroll
             for (int q = 0; q < IC; ++q)
-                pair_ds<SOFT, true>(p, l, v, xh[q], xl[q], vi[q], eps2, va[q], vk[q], vp[q], j, ii[q]);
+                if (q == 0 || q < nq)
+                    pair_ds<SOFT, true>(p, l, v, xh[q], xl[q], vi[q], eps2, va[q], vk[q], vp[q], j, ii[q]);
         }
-        // Warp tree in double-single.  The xor butterfly leaves every lane with
-        // the same value, since TwoSum is exact in either operand order.
-        float h[NV], lo[NV];
+        // one i at a time keeps the live registers down: 8 values (7 and a
+        // zero) per reduce-scatter, lane l ends with value l >> 2
 #pragma unroll
         for (int q = 0; q < IC; ++q) {
-            h[q * kComp + 0] = va[q][0]; h[q * kComp + 1] = va[q][1]; h[q * kComp + 2] = va[q][2];
-            h[q * kComp + 3] = vk[q][0]; h[q * kComp + 4] = vk[q][1]; h[q * kComp + 5] = vk[q][2];
-            h[q * kComp + 6] = vp[q];
-        }
-#pragma unroll
-        for (int e = 0; e < NV; ++e) lo[e] = 0.0f;
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-#pragma unroll
-            for (int e = 0; e < NV; ++e) {
-                const float h2 = __shfl_xor_sync(0xffffffffu, h[e], off);
-                const float l2 = __shfl_xor_sync(0xffffffffu, lo[e], off);
-                ds_add(h[e], lo[e], h2, l2);
-            }
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int e = 0; e < NV; ++e) {
-                s_h[warp][e] = h[e];
-                s_l[warp][e] = lo[e];
+            float h[8] = {va[q][0], va[q][1], va[q][2], vk[q][0], vk[q][1], vk[q][2], vp[q], 0.0f};
+            float lo[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            if (q == 0 || q < nq) {
+                warp_reduce_scatter<8>(h, lo, lane);
+                const int e = lane >> 2;
+                if ((lane & 3) == 0 && e < kComp) {
+                    s_h[warp][q * kComp + e] = h[0];
+                    s_l[warp][q * kComp + e] = lo[0];
+                }
             }
         }
         __syncthreads();
-        if (tid < NV) {
+        if (tid < nq * kComp) {
             float th = s_h[0][tid], tl = s_l[0][tid];
+#pragma unroll
             for (int ww = 1; ww < NW; ++ww) ds_add(th, tl, s_h[ww][tid], s_l[ww][tid]);
-            const int q = tid / kComp, c = tid % kComp;
-            const int a = ch * IC + q;
-            if (a < na) {
-                const double r = (double)th + (double)tl;
-                fa.part[((long long)sl * kComp + c) * na + a] = r;
+            fa.part[((long long)ch * NV + tid) * P.S + sl] = (double)th + (double)tl;
+            __threadfence();
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const int old = atomicAdd(&fa.jcnt[ch], 1);
+            s_last = old == P.S - 1;
+            if (s_last) fa.jcnt[ch] = 0;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            // warp per output: lane l adds slices l, l + 32, ... in four
+            // interleaved chains, then a fixed xor tree
+            for (int e = warp; e < nq * kComp; e += NW) {
+                const double *src = fa.part + (long long)ch * NV * P.S + (long long)e * P.S;
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                int q = lane;
+                for (; q + 96 < P.S; q += 128) {
+                    const double v0 = __ldcg(src + q), v1 = __ldcg(src + q + 32);
+                    const double v2 = __ldcg(src + q + 64), v3 = __ldcg(src + q + 96);
+                    s0 += v0; s1 += v1; s2 += v2; s3 += v3;
+                }
+                for (; q < P.S; q += 32) s0 += __ldcg(src + q);
+                double s = (s0 + s1) + (s2 + s3);
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+                if (lane == 0) {
+                    const int qq = e / kComp, c = e % kComp;
+                    write_combined(fa.out, c, ch * IC + qq, s);
+                }
             }
         }
         __syncthreads();
     }
+}
+
+template <int NT, bool SOFT>
+__global__ void __launch_bounds__(NT, 2) k_force_jpar_ds(ForceArgs fa, JDS J)
+{
+    const int na = read_na(fa);
+    if (na <= 0 || !use_jpar(na, fa.jpar_max)) return;
+    if (na <= kJparIC1Max) jpar_ds_items<NT, 1, SOFT>(fa, J, na);
+    else jpar_ds_items<NT, kJparIC, SOFT>(fa, J, na);
 }
 
 // ----------------------------------------------------------------------------
@@ -416,6 +486,7 @@ __global__ void k_force_combine(ForceArgs fa, int precision)
     const int reg = precision == NB_FP64 ? (use_jpar(na, fa.jpar_max) ? kRegJpar : kRegIpar)
                                          : regime_of(na, fa.jpar_max, fa.small_max);
     if (reg == kRegJpar) {
+        if (precision != NB_FP64) return;   // the DS j-parallel kernel combines its own slices
         S = plan_jpar(na, fa.n, kJparNT, kJparIC, fa.slots_jpar, fa.part_cap).S;
     } else {
         const int r = precision == NB_FP64 ? IR64 : (reg == kRegSmall ? kIparSmallR : IR);
@@ -463,23 +534,29 @@ int combine_grid(const ForceArgs &fa)
 
 }  // namespace
 
-void launch_force_ds(const ForceArgs &fa, const JDS &j, bool softened, int grid_ipar,
-                     int grid_jpar, int grid_small, cudaStream_t st)
+int launch_force_ds(const ForceArgs &fa, const JDS &j, bool softened, int grid_ipar,
+                    int grid_jpar, int grid_small, cudaStream_t st)
 {
     if (softened) {
         if (grid_ipar > 0)
             k_force_ipar_ds<kIparNT, kIparR, kRegIpar, true><<<grid_ipar, kIparNT, 0, st>>>(fa, j);
         if (grid_small > 0)
             k_force_ipar_ds<kIparNT, kIparSmallR, kRegSmall, true><<<grid_small, kIparNT, 0, st>>>(fa, j);
-        if (grid_jpar > 0) k_force_jpar_ds<kJparNT, kJparIC, true><<<grid_jpar, kJparNT, 0, st>>>(fa, j);
+        if (grid_jpar > 0) k_force_jpar_ds<kJparNT, true><<<grid_jpar, kJparNT, 0, st>>>(fa, j);
     } else {
         if (grid_ipar > 0)
             k_force_ipar_ds<kIparNT, kIparR, kRegIpar, false><<<grid_ipar, kIparNT, 0, st>>>(fa, j);
         if (grid_small > 0)
             k_force_ipar_ds<kIparNT, kIparSmallR, kRegSmall, false><<<grid_small, kIparNT, 0, st>>>(fa, j);
-        if (grid_jpar > 0) k_force_jpar_ds<kJparNT, kJparIC, false><<<grid_jpar, kJparNT, 0, st>>>(fa, j);
+        if (grid_jpar > 0) k_force_jpar_ds<kJparNT, false><<<grid_jpar, kJparNT, 0, st>>>(fa, j);
     }
-    k_force_combine<kIparR, kIparR64><<<combine_grid(fa), 256, 0, st>>>(fa, NB_DS);
+    int launches = (grid_ipar > 0) + (grid_small > 0) + (grid_jpar > 0);
+    // a host-sized j-parallel launch combines its own slices
+    if (fa.na_dev || grid_ipar > 0 || grid_small > 0) {
+        k_force_combine<kIparR, kIparR64><<<combine_grid(fa), 256, 0, st>>>(fa, NB_DS);
+        ++launches;
+    }
+    return launches;
 }
 
 void launch_force_f64(const ForceArgs &fa, const JF64 &j, bool softened, int grid_ipar,
@@ -506,7 +583,7 @@ int occupancy_force(int precision, int regime, int *blocks_per_sm)
                       blocks_per_sm, k_force_ipar_f64<kIparNT, kIparR64, true>, kIparNT, 0);
     else if (regime == kRegJpar)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            blocks_per_sm, k_force_jpar_ds<kJparNT, kJparIC, true>, kJparNT, 0);
+            blocks_per_sm, k_force_jpar_ds<kJparNT, true>, kJparNT, 0);
     else if (regime == kRegSmall)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             blocks_per_sm, k_force_ipar_ds<kIparNT, kIparSmallR, kRegSmall, true>, kIparNT, 0);

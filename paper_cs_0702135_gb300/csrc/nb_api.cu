@@ -40,6 +40,7 @@ struct nb_ctx {
     JF64 jf{};
     double *d_res = nullptr;        // force results: acc [n][3], jerk [n][3], pot [n]
     double *d_part = nullptr;       // slice partials
+    int *d_jcnt = nullptr;          // [n] slice arrival counters of the DS j-parallel kernel
     long long part_cap = 0;
     int *d_act = nullptr;           // block of the device-driven step
     int *d_idx = nullptr;           // indices passed by the host-driven calls
@@ -191,6 +192,7 @@ ForceArgs force_args(nb_ctx *c, const int *act, int na_host, const int *na_dev, 
     fa.slots_small = c->slots_small;
     fa.part_cap = c->part_cap;
     fa.part = c->d_part;
+    fa.jcnt = c->d_jcnt;
     fa.out = out;
     fa.eps2 = c->eps * c->eps;
     fa.err = &c->d_ctrl->err;
@@ -220,7 +222,8 @@ void enqueue_force(nb_ctx *c, const int *act, int na_host, const int *na_dev, Fo
                             : regime_of(na_host, c->jpar_max, c->small_max);
         gi = gj = gs = 0;
         if (reg == kRegJpar) {
-            const Plan p = plan_jpar(na_host, c->n, kJparNT, kJparIC, c->slots_jpar, c->part_cap);
+            const int ic = !f64 && na_host <= kJparIC1Max ? 1 : kJparIC;
+            const Plan p = plan_jpar(na_host, c->n, kJparNT, ic, c->slots_jpar, c->part_cap);
             gj = p.items < c->slots_jpar ? p.items : c->slots_jpar;
         } else if (reg == kRegSmall) {
             const Plan p = plan_ipar(na_host, c->n, kIparNT * kIparSmallR, kIparNT, c->slots_small,
@@ -254,8 +257,7 @@ void enqueue_force(nb_ctx *c, const int *act, int na_host, const int *na_dev, Fo
         launch_force_f64(fa, c->jf, c->eps > 0.0, gi, gj, c->st);
         c->launches += (gi > 0) + (gj > 0) + 1;
     } else {
-        launch_force_ds(fa, c->jds, c->eps > 0.0, gi, gj, gs, c->st);
-        c->launches += (gi > 0) + (gj > 0) + (gs > 0) + 1;
+        c->launches += launch_force_ds(fa, c->jds, c->eps > 0.0, gi, gj, gs, c->st);
     }
     if (timed) {
         if (ev[0] && ev[1]) {
@@ -316,7 +318,7 @@ void release(nb_ctx *c)
                     c->jds.pos_lo, c->jds.vel, c->jf.pos, c->jf.vel, c->d_res, c->d_part,
                     c->d_act, c->d_idx, c->d_all, c->d_bitmap, c->d_ctrl, c->d_blockmin,
                     c->d_blockcnt, c->d_epart, c->d_stage, c->d_ck, c->d_seg, c->d_fin, c->d_tfin,
-                    c->d_cot, c->vrec.ph, c->vrec.pl, c->vrec.v, c->vrec.ab, c->vrec.kb,
+                    c->d_jcnt, c->d_cot, c->vrec.ph, c->vrec.pl, c->vrec.v, c->vrec.ab, c->vrec.kb,
                     c->vrec64.x, c->vrec64.v, c->vrec64.ab, c->vrec64.kb, c->d_bounds, c->d_sort,
                     c->d_run_part, c->d_run_mins, c->d_run_counts, c->d_run_maxs, c->d_run_bar};
     for (void *p : ptrs)
@@ -588,7 +590,7 @@ static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, con
         (rc = dalloc(c, &c->d_bitmap, (N + 31) / 32)) || (rc = dalloc(c, &c->d_ctrl, 1)) ||
         (rc = dalloc(c, &c->d_blockmin, c->nsched)) || (rc = dalloc(c, &c->d_blockcnt, c->nsched)) ||
         (rc = dalloc(c, &c->d_epart, 2LL * energy_blocks(c->n))) ||
-        (rc = dalloc(c, &c->d_stage, 7 * N)))
+        (rc = dalloc(c, &c->d_stage, 7 * N)) || (rc = dalloc(c, &c->d_jcnt, N)))
         return rc;
     if (o.summation == NB_SUM_FIXED) {
         if ((rc = dalloc(c, &c->d_bounds, 2))) return rc;
@@ -626,6 +628,7 @@ static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, con
     CK(cudaMemsetAsync(c->d_a, 0, sizeof(double) * 3 * N, c->st));
     CK(cudaMemsetAsync(c->d_k, 0, sizeof(double) * 3 * N, c->st));
     CK(cudaMemsetAsync(c->d_t, 0, sizeof(long long) * N, c->st));
+    CK(cudaMemsetAsync(c->d_jcnt, 0, sizeof(int) * N, c->st));
     CK(cudaMemcpyAsync(c->d_m, m, sizeof(double) * N, cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->d_stage, x, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->d_stage + 3 * N, v, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));

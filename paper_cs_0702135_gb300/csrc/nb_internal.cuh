@@ -72,6 +72,7 @@ constexpr int kIparUnroll = NB_IPAR_UNROLL;  // j unrolling of the DS inner loop
 constexpr int kIparR64 = 1;    // i per thread, FP64 i-parallel kernel
 constexpr int kJparNT = 256;   // threads per CTA, j-parallel kernels
 constexpr int kJparIC = 4;     // i per pass, j-parallel kernels
+constexpr int kJparIC1Max = 2;  // DS j-parallel kernel: one i per pass up to this block size
 constexpr int kJparMaxActive = 32;  // automatic mode: j-parallel up to this block size
 constexpr int kIparSmallR = 1;      // i per thread of the small-block DS i-parallel kernel
 constexpr int kSmallMaxActive = 192;  // automatic mode: small-block kernel up to this size
@@ -146,16 +147,19 @@ __host__ __device__ inline Plan plan_ipar(int na, int n, int iblk, int tile, int
 }
 
 // j-parallel: CTAs own ic active particles and one j slice; each thread takes
-// every nt-th j of the slice, at least eight per thread.
+// every nt-th j of the slice, at least eight per thread.  The slice count aims
+// at two work items per resident CTA, else (slices too short) at one, so that
+// the last wave is not a small remainder.
 __host__ __device__ inline Plan plan_jpar(int na, int n, int nt, int ic, int slots,
                                           long long part_cap)
 {
     Plan p;
     p.n_iblk = cdiv(na, ic);
     int S = cdiv(2LL * slots, p.n_iblk);
-    int smax = cdiv(n, 8LL * nt);
+    const int smax = cdiv(n, 8LL * nt);
+    if (S > smax) S = cdiv((long long)slots, p.n_iblk);
     if (S > smax) S = smax;
-    long long pmax = part_cap / ((long long)kComp * (na > 0 ? na : 1));
+    long long pmax = part_cap / ((long long)kComp * ic * p.n_iblk);
     if (S > pmax) S = (int)pmax;
     if (S < 1) S = 1;
     p.jslice = cdiv(cdiv(n, S), nt) * nt;
@@ -189,7 +193,9 @@ struct ForceArgs {
     int split;                // forced slice count for i-parallel, 0 = auto
     int slots_ipar, slots_jpar, slots_small;
     long long part_cap;       // capacity of part in doubles
-    double *part;             // slice partials: part[(s * 7 + c) * na + a]
+    double *part;             // slice partials: part[(s * 7 + c) * na + a]; the DS
+                              // j-parallel kernel: part[(chunk * 7 ic + e) * S + s]
+    int *jcnt;                // per-chunk slice arrival counters (zero between launches)
     ForceOut out;
     double eps2;
     int *err;                 // device error word
@@ -271,8 +277,9 @@ struct VjpArgs {
 // Launchers (defined in the .cu files).
 
 // k_force.cu
-void launch_force_ds(const ForceArgs &fa, const JDS &j, bool softened, int grid_ipar, int grid_jpar,
-                     int grid_small, cudaStream_t st);
+// Returns the number of kernels launched.
+int launch_force_ds(const ForceArgs &fa, const JDS &j, bool softened, int grid_ipar, int grid_jpar,
+                    int grid_small, cudaStream_t st);
 void launch_force_f64(const ForceArgs &fa, const JF64 &j, bool softened, int grid_ipar,
                       int grid_jpar, cudaStream_t st);
 int occupancy_force(int precision, int regime, int *blocks_per_sm);

@@ -167,7 +167,7 @@ def test_host_argument_errors(nb):
         nb.nb_free(ctx)
 
 
-@pytest.mark.parametrize("na", [1, 256, 4096])
+@pytest.mark.parametrize("na", [1, 2, 3, 32, 256, 4096])
 def test_full_size_sampled(nb, na):
     # N = 2^20, eps = 1/1024: the benchmark's sweep configuration; 64 of the
     # active particles are checked one by one against the oracle.
@@ -183,3 +183,25 @@ def test_full_size_sampled(nb, na):
     ref = oracle.force(m, x, v, eps, idx[pick], nthreads=8)
     mags = pair_magnitudes(m, x, v, eps, idx[pick], chunk=4)
     assert_force_close(tuple(g[pick] for g in got), ref, mags, TOL_DS, "N=2^20 na=%d" % na)
+
+
+def test_jpar_slice_counters_reset_between_calls(nb):
+    # The DS j-parallel kernel sums its slices in the CTA that finishes a
+    # chunk last, found by per-chunk arrival counters that this CTA resets.
+    # Alternating block sizes (one i per pass, four i per pass, different
+    # chunk and slice counts) must give bitwise the same result every time.
+    n = 300000
+    m, x, v = plummer(n, 21)
+    ctx = nb.nb_init(m, x, v, EPS, nb.nb_default_opts(flags=nb.NB_INIT_NO_FORCE))
+    try:
+        blocks = [sample_active(n, na, 40 + na) for na in (5, 1, 2, 31, 3)]
+        first = [nb.nb_force(ctx, idx) for idx in blocks]
+        again = [nb.nb_force(ctx, idx) for idx in reversed(blocks)][::-1]
+    finally:
+        nb.nb_free(ctx)
+    for f, g in zip(first, again):
+        for p, q in zip(f, g):
+            assert np.array_equal(p, q)
+    ref = oracle.force(m, x, v, EPS, blocks[0], nthreads=8)
+    mags = pair_magnitudes(m, x, v, EPS, blocks[0])
+    assert_force_close(first[0], ref, mags, TOL_DS, "na=5 N=300000")

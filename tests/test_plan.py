@@ -80,15 +80,23 @@ def test_ipar_plans(planner):
 
 def test_jpar_plans(planner):
     cases = []
-    for na, n, slots in itertools.product([1, 2, 4, 5, 16, 32, 33], [2, 300, 65536, 1 << 20], [152, 304]):
+    for na, n, slots, ic in itertools.product([1, 2, 4, 5, 16, 32, 33], [2, 300, 65536, 1 << 20],
+                                              [152, 304], [1, 4]):
         if na > n:
             continue
         cap = 7 * 8 * slots * 4
-        cases.append(("j", na, n, 4, 256, slots, 0, cap))
+        cases.append(("j", na, n, ic, 256, slots, 0, cap))
     for c, (nch, S, js, items) in zip(cases, _run(planner, cases)):
         _, na, n, ic, nt, slots, _, cap = c
         assert nch == -(-na // ic)
         assert (S - 1) * js < n <= S * js and js % nt == 0
-        assert S * 7 * na <= cap
+        # partials are stored per chunk slot: ic values of 7 components per slice
+        assert S * 7 * nch * ic <= cap
         assert items == nch * S
         assert S == 1 or js >= 8 * nt
+        # a lone particle on 2^20 bodies fills two waves, or one when the
+        # slices of two would be too short, never one and a fraction
+        # (rounding the slices to whole tiles loses a few percent)
+        if na == 1 and n == 1 << 20:
+            waves = 2 if 2 * slots * 8 * nt <= n else 1
+            assert 0.9 * waves * slots <= items <= waves * slots, c
