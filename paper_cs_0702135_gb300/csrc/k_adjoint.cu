@@ -105,7 +105,7 @@ __device__ __forceinline__ void vjp_pair_ds(const VjpRec &P, const VjpRec &Kp, f
 template <bool SOFT>
 __global__ void __launch_bounds__(kVNT) k_force_vjp_ds(VjpArgs va)
 {
-    const Plan P = plan_ipar(va.n, va.n, kVNT, kVNT, va.slots, 0, va.part_cap);
+    const Plan P = va.plan;
     __shared__ float4 s_ph[kVNT], s_pl[kVNT], s_v[kVNT], s_ab[kVNT], s_kb[kVNT];
     const float eps2 = (float)va.eps2;
     const int tid = threadIdx.x;
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kVNT) k_force_vjp_ds(VjpArgs va)
 template <bool SOFT>
 __global__ void __launch_bounds__(kVNT) k_force_vjp_f64(VjpArgs va)
 {
-    const Plan P = plan_ipar(va.n, va.n, kVNT, kVNT, va.slots, 0, va.part_cap);
+    const Plan P = va.plan;
     __shared__ double4_32a s_x[kVNT], s_v[kVNT], s_a[kVNT], s_k[kVNT];
     const double eps2 = va.eps2;
     const int tid = threadIdx.x;
@@ -382,9 +382,11 @@ int vjp_slots(int precision, int sms)
 
 int vjp_tile() { return kVNT; }
 
-int launch_force_vjp(const VjpArgs &va, int precision, bool softened, cudaStream_t st)
+int launch_force_vjp(const VjpArgs &va_in, int precision, bool softened, cudaStream_t st)
 {
-    const Plan P = plan_ipar(va.n, va.n, kVNT, kVNT, va.slots, 0, va.part_cap);
+    VjpArgs va = va_in;
+    va.plan = plan_ipar(va.n, va.n, kVNT, kVNT, va.slots, 0, va.part_cap);   // once, on the host
+    const Plan P = va.plan;
     const int g = P.items < va.slots ? P.items : va.slots;
     if (precision == NB_FP64) {
         if (softened) k_force_vjp_f64<true><<<g, kVNT, 0, st>>>(va);

@@ -74,10 +74,10 @@ __device__ __forceinline__ void pair_f64(const double4_32a &p, const double4_32a
 template <int NT, int R, int REG, bool SOFT>
 __global__ void __launch_bounds__(NT) k_force_ipar_ds(ForceArgs fa, JDS J)
 {
-    const int na = read_na(fa);
-    if (na <= 0 || regime_of(na, fa.jpar_max, fa.small_max) != REG) return;
-    const int slots = REG == kRegSmall ? fa.slots_small : fa.slots_ipar;
-    const Plan P = plan_ipar(na, fa.n, NT * R, NT, slots, fa.split, fa.part_cap);
+    const ForcePlan F = load_plan(fa);
+    const int na = F.na;
+    if (na <= 0 || F.regime != REG) return;
+    const Plan P = F.p;
     __shared__ float4 s_p[NT], s_l[NT], s_v[NT];
     const float eps2 = (float)fa.eps2;
     const int tid = threadIdx.x;
@@ -222,9 +222,8 @@ __device__ __forceinline__ void warp_reduce_scatter(float (&h)[P], float (&lo)[P
 }
 
 template <int NT, int IC, bool SOFT>
-__device__ __forceinline__ void jpar_ds_items(const ForceArgs &fa, const JDS &J, int na)
+__device__ __forceinline__ void jpar_ds_items(const ForceArgs &fa, const JDS &J, int na, const Plan &P)
 {
-    const Plan P = plan_jpar(na, fa.n, NT, IC, fa.slots_jpar, fa.part_cap);
     constexpr int NW = NT / 32;
     constexpr int NV = IC * kComp;
     __shared__ float s_h[NW][NV], s_l[NW][NV];
@@ -327,10 +326,10 @@ __device__ __forceinline__ void jpar_ds_items(const ForceArgs &fa, const JDS &J,
 template <int NT, bool SOFT>
 __global__ void __launch_bounds__(NT, 2) k_force_jpar_ds(ForceArgs fa, JDS J)
 {
-    const int na = read_na(fa);
-    if (na <= 0 || !use_jpar(na, fa.jpar_max)) return;
-    if (na <= kJparIC1Max) jpar_ds_items<NT, 1, SOFT>(fa, J, na);
-    else jpar_ds_items<NT, kJparIC, SOFT>(fa, J, na);
+    const ForcePlan F = load_plan(fa);
+    if (F.na <= 0 || F.regime != kRegJpar) return;
+    if (F.ic == 1) jpar_ds_items<NT, 1, SOFT>(fa, J, F.na, F.p);
+    else jpar_ds_items<NT, kJparIC, SOFT>(fa, J, F.na, F.p);
 }
 
 // ----------------------------------------------------------------------------
@@ -339,9 +338,10 @@ __global__ void __launch_bounds__(NT, 2) k_force_jpar_ds(ForceArgs fa, JDS J)
 template <int NT, int R, bool SOFT>
 __global__ void __launch_bounds__(NT) k_force_ipar_f64(ForceArgs fa, JF64 J)
 {
-    const int na = read_na(fa);
-    if (na <= 0 || use_jpar(na, fa.jpar_max)) return;
-    const Plan P = plan_ipar(na, fa.n, NT * R, NT, fa.slots_ipar, fa.split, fa.part_cap);
+    const ForcePlan F = load_plan(fa);
+    const int na = F.na;
+    if (na <= 0 || F.regime != kRegIpar) return;
+    const Plan P = F.p;
     __shared__ double4_32a s_p[NT], s_v[NT];
     const double eps2 = fa.eps2;
     const int tid = threadIdx.x;
@@ -412,9 +412,10 @@ __global__ void __launch_bounds__(NT) k_force_ipar_f64(ForceArgs fa, JF64 J)
 template <int NT, int IC, bool SOFT>
 __global__ void __launch_bounds__(NT) k_force_jpar_f64(ForceArgs fa, JF64 J)
 {
-    const int na = read_na(fa);
-    if (na <= 0 || !use_jpar(na, fa.jpar_max)) return;
-    const Plan P = plan_jpar(na, fa.n, NT, IC, fa.slots_jpar, fa.part_cap);
+    const ForcePlan F = load_plan(fa);
+    const int na = F.na;
+    if (na <= 0 || F.regime != kRegJpar) return;
+    const Plan P = F.p;
     constexpr int NW = NT / 32;
     constexpr int NV = IC * kComp;
     __shared__ double s_r[NW][NV];
@@ -477,54 +478,41 @@ __global__ void __launch_bounds__(NT) k_force_jpar_f64(ForceArgs fa, JF64 J)
 // ----------------------------------------------------------------------------
 // Slice combine: out = sum over slices in a fixed order (FP64).
 
-template <int IR, int IR64>
 __global__ void k_force_combine(ForceArgs fa, int precision)
 {
-    const int na = read_na(fa);
+    const ForcePlan F = load_plan(fa);
+    const int na = F.na;
     if (na <= 0) return;
-    int S;
-    const int reg = precision == NB_FP64 ? (use_jpar(na, fa.jpar_max) ? kRegJpar : kRegIpar)
-                                         : regime_of(na, fa.jpar_max, fa.small_max);
-    if (reg == kRegJpar) {
-        if (precision != NB_FP64) return;   // the DS j-parallel kernel combines its own slices
-        S = plan_jpar(na, fa.n, kJparNT, kJparIC, fa.slots_jpar, fa.part_cap).S;
-    } else {
-        const int r = precision == NB_FP64 ? IR64 : (reg == kRegSmall ? kIparSmallR : IR);
-        const int slots = reg == kRegSmall ? fa.slots_small : fa.slots_ipar;
-        const Plan p = plan_ipar(na, fa.n, kIparNT * r, kIparNT, slots, fa.split, fa.part_cap);
-        if (p.S == 1) return;
-        S = p.S;
-    }
+    // the DS j-parallel kernel combines its own slices; the i-parallel kernels
+    // store the result directly when there is one slice
+    if (F.regime == kRegJpar ? precision != NB_FP64 : F.p.S == 1) return;
+    const int S = F.p.S;
     const long long total = (long long)na * kComp;
-    if (S <= 8) {
-        // one thread per output, slices in order
-        for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-             e += (long long)gridDim.x * blockDim.x) {
-            const int c = (int)(e / na), a = (int)(e % na);
-            double s = 0.0;
-            for (int q = 0; q < S; ++q) s += fa.part[((long long)q * kComp + c) * na + a];
-            write_combined(fa.out, c, a, s);
-        }
-        return;
-    }
-    // one warp per output: lane l sums slices l, l + 32, ... in order, then a
-    // fixed xor tree; the order depends only on S, so results are reproducible
-    const int lane = threadIdx.x & 31;
+    // T lanes per output (a power of two, chosen from na and S only, so the
+    // order of the additions is fixed): lane t of a group adds slices t,
+    // t + T, ... in order, then a fixed xor tree over the group.  The groups
+    // of a warp take consecutive particles, so each load instruction reads
+    // whole 32-byte sectors of T slice rows.
+    const int T = F.lanes;
+    const int gpw = 32 / T;
+    const int lane = threadIdx.x & 31, sub = lane & (T - 1);
     const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long e = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; e < total; e += warps) {
-        const int c = (int)(e / na), a = (int)(e % na);
+    for (long long wb = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; wb * gpw < total;
+         wb += warps) {
+        const long long o = wb * gpw + lane / T;
+        const int c = (int)(o / na), a = (int)(o % na);
         double s = 0.0;
-        for (int q = lane; q < S; q += 32) s += fa.part[((long long)q * kComp + c) * na + a];
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) write_combined(fa.out, c, a, s);
+        if (o < total)
+            for (int q = sub; q < S; q += T) s += fa.part[((long long)q * kComp + c) * na + a];
+        for (int off = T / 2; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (sub == 0 && o < total) write_combined(fa.out, c, a, s);
     }
 }
 
 int combine_grid(const ForceArgs &fa)
 {
     if (!fa.na_dev) {
-        // enough threads for a warp per output when there are many slices
+        // one thread per lane of every output group (up to 32 per output)
         long long total = (long long)fa.na_host * kComp * 32;
         long long g = (total + 255) / 256;
         return (int)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
@@ -553,7 +541,7 @@ int launch_force_ds(const ForceArgs &fa, const JDS &j, bool softened, int grid_i
     int launches = (grid_ipar > 0) + (grid_small > 0) + (grid_jpar > 0);
     // a host-sized j-parallel launch combines its own slices
     if (fa.na_dev || grid_ipar > 0 || grid_small > 0) {
-        k_force_combine<kIparR, kIparR64><<<combine_grid(fa), 256, 0, st>>>(fa, NB_DS);
+        k_force_combine<<<combine_grid(fa), 256, 0, st>>>(fa, NB_DS);
         ++launches;
     }
     return launches;
@@ -569,7 +557,7 @@ void launch_force_f64(const ForceArgs &fa, const JF64 &j, bool softened, int gri
         if (grid_ipar > 0) k_force_ipar_f64<kIparNT, kIparR64, false><<<grid_ipar, kIparNT, 0, st>>>(fa, j);
         if (grid_jpar > 0) k_force_jpar_f64<kJparNT, kJparIC, false><<<grid_jpar, kJparNT, 0, st>>>(fa, j);
     }
-    k_force_combine<kIparR, kIparR64><<<combine_grid(fa), 256, 0, st>>>(fa, NB_FP64);
+    k_force_combine<<<combine_grid(fa), 256, 0, st>>>(fa, NB_FP64);
 }
 
 int occupancy_force(int precision, int regime, int *blocks_per_sm)

@@ -167,7 +167,8 @@ __global__ void k_sched_count(State s, Ctrl *ctrl, const long long *blockmin, in
     if (threadIdx.x == 0) blockcnt[blockIdx.x] = cnt;
 }
 
-__global__ void k_sched_scatter(State s, Ctrl *ctrl, const int *blockcnt, int *act, int nblocks)
+__global__ void k_sched_scatter(State s, Ctrl *ctrl, const int *blockcnt, int *act, int nblocks,
+                                ForceArgs fa, ForcePlan *plan_out)
 {
     __shared__ int si[kSchedNT / 32];
     __shared__ int wtot[kSchedNT / 32];
@@ -201,6 +202,7 @@ __global__ void k_sched_scatter(State s, Ctrl *ctrl, const int *blockcnt, int *a
     if (blockIdx.x == nblocks - 1 && threadIdx.x == 0) {
         const int total = pre + running;
         ctrl->n_active = total;
+        *plan_out = make_force_plan(fa, total);   // the force launches read it
         if (total > 0) {
             ctrl->t_now = tn;
             ctrl->steps += 1;
@@ -336,11 +338,11 @@ void launch_initial_steps(const State &s, const double *acc, const double *jerk,
 int schedule_blocks(int n) { return cdiv(n, kSchedChunk); }
 
 void launch_schedule(const State &s, Ctrl *ctrl, long long *blockmin, int *blockcnt, int *act,
-                     int nblocks, cudaStream_t st)
+                     int nblocks, const ForceArgs &fa, ForcePlan *plan_out, cudaStream_t st)
 {
     k_sched_min<<<nblocks, kSchedNT, 0, st>>>(s, blockmin);
     k_sched_count<<<nblocks, kSchedNT, 0, st>>>(s, ctrl, blockmin, blockcnt, nblocks);
-    k_sched_scatter<<<nblocks, kSchedNT, 0, st>>>(s, ctrl, blockcnt, act, nblocks);
+    k_sched_scatter<<<nblocks, kSchedNT, 0, st>>>(s, ctrl, blockcnt, act, nblocks, fa, plan_out);
 }
 
 int energy_blocks(int n)

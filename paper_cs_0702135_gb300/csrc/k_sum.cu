@@ -59,11 +59,6 @@ __global__ void k_fixed_bounds(JDS J, int n, unsigned *bounds)
     }
 }
 
-__device__ __forceinline__ Plan plan_fixed(int na, const ForceArgs &fa, const SumArgs &sa)
-{
-    return plan_ipar(na, fa.n, kFixNT * kFixR, kFixNT, sa.slots, fa.split, fa.part_cap / 2);
-}
-
 // One pair into the tile's split sums; the pair j = i adds zeros, so every
 // tile adds exactly NT terms.
 template <bool GUARD>
@@ -84,7 +79,8 @@ __device__ __forceinline__ void pair_fixed(const float4 &p, const float4 &l, con
 template <int NT, int R>
 __global__ void __launch_bounds__(NT) k_force_fixed(ForceArgs fa, JDS J, SumArgs sa)
 {
-    const int na = read_na(fa);
+    const ForcePlan F = load_plan(fa);
+    const int na = F.na;
     if (na <= 0) return;
     const float eps2 = (float)fa.eps2;
     Scale S;
@@ -92,7 +88,7 @@ __global__ void __launch_bounds__(NT) k_force_fixed(ForceArgs fa, JDS J, SumArgs
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(fa.err, 0, kErrFixedScale);
         return;
     }
-    const Plan P = plan_fixed(na, fa, sa);
+    const Plan P = F.p;
     long long *part = reinterpret_cast<long long *>(fa.part);
     __shared__ float4 s_p[NT], s_l[NT], s_v[NT];
     const int tid = threadIdx.x;
@@ -181,9 +177,10 @@ __global__ void __launch_bounds__(NT) k_force_fixed(ForceArgs fa, JDS J, SumArgs
 // Sum of the slices' 128-bit totals (exact, any order) and conversion.
 __global__ void k_fixed_combine(ForceArgs fa, SumArgs sa)
 {
-    const int na = read_na(fa);
+    const ForcePlan F = load_plan(fa);
+    const int na = F.na;
     if (na <= 0) return;
-    const Plan P = plan_fixed(na, fa, sa);
+    const Plan P = F.p;
     if (P.S == 1) return;
     Scale S;
     if (!fixed_scale(sa.bounds, (float)fa.eps2, S)) return;
@@ -415,7 +412,7 @@ int grid_summed(const ForceArgs &fa, const SumArgs &sa)
     if (na <= 0) return 0;
     long long items;
     if (sa.mode == NB_SUM_FIXED)
-        items = plan_ipar(na, fa.n, kFixNT * kFixR, kFixNT, sa.slots, fa.split, fa.part_cap / 2).items;
+        items = fa.plan.p.items;
     else if (sa.mode == NB_SUM_FP32)
         items = cdiv(na, kSeqNT);
     else

@@ -40,6 +40,7 @@ struct nb_ctx {
     JF64 jf{};
     double *d_res = nullptr;        // force results: acc [n][3], jerk [n][3], pot [n]
     double *d_part = nullptr;       // slice partials
+    ForcePlan *d_plan = nullptr;    // plan of the device-sized force (written by the scheduler)
     int *d_jcnt = nullptr;          // [n] slice arrival counters of the DS j-parallel kernel
     long long part_cap = 0;
     int *d_act = nullptr;           // block of the device-driven step
@@ -196,6 +197,11 @@ ForceArgs force_args(nb_ctx *c, const int *act, int na_host, const int *na_dev, 
     fa.out = out;
     fa.eps2 = c->eps * c->eps;
     fa.err = &c->d_ctrl->err;
+    fa.precision = c->o.precision;
+    fa.summation = c->o.summation;
+    fa.slots_sum = c->sum.slots;
+    if (na_dev) fa.plan_dev = c->d_plan;   // written by the scheduler with *na_dev
+    else fa.plan = make_force_plan(fa, na_host);
     return fa;
 }
 
@@ -218,22 +224,11 @@ void enqueue_force(nb_ctx *c, const int *act, int na_host, const int *na_dev, Fo
     int gi = c->slots_ipar, gj = c->slots_jpar, gs = f64 ? 0 : c->slots_small;
     if (!na_dev) {
         if (na_host <= 0) return;
-        const int reg = f64 ? (use_jpar(na_host, c->jpar_max) ? kRegJpar : kRegIpar)
-                            : regime_of(na_host, c->jpar_max, c->small_max);
+        const Plan &p = fa.plan.p;
         gi = gj = gs = 0;
-        if (reg == kRegJpar) {
-            const int ic = !f64 && na_host <= kJparIC1Max ? 1 : kJparIC;
-            const Plan p = plan_jpar(na_host, c->n, kJparNT, ic, c->slots_jpar, c->part_cap);
-            gj = p.items < c->slots_jpar ? p.items : c->slots_jpar;
-        } else if (reg == kRegSmall) {
-            const Plan p = plan_ipar(na_host, c->n, kIparNT * kIparSmallR, kIparNT, c->slots_small,
-                                     c->o.split_j, c->part_cap);
-            gs = p.items < c->slots_small ? p.items : c->slots_small;
-        } else {
-            const Plan p = plan_ipar(na_host, c->n, kIparNT * (f64 ? kIparR64 : kIparR), kIparNT,
-                                     c->slots_ipar, c->o.split_j, c->part_cap);
-            gi = p.items < c->slots_ipar ? p.items : c->slots_ipar;
-        }
+        if (fa.plan.regime == kRegJpar) gj = p.items < c->slots_jpar ? p.items : c->slots_jpar;
+        else if (fa.plan.regime == kRegSmall) gs = p.items < c->slots_small ? p.items : c->slots_small;
+        else gi = p.items < c->slots_ipar ? p.items : c->slots_ipar;
     }
     const bool summed = c->o.summation != NB_SUM_COMPENSATED;
     const int gsum = summed ? grid_summed(fa, c->sum) : 0;
@@ -274,7 +269,8 @@ void enqueue_force(nb_ctx *c, const int *act, int na_host, const int *na_dev, Fo
 // The device-driven block step: schedule, predict all, force, correct.
 void enqueue_step(nb_ctx *c)
 {
-    launch_schedule(c->S, c->d_ctrl, c->d_blockmin, c->d_blockcnt, c->d_act, c->nsched, c->st);
+    launch_schedule(c->S, c->d_ctrl, c->d_blockmin, c->d_blockcnt, c->d_act, c->nsched,
+                    force_args(c, c->d_act, 0, &c->d_ctrl->n_active, res_out(c)), c->d_plan, c->st);
     launch_predict(c->S, 0, &c->d_ctrl->t_next, &c->d_ctrl->n_active, c->o.precision, c->jds,
                    c->jf, c->st);
     enqueue_force(c, c->d_act, 0, &c->d_ctrl->n_active, res_out(c));
@@ -318,7 +314,7 @@ void release(nb_ctx *c)
                     c->jds.pos_lo, c->jds.vel, c->jf.pos, c->jf.vel, c->d_res, c->d_part,
                     c->d_act, c->d_idx, c->d_all, c->d_bitmap, c->d_ctrl, c->d_blockmin,
                     c->d_blockcnt, c->d_epart, c->d_stage, c->d_ck, c->d_seg, c->d_fin, c->d_tfin,
-                    c->d_jcnt, c->d_cot, c->vrec.ph, c->vrec.pl, c->vrec.v, c->vrec.ab, c->vrec.kb,
+                    c->d_jcnt, c->d_plan, c->d_cot, c->vrec.ph, c->vrec.pl, c->vrec.v, c->vrec.ab, c->vrec.kb,
                     c->vrec64.x, c->vrec64.v, c->vrec64.ab, c->vrec64.kb, c->d_bounds, c->d_sort,
                     c->d_run_part, c->d_run_mins, c->d_run_counts, c->d_run_maxs, c->d_run_bar};
     for (void *p : ptrs)
@@ -558,7 +554,7 @@ static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, con
     c->slots_small = c->sms * (bs > 0 ? bs : 1);
     c->jpar_max = o.force_mode == NB_FORCE_IPAR ? 0
                   : o.force_mode == NB_FORCE_JPAR ? INT_MAX
-                                                  : kJparMaxActive;
+                                                  : (f64 ? kJparMaxActive64 : kJparMaxActive);
     c->small_max = f64 || o.force_mode == NB_FORCE_JPAR ? 0 : kSmallMaxActive;
     if (o.summation != NB_SUM_COMPENSATED) {
         int bsum = 0;
@@ -590,7 +586,8 @@ static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, con
         (rc = dalloc(c, &c->d_bitmap, (N + 31) / 32)) || (rc = dalloc(c, &c->d_ctrl, 1)) ||
         (rc = dalloc(c, &c->d_blockmin, c->nsched)) || (rc = dalloc(c, &c->d_blockcnt, c->nsched)) ||
         (rc = dalloc(c, &c->d_epart, 2LL * energy_blocks(c->n))) ||
-        (rc = dalloc(c, &c->d_stage, 7 * N)) || (rc = dalloc(c, &c->d_jcnt, N)))
+        (rc = dalloc(c, &c->d_stage, 7 * N)) || (rc = dalloc(c, &c->d_jcnt, N)) ||
+        (rc = dalloc(c, &c->d_plan, 1)))
         return rc;
     if (o.summation == NB_SUM_FIXED) {
         if ((rc = dalloc(c, &c->d_bounds, 2))) return rc;

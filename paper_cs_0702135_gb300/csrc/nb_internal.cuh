@@ -73,7 +73,8 @@ constexpr int kIparR64 = 1;    // i per thread, FP64 i-parallel kernel
 constexpr int kJparNT = 256;   // threads per CTA, j-parallel kernels
 constexpr int kJparIC = 4;     // i per pass, j-parallel kernels
 constexpr int kJparIC1Max = 2;  // DS j-parallel kernel: one i per pass up to this block size
-constexpr int kJparMaxActive = 32;  // automatic mode: j-parallel up to this block size
+constexpr int kJparMaxActive = 64;     // automatic mode, DS: j-parallel up to this block size
+constexpr int kJparMaxActive64 = 32;   // automatic mode, FP64
 constexpr int kIparSmallR = 1;      // i per thread of the small-block DS i-parallel kernel
 constexpr int kSmallMaxActive = 192;  // automatic mode: small-block kernel up to this size
 constexpr int kComp = 7;       // acc xyz, jerk xyz, pot
@@ -88,36 +89,38 @@ struct Plan {
 __host__ __device__ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // i-parallel: CTAs own iblk consecutive active particles and one j slice.
-// Slices are added until there are about two work items per resident CTA,
-// keeping at least two tiles per slice and the partial buffer within
-// part_cap doubles.
-// i-parallel: CTAs own iblk consecutive active particles and one j slice.
 // The slice count S starts at s0 = 1, or, with fewer than two i-blocks per
 // resident CTA, at the count that makes two; then among a few candidates
 // (s0 .. s0 + 7 and the counts that fill 1 .. 8 waves of the slots resident
 // CTAs exactly) the smallest whose last wave is at least 95% full is taken,
 // else the one with the fullest last wave.  Slices keep at least two tiles and
-// the partials fit in part_cap doubles.  Integer arithmetic only: this runs at
-// the start of every CTA.
-__host__ __device__ inline bool better_fill(long long items_a, int slots, long long items_b)
+// the partials fit in part_cap doubles.  Integer arithmetic only, computed
+// once per force launch (host or scheduler, see ForcePlan).
+// Every quotient in the slice search has operands below 2^31 (item counts are
+// at most 8 slots + 8 i-blocks), so it uses 32-bit unsigned divisions, which
+// cost a fraction of the 64-bit ones.
+__host__ __device__ inline unsigned udiv(unsigned a, unsigned b) { return a / b; }
+__host__ __device__ inline unsigned ucdiv(unsigned a, unsigned b) { return (a + b - 1) / b; }
+
+__host__ __device__ inline bool better_fill(unsigned items_a, unsigned slots, unsigned items_b)
 {
     // fill(x) = x / (ceil(x / slots) * slots); compare fill(a) > fill(b)
-    const long long wa = (items_a + slots - 1) / slots, wb = (items_b + slots - 1) / slots;
+    const unsigned long long wa = ucdiv(items_a, slots), wb = ucdiv(items_b, slots);
     return items_a * wb > items_b * wa;
 }
 
-__host__ __device__ inline bool fill_ok(long long items, int slots)
+__host__ __device__ inline bool fill_ok(unsigned items, unsigned slots)
 {
-    const long long w = (items + slots - 1) / slots;
-    return 20 * items >= 19 * w * slots;
+    const unsigned long long w = ucdiv(items, slots);
+    return 20ULL * items >= 19ULL * w * slots;
 }
 
 __host__ __device__ inline Plan plan_ipar(int na, int n, int iblk, int tile, int slots,
                                           int split, long long part_cap)
 {
     Plan p;
-    p.n_iblk = cdiv(na, iblk);
-    const int smax_tiles = cdiv(n, 2LL * tile);
+    p.n_iblk = (int)ucdiv((unsigned)na, (unsigned)iblk);
+    const int smax_tiles = (int)ucdiv((unsigned)n, 2u * (unsigned)tile);
     const long long pmax = part_cap / ((long long)kComp * (na > 0 ? na : 1));
     int smax = smax_tiles < pmax ? smax_tiles : (int)pmax;
     if (smax < 1) smax = 1;
@@ -125,18 +128,20 @@ __host__ __device__ inline Plan plan_ipar(int na, int n, int iblk, int tile, int
     if (split > 0) {
         S = split < smax ? split : smax;
     } else {
-        int s0 = p.n_iblk >= 2 * slots ? 1 : cdiv(2LL * slots, p.n_iblk);
+        const unsigned nib = (unsigned)p.n_iblk, us = (unsigned)slots;
+        int s0 = nib >= 2 * us ? 1 : (int)ucdiv(2 * us, nib);
         if (s0 > smax) s0 = smax;
-        int best = s0, first_ok = fill_ok((long long)p.n_iblk * s0, slots) ? s0 : 0;
+        int best = s0, first_ok = fill_ok(nib * (unsigned)s0, us) ? s0 : 0;
+#pragma unroll
         for (int q = 0; q < 24; ++q) {
             int s;
             if (q < 8) s = s0 + q;
-            else if (q < 16) s = (int)(((long long)(q - 7) * slots) / p.n_iblk);
-            else s = cdiv((long long)(q - 15) * slots, p.n_iblk);
+            else if (q < 16) s = (int)udiv((unsigned)(q - 7) * us, nib);
+            else s = (int)ucdiv((unsigned)(q - 15) * us, nib);
             if (s < s0 || s > smax) continue;
-            const long long it = (long long)p.n_iblk * s;
-            if (fill_ok(it, slots) && (first_ok == 0 || s < first_ok)) first_ok = s;
-            if (better_fill(it, slots, (long long)p.n_iblk * best)) best = s;
+            const unsigned it = nib * (unsigned)s;
+            if (fill_ok(it, us) && (first_ok == 0 || s < first_ok)) first_ok = s;
+            if (better_fill(it, us, nib * (unsigned)best)) best = s;
         }
         S = first_ok ? first_ok : best;
     }
@@ -168,6 +173,17 @@ __host__ __device__ inline Plan plan_jpar(int na, int n, int nt, int ic, int slo
     return p;
 }
 
+// Lanes per output of the slice combine: a power of two T <= 32, T <= S, with
+// about 2^18 threads in all (T * 7 na), so that both small blocks with many
+// slices and large blocks with few get enough loads in flight.
+__host__ __device__ inline int combine_lanes(int na, int S)
+{
+    const long long want = (1LL << 18) / ((long long)kComp * (na > 0 ? na : 1));
+    int T = 1;
+    while (T < 32 && T < want && 2 * T <= S) T *= 2;
+    return T;
+}
+
 // Which kernel serves a block of na particles: jpar for na <= jpar_max.
 __host__ __device__ inline bool use_jpar(int na, int jpar_max) { return na <= jpar_max; }
 
@@ -182,12 +198,30 @@ __host__ __device__ inline int regime_of(int na, int jpar_max, int small_max)
     return kRegIpar;
 }
 
+// The work decomposition of one force launch: the block size, the kernel
+// that serves it and that kernel's plan.  It is computed once per launch, by
+// make_force_plan on the host when the block size is known there, else by the
+// scheduler's last thread next to the block size; kernels read it instead of
+// planning in every CTA.
+struct ForcePlan {
+    Plan p;        // plan of the serving kernel (zero for the FP32 summation variants)
+    int na;        // block size
+    int regime;    // kRegJpar / kRegSmall / kRegIpar (summation variants: kRegIpar)
+    int ic;        // j-parallel: i per pass
+    int lanes;     // slice combine: lanes per output
+};
+
 // Everything a force launch needs.
 struct ForceArgs {
     int n;                    // j count
     const int *act;           // active indices (device)
     const int *na_dev;        // device block size, or nullptr to use na_host
     int na_host;
+    ForcePlan plan;           // the plan for na_host (na_dev == nullptr)
+    const ForcePlan *plan_dev;  // the plan for *na_dev, written by the scheduler
+    int precision;            // NB_DS or NB_FP64
+    int summation;            // NB_SUM_*
+    int slots_sum;            // resident CTAs of the summation variant's kernel
     int jpar_max;             // regime boundaries (see regime_of)
     int small_max;
     int split;                // forced slice count for i-parallel, 0 = auto
@@ -226,6 +260,40 @@ constexpr int kFixUnroll = NB_FIX_UNROLL;  // fixed point: j unrolling of the in
 constexpr int kSeqNT = 128;         // FP32 index order: threads per CTA, one i each
 constexpr int kSortNT = 1024;       // FP32 sorted: one CTA per i
 constexpr int kErrFixedScale = 64;  // device error word: fixed-point scales out of range
+
+__host__ __device__ inline ForcePlan make_force_plan(const ForceArgs &fa, int na)
+{
+    ForcePlan f{};
+    f.na = na;
+    f.regime = kRegIpar;
+    if (na <= 0) return f;
+    if (fa.summation == NB_SUM_FIXED) {
+        f.p = plan_ipar(na, fa.n, kFixNT * kFixR, kFixNT, fa.slots_sum, fa.split, fa.part_cap / 2);
+        return f;
+    }
+    if (fa.summation != NB_SUM_COMPENSATED) return f;   // no slices
+    const bool f64 = fa.precision == NB_FP64;
+    f.regime = f64 ? (use_jpar(na, fa.jpar_max) ? kRegJpar : kRegIpar)
+                   : regime_of(na, fa.jpar_max, fa.small_max);
+    if (f.regime == kRegJpar) {
+        f.ic = !f64 && na <= kJparIC1Max ? 1 : kJparIC;
+        f.p = plan_jpar(na, fa.n, kJparNT, f.ic, fa.slots_jpar, fa.part_cap);
+    } else {
+        const int r = f64 ? kIparR64 : (f.regime == kRegSmall ? kIparSmallR : kIparR);
+        const int slots = f.regime == kRegSmall ? fa.slots_small : fa.slots_ipar;
+        f.p = plan_ipar(na, fa.n, kIparNT * r, kIparNT, slots, fa.split, fa.part_cap);
+    }
+    f.lanes = combine_lanes(na, f.p.S);
+    return f;
+}
+
+#ifdef __CUDACC__
+// The plan of this launch (a uniform load for the device-sized launches).
+__device__ __forceinline__ ForcePlan load_plan(const ForceArgs &fa)
+{
+    return fa.plan_dev ? *fa.plan_dev : fa.plan;
+}
+#endif
 
 // Persistent block-step loop (k_run.cu): nb_run in one cooperative launch for
 // systems of up to kRunMaxN particles, kRunNT threads per CTA, one CTA per
@@ -266,6 +334,7 @@ struct VjpArgs {
     double eps2;
     int slots;
     long long part_cap;
+    Plan plan;             // plan_ipar over all n particles (set by the launcher)
     double *part;          // slice partials part[(s * 7 + c) * n + k]
     VjpRecDS rec;
     VjpRec64 rec64;
@@ -306,8 +375,9 @@ void launch_correct(const State &s, const int *act, int na_host, const int *na_d
                     int *err, cudaStream_t st);
 void launch_initial_steps(const State &s, const double *acc, const double *jerk, double eta_init,
                           int level_min, int level_fixed, int *err, cudaStream_t st);
+// Also writes the plan of the force on the new block (make_force_plan(fa, n_active)).
 void launch_schedule(const State &s, Ctrl *ctrl, long long *blockmin, int *blockcnt, int *act,
-                     int nblocks, cudaStream_t st);
+                     int nblocks, const ForceArgs &fa, ForcePlan *plan_out, cudaStream_t st);
 int schedule_blocks(int n);
 void launch_energy(const State &s, const long long *t_ptr, const double *pot, double *part,
                    Ctrl *ctrl, cudaStream_t st);

@@ -21,6 +21,10 @@ using namespace nbk;
 int main() {
     int na, n, iblk, tile, slots, split; long long cap; char kind;
     while (std::scanf(" %c %d %d %d %d %d %d %lld", &kind, &na, &n, &iblk, &tile, &slots, &split, &cap) == 8) {
+        if (kind == 'c') {   // slice combine: lanes per output for na outputs, n slices
+            std::printf("%d 0 0 0\n", combine_lanes(na, n));
+            continue;
+        }
         Plan p = kind == 'i' ? plan_ipar(na, n, iblk, tile, slots, split, cap)
                              : plan_jpar(na, n, tile, iblk, slots, cap);
         std::printf("%d %d %d %d\n", p.n_iblk, p.S, p.jslice, p.items);
@@ -100,3 +104,14 @@ def test_jpar_plans(planner):
         if na == 1 and n == 1 << 20:
             waves = 2 if 2 * slots * 8 * nt <= n else 1
             assert 0.9 * waves * slots <= items <= waves * slots, c
+
+
+def test_combine_lanes(planner):
+    cases = [("c", na, S, 0, 0, 0, 0, 0) for na in (1, 2, 7, 33, 300, 1820, 4096, 65536, 1 << 20)
+             for S in (1, 2, 3, 8, 9, 76, 512, 2432)]
+    for c, (T, _, _, _) in zip(cases, _run(planner, cases)):
+        _, na, S = c[:3]
+        assert T in (1, 2, 4, 8, 16, 32), c
+        assert T == 1 or T <= S, c
+        # doubling T would pass 2^18 threads or S, or T is already 32
+        assert T == 32 or 2 * T > S or T * 7 * na >= 1 << 18, c
