@@ -49,6 +49,9 @@ FP64_SAMPLE = 4096
 L2_FLUSH_BYTES = 256 << 20
 FP32_LANES_PER_SM = 128
 MAX_SM_MHZ_FALLBACK = 2070.0
+J_RECORD_BYTES = 48                # DS j record: three float4
+SWEEP_HBM_MAX_ACTIVE = 2           # sweeps this small are bound by the j-record stream
+HBM_GBS_FALLBACK = 6800.0          # earlier GB300 copy measurement, when no measured file exists
 
 
 def parse_args():
@@ -60,7 +63,8 @@ def parse_args():
     p.add_argument("--n", type=int, default=N_DEFAULT)
     p.add_argument("--no-extras", action="store_true", help="skip ladder, FP64 arm, e2e, CPU baseline")
     p.add_argument("--workload", default="full_active_step",
-                   choices=["full_active_step", "blockstep", "adjoint", "ensemble", "replay", "summation"],
+                   choices=["full_active_step", "blockstep", "adjoint", "ensemble", "replay", "summation",
+                            "sweep"],
                    help="blockstep: individual block steps of a Plummer run (Section 2 step loop)")
     p.add_argument("--t-end", type=float, default=0.25, help="blockstep: end time (multiple of dt_max)")
     p.add_argument("--eps", type=float, default=None, help="blockstep: softening (default 1/256)")
@@ -72,6 +76,8 @@ def parse_args():
     p.add_argument("--baseline-sample", type=int, default=32,
                    help="ensemble: clusters timed one by one through the single-system path")
     p.add_argument("--oracle-n", type=int, default=1024, help="adjoint: size of the CPU FP64 comparison")
+    p.add_argument("--n-active", default="1,96,256,4096",
+                   help="sweep: comma-separated block sizes, each against all N j")
     p.add_argument("--sample-errors", type=int, default=0,
                    help="blockstep: check this many sampled i against the oracle at each of 16 checkpoints")
     return p.parse_args()
@@ -161,6 +167,15 @@ def max_over_ranks(x, device):
 def whole_job_rate(world, steps, units_per_step, elapsed_max):
     """Units processed by all ranks divided by the slowest rank's time."""
     return world * steps * units_per_step / elapsed_max
+
+
+def hbm_peak_gbs():
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return HBM_GBS_FALLBACK
 
 
 def fp32_peak_tflops(sms, mhz):
@@ -355,39 +370,55 @@ def run_mine(args):
         torch.distributed.destroy_process_group()
 
 
-def run_extras(args, nb, ctx, m, x, v, stream, dev, torch, sample_active):
-    n = args.n
-    out = {}
-    # Isolated sweeps: n_active i (uniform without replacement) against all N j.
+def time_sweeps(ctx, n, nas, dev, torch, sample_active, flush):
+    """Isolated force sweeps: for each n_active, that many i (uniform without
+    replacement, seed SEED + n_active) against all n j; 5 warm-ups, then the
+    median of 20 repetitions (3 for the full sweep), each timed with CUDA
+    events around the force kernels, with a memset larger than L2 before each
+    (outside the events) so that the j records come from HBM."""
     ladder = {}
-    for na in SWEEP_LADDER + [n]:
-        if na > n:
-            continue
+    for na in nas:
         idx = torch.from_numpy(sample_active(n, na, SEED + na)).to(dev)
         acc = torch.empty((na, 3), dtype=torch.float64, device=dev)
         jerk = torch.empty_like(acc)
         pot = torch.empty(na, dtype=torch.float64, device=dev)
-        # 5 warm-ups, then the median of 20 repetitions, each timed with CUDA
-        # events (3 for the full sweep, 1.26 s each)
         reps = 3 if na == n else 20
         for _ in range(5):
             ctx.nb_force_dev(idx, na, acc, jerk, pot)
         ctx.nb_set_profiling(True)
-        times = []
+        times, launches = [], 0
         t0 = time.perf_counter()
         for _ in range(reps):
+            flush.zero_()
             ctx.nb_get_stats(reset=True)
             ctx.nb_force_dev(idx, na, acc, jerk, pot)
             st = ctx.nb_get_stats(reset=True)
             times.append(st["force_ms"] / 1e3 / max(1, st["force_launches"]))
+            launches += st["kernel_launches"]
         torch.cuda.synchronize(dev)
         call_s = (time.perf_counter() - t0) / reps
         ctx.nb_set_profiling(False)
         fs = float(np.median(times))
+        # every sweep streams the 48-byte j records once: for a handful of
+        # active i that is the bound
+        jbytes = J_RECORD_BYTES * n
         ladder[str(na)] = {"force_us": fs * 1e6, "force_us_mean": float(np.mean(times)) * 1e6,
-                           "repetitions": reps, "call_us": call_s * 1e6,
+                           "repetitions": reps, "wall_us_per_rep": call_s * 1e6,
+                           "kernel_launches": launches,
                            "interactions_per_s": na * (n - 1) / fs,
-                           "gflops": FLOP_PER_INTERACTION * na * (n - 1) / fs / 1e9}
+                           "gflops": FLOP_PER_INTERACTION * na * (n - 1) / fs / 1e9,
+                           "j_record_gbs": jbytes / fs / 1e9,
+                           "j_record_hbm_frac": jbytes / fs / 1e9 / hbm_peak_gbs()}
+    return ladder
+
+
+def run_extras(args, nb, ctx, m, x, v, stream, dev, torch, sample_active):
+    n = args.n
+    out = {}
+    # Isolated sweeps: n_active i (uniform without replacement) against all N j.
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ladder = time_sweeps(ctx, n, [na for na in SWEEP_LADDER + [n] if na <= n], dev, torch,
+                         sample_active, flush)
     out["sweeps"] = ladder
 
     # The all-FP64 kernel on the same sweep (FP64_SAMPLE active i against all N).
@@ -926,6 +957,62 @@ def run_summation(args):
         torch.distributed.destroy_process_group()
 
 
+def run_sweep(args):
+    """Isolated force sweeps (the block sizes of a block-step run): for each
+    n_active of --n-active, that many i against all N j of the default Plummer
+    system.  value = the first block size's interactions/s; its roofline is the
+    j-record stream (HBM) when the block is at most a few particles, else the
+    FP32 ALU."""
+    import torch
+    import paper_cs_0702135_gb300 as nb
+    from synth import plummer, sample_active
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    n = args.n
+    nas = [int(a) for a in args.n_active.split(",")]
+    if any(na < 1 or na > n for na in nas):
+        raise SystemExit("--n-active entries must lie in [1, N]")
+    m, x, v = plummer(n, SEED + rank)
+    ctx = nb.Context(m, x, v, EPS, flags=nb.NB_INIT_NO_FORCE, stream=stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    sampler = ClockSampler(nvsmi_index(local))
+    sampler.start()
+    ladder = time_sweeps(ctx, n, nas, dev, torch, sample_active, flush)
+    clocks = sampler.stop()
+    launches = sum(e["kernel_launches"] for e in ladder.values())
+    first = ladder[str(nas[0])]
+    if nas[0] <= SWEEP_HBM_MAX_ACTIVE:
+        roofline = {"bound": "hbm", "achieved": first["j_record_gbs"], "peak": hbm_peak_gbs(),
+                    "unit": "GB/s", "frac": first["j_record_hbm_frac"], "traffic": None,
+                    "kernel": "k_force_jpar_ds (%d active i; algorithmic bytes: the 48-byte j "
+                              "records of all N, read once)" % nas[0]}
+    else:
+        peak = fp32_peak_tflops(sms, MAX_SM_MHZ_FALLBACK)
+        ach = FLOP_PER_INTERACTION * first["interactions_per_s"] / 1e12
+        roofline = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None,
+                    "kernel": "force kernels of a %d-particle block (60 flop per interaction)" % nas[0]}
+    line = {
+        "metric": "isolated force sweep: acc+jerk interactions/s", "value": first["interactions_per_s"],
+        "unit": UNIT, "n_gpus": 1, "steps": sum(e["repetitions"] for e in ladder.values()),
+        "warmup": 5 * len(nas), "ms_per_step": first["force_us"] / 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "plummer_N%d_eps1/1024_isolated_sweeps" % n, "N": n, "eps": EPS,
+                   "seed": SEED, "n_active": nas,
+                   "l2": "a 256 MiB memset before each repetition, outside the timed region"},
+        "sweeps": ladder, "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
+        "device": {"name": props.name, "sms": sms},
+    }
+    ctx.nb_free()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -940,6 +1027,8 @@ def main():
         run_replay(args)
     elif args.workload == "summation":
         run_summation(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_mine(args)
 

@@ -73,10 +73,10 @@ constexpr int kIparR64 = 1;    // i per thread, FP64 i-parallel kernel
 constexpr int kJparNT = 256;   // threads per CTA, j-parallel kernels
 constexpr int kJparIC = 4;     // i per pass, j-parallel kernels
 constexpr int kJparIC1Max = 2;  // DS j-parallel kernel: one i per pass up to this block size
-constexpr int kJparMaxActive = 64;     // automatic mode, DS: j-parallel up to this block size
+constexpr int kJparMaxActive = 96;     // automatic mode, DS: j-parallel up to this block size
 constexpr int kJparMaxActive64 = 32;   // automatic mode, FP64
 constexpr int kIparSmallR = 1;      // i per thread of the small-block DS i-parallel kernel
-constexpr int kSmallMaxActive = 192;  // automatic mode: small-block kernel up to this size
+constexpr int kSmallMaxActive = 1024;  // automatic mode: small-block kernel considered up to this size
 constexpr int kComp = 7;       // acc xyz, jerk xyz, pot
 
 struct Plan {
@@ -188,13 +188,24 @@ __host__ __device__ inline int combine_lanes(int na, int S)
 __host__ __device__ inline bool use_jpar(int na, int jpar_max) { return na <= jpar_max; }
 
 // Force kernels by block size: j-parallel, small-block i-parallel (one i per
-// thread), i-parallel (kIparR i per thread).  small_max <= jpar_max disables
-// the middle one.
+// thread, blocks of kIparNT i), i-parallel (kIparR i per thread, blocks of
+// kIparNT * kIparR i).  The small-block kernel runs at about three quarters of
+// the other's rate on full blocks, so it serves a block when its padded i
+// count is at most 3/4 of the other's: up to 192, 257..384 and 513..576 active
+// with 64-i and 256-i blocks (measured crossings on 2^16 and 2^20 bodies).
+// small_max <= jpar_max disables it.
+__host__ __device__ inline bool small_pays(int na)
+{
+    const long long s = (long long)cdiv(na, kIparNT) * kIparNT;
+    const long long r = (long long)cdiv(na, kIparNT * kIparR) * (kIparNT * kIparR);
+    return 4 * s <= 3 * r;
+}
+
 enum Regime { kRegJpar = 0, kRegSmall = 1, kRegIpar = 2 };
 __host__ __device__ inline int regime_of(int na, int jpar_max, int small_max)
 {
     if (na <= jpar_max) return kRegJpar;
-    if (na <= small_max) return kRegSmall;
+    if (na <= small_max && small_pays(na)) return kRegSmall;
     return kRegIpar;
 }
 

@@ -25,6 +25,10 @@ int main() {
             std::printf("%d 0 0 0\n", combine_lanes(na, n));
             continue;
         }
+        if (kind == 'r') {   // regime for na active with jpar_max = n, small_max = iblk
+            std::printf("%d 0 0 0\n", regime_of(na, n, iblk));
+            continue;
+        }
         Plan p = kind == 'i' ? plan_ipar(na, n, iblk, tile, slots, split, cap)
                              : plan_jpar(na, n, tile, iblk, slots, cap);
         std::printf("%d %d %d %d\n", p.n_iblk, p.S, p.jslice, p.items);
@@ -115,3 +119,17 @@ def test_combine_lanes(planner):
         assert T == 1 or T <= S, c
         # doubling T would pass 2^18 threads or S, or T is already 32
         assert T == 32 or 2 * T > S or T * 7 * na >= 1 << 18, c
+
+
+def test_regimes(planner):
+    # automatic mode: j-parallel up to 96, then the one-i-per-thread kernel
+    # whenever its 64-i padding is at most 3/4 of the 256-i padding
+    cases = [("r", na, 96, 1024, 0, 0, 0, 0) for na in range(1, 1500)]
+    got = {c[1]: r[0] for c, r in zip(cases, _run(planner, cases))}
+    small = {na for na in range(1, 1500) if 96 < na <= 192 or 256 < na <= 384 or 512 < na <= 576}
+    for na, reg in got.items():
+        want = 0 if na <= 96 else (1 if na in small else 2)
+        assert reg == want, (na, reg)
+    # small_max <= jpar_max disables the small-block kernel; jpar_max = 0 the j-parallel one
+    cases = [("r", na, 0, 0, 0, 0, 0, 0) for na in (1, 100, 300)]
+    assert [r[0] for r in _run(planner, cases)] == [2, 2, 2]
