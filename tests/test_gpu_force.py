@@ -1,9 +1,11 @@
 """Parity of the CUDA force sweep (nb_force) with the FP64 oracle.
 
-Sizes span several 128-j tiles and ragged tails, block sizes cover the
-edges of the i-blocks (1, 7, 16/17 at the j-parallel boundary, 31..33,
-255..257, N), both kernels are forced as well as chosen automatically, and
-both precisions are checked.
+Sizes span several tiles and ragged tails, block sizes cover the edges of
+the i-blocks and of the automatic regimes (one or four i per pass of the
+j-parallel kernel at 2/3, j-parallel up to 96, the one-i-per-thread kernel
+for 97..192, 257..384 and 513..576, four i per thread otherwise), both
+kernels are forced as well as chosen automatically, and both precisions are
+checked.
 """
 import numpy as np
 import pytest
@@ -39,7 +41,8 @@ def test_full_sweep(nb, n, precision):
 
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1, 2])
-@pytest.mark.parametrize("na", [1, 7, 16, 17, 31, 32, 33, 64, 65, 191, 192, 193, 255, 256, 257, 1000])
+@pytest.mark.parametrize("na", [1, 2, 3, 7, 16, 17, 31, 32, 33, 64, 65, 96, 97, 191, 192, 193, 255, 256,
+                                257, 384, 385, 576, 577, 1000])
 def test_block_sizes_and_kernels(nb, na, mode, precision):
     n = 3001
     m, x, v = plummer(n, 7)

@@ -223,6 +223,38 @@ def test_host_driven_step_matches_device_step(nb):
         nb.nb_free(b)
 
 
+@pytest.mark.parametrize("k", [1, 5, 97, 300, 513, 700, 3000])
+def test_device_and_host_force_plans_agree(nb, k):
+    # The force of a device-driven step is planned by the scheduler on the
+    # device, that of nb_force by the host; for blocks in every regime (one or
+    # four i per pass of the j-parallel kernel, one or four i per thread of the
+    # i-parallel kernels, several slices) the two steps must agree bit for bit.
+    n = 40000
+    m, x, v = plummer(n, 12)
+    a = nb.nb_init(m, x, v, EPS)
+    b = nb.nb_init(m, x, v, EPS)
+    try:
+        st = nb.nb_get_state(a)
+        lev = np.full(n, 10, dtype=np.int32)
+        block = np.sort(np.random.default_rng(k).choice(n, size=k, replace=False)).astype(np.int32)
+        lev[block] = 12
+        t = np.zeros(n, dtype=np.int64)
+        for c in (a, b):
+            nb.nb_set_state(c, st["x"], st["v"], st["a"], st["k"], t, lev)
+        tn = 1 << (40 - 12)
+        nb.nb_predict(a, tn / T)
+        nb.nb_force(a, block)
+        nb.nb_correct(a, block, tn / T)
+        tb, na = nb.nb_step(b)
+        assert na == k and tb == tn / T
+        s1, s2 = nb.nb_get_state(a), nb.nb_get_state(b)
+        for key in s1:
+            assert np.array_equal(s1[key], s2[key]), key
+    finally:
+        nb.nb_free(a)
+        nb.nb_free(b)
+
+
 def test_shared_step_mode(nb):
     m, x, v = plummer(256, 8)
     ctx = nb.nb_init(m, x, v, EPS, nb.nb_default_opts(level_fixed=10))
