@@ -41,9 +41,12 @@ extern "C" {
 #define NB_DS 0   /* FP32 pair arithmetic on double-single (hi + lo FP32) positions */
 #define NB_FP64 1 /* all pair arithmetic in FP64 */
 
-#define NB_FORCE_AUTO 0  /* pick the force kernel from n_active */
-#define NB_FORCE_IPAR 1  /* i across threads, j tiles broadcast from shared memory (the
-                          * small-block variant, one i per thread, serves n_active <= 192) */
+#define NB_FORCE_AUTO 0  /* pick the force kernel from n_active (DS: j-parallel up to 96,
+                          * then the i-parallel kernels) */
+#define NB_FORCE_IPAR 1  /* i across threads, j tiles broadcast from shared memory; DS uses
+                          * the one-i-per-thread variant wherever its 64-i blocks pad the
+                          * block by at most 3/4 of the 256-i blocks (n_active <= 192,
+                          * 257..384, 513..576), four i per thread otherwise */
 #define NB_FORCE_JPAR 2  /* j across threads, warp-shuffle tree reduction (small n_active) */
 
 /*
