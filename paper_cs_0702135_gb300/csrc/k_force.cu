@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(NT) k_force_ipar_ds(ForceArgs fa, JDS J)
     const int na = F.na;
     if (na <= 0 || F.regime != REG) return;
     const Plan P = F.p;
-    __shared__ float4 s_p[NT], s_l[NT], s_v[NT];
+    constexpr int TL = NT * kIparTileMult;   // j per shared-memory tile
+    __shared__ float4 s_p[TL], s_l[TL], s_v[TL];
     const float eps2 = (float)fa.eps2;
     const int tid = threadIdx.x;
 
@@ -107,17 +108,20 @@ __global__ void __launch_bounds__(NT) k_force_ipar_ds(ForceArgs fa, JDS J)
 #pragma unroll
             for (int c = 0; c < kComp; ++c) hi[r][c] = lo[r][c] = 0.0f;
 
-        for (int jt = j0; jt < j1; jt += NT) {
+        for (int jt = j0; jt < j1; jt += TL) {
             __syncthreads();
-            const int j = jt + tid;
-            if (j < j1) {
-                s_p[tid] = J.pos_hi[j];
-                s_l[tid] = J.pos_lo[j];
-                s_v[tid] = J.vel[j];
-            } else {
-                s_p[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-                s_l[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-                s_v[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < kIparTileMult; ++u) {
+                const int t = tid + u * NT, j = jt + t;
+                if (j < j1) {
+                    s_p[t] = J.pos_hi[j];
+                    s_l[t] = J.pos_lo[j];
+                    s_v[t] = J.vel[j];
+                } else {
+                    s_p[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    s_l[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    s_v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
             }
             __syncthreads();
             float ta[R][3], tk[R][3], tp[R];
@@ -129,9 +133,9 @@ __global__ void __launch_bounds__(NT) k_force_ipar_ds(ForceArgs fa, JDS J)
             }
             bool mine = false;
 #pragma unroll
-            for (int r = 0; r < R; ++r) mine |= (unsigned)(ii[r] - jt) < (unsigned)NT;
+            for (int r = 0; r < R; ++r) mine |= (unsigned)(ii[r] - jt) < (unsigned)TL;
             if (__any_sync(0xffffffffu, mine)) {
-                for (int jj = 0; jj < NT; ++jj) {
+                for (int jj = 0; jj < TL; ++jj) {
                     const float4 p = s_p[jj], l = s_l[jj], v = s_v[jj];
 #pragma unroll
                     for (int r = 0; r < R; ++r)
@@ -140,7 +144,7 @@ __global__ void __launch_bounds__(NT) k_force_ipar_ds(ForceArgs fa, JDS J)
                 }
             } else {
 #pragma unroll (kIparUnroll)
-                for (int jj = 0; jj < NT; ++jj) {
+                for (int jj = 0; jj < TL; ++jj) {
                     const float4 p = s_p[jj], l = s_l[jj], v = s_v[jj];
 #pragma unroll
                     for (int r = 0; r < R; ++r)

@@ -69,6 +69,10 @@ struct ForceOut {
 constexpr int kIparNT = NB_IPAR_NT;  // threads per CTA (= j per tile), i-parallel kernels
 constexpr int kIparR = NB_IPAR_R;    // i per thread, DS i-parallel kernel
 constexpr int kIparUnroll = NB_IPAR_UNROLL;  // j unrolling of the DS inner loop
+#ifndef NB_IPAR_TILE_MULT
+#define NB_IPAR_TILE_MULT 2
+#endif
+constexpr int kIparTileMult = NB_IPAR_TILE_MULT;  // DS i-parallel: j per tile = threads x this
 constexpr int kIparR64 = 1;    // i per thread, FP64 i-parallel kernel
 constexpr int kJparNT = 256;   // threads per CTA, j-parallel kernels
 constexpr int kJparIC = 4;     // i per pass, j-parallel kernels
@@ -292,7 +296,8 @@ __host__ __device__ inline ForcePlan make_force_plan(const ForceArgs &fa, int na
     } else {
         const int r = f64 ? kIparR64 : (f.regime == kRegSmall ? kIparSmallR : kIparR);
         const int slots = f.regime == kRegSmall ? fa.slots_small : fa.slots_ipar;
-        f.p = plan_ipar(na, fa.n, kIparNT * r, kIparNT, slots, fa.split, fa.part_cap);
+        f.p = plan_ipar(na, fa.n, kIparNT * r, kIparNT * (f64 ? 1 : kIparTileMult), slots, fa.split,
+                        fa.part_cap);
     }
     f.lanes = combine_lanes(na, f.p.S);
     return f;
