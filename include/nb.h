@@ -111,7 +111,8 @@ void nb_default_opts(nb_opts *opts);
  * With opts->flags & NB_INIT_NO_FORCE the start-up sweep is skipped:
  * acceleration and jerk start at zero and every level at level_min, for
  * callers that only use nb_force or that load a state with nb_set_state.
- * Errors: NB_EINVAL (n < 1 or n > 2^31 - 1, eps < 0, non-finite input, bad
+ * Errors: NB_EINVAL (n < 1 or n > 2^28 - 1 (the largest count whose 8-byte
+ * per-particle index arithmetic stays in 32 bits), eps < 0, non-finite input, bad
  * opts, among them a summation other than NB_SUM_COMPENSATED with NB_FP64, or
  * NB_SUM_FIXED with eps^2 not a normal single-precision number), NB_ENOMEM,
  * NB_ECUDA, NB_ESTEP.  On error *ctx is NULL.
