@@ -76,6 +76,8 @@ def parse_args():
     p.add_argument("--baseline-sample", type=int, default=32,
                    help="ensemble: clusters timed one by one through the single-system path")
     p.add_argument("--oracle-n", type=int, default=1024, help="adjoint: size of the CPU FP64 comparison")
+    p.add_argument("--cpu-budget", type=float, default=20.0,
+                   help="blockstep: seconds of the oracle's integrator timed beside the GPU run")
     p.add_argument("--n-active", default="1,96,256,4096",
                    help="sweep: comma-separated block sizes, each against all N j")
     p.add_argument("--sample-errors", type=int, default=0,
@@ -542,7 +544,54 @@ def run_blockstep(args):
         ctx.nb_free()
     if "ds" in out and "fp64" in out:
         out["ds_over_fp64"] = out["ds"]["interactions_per_s"] / out["fp64"]["interactions_per_s"]
+    if not args.no_extras:
+        out["cpu_baseline"] = oracle_blockstep_rate(m, x, v, eps, level_min, args.t_end,
+                                                    out.get("ds", out.get("fp64")), args.cpu_budget)
     print(json.dumps(out), flush=True)
+
+
+def oracle_blockstep_rate(m, x, v, eps, level_min, t_end, gpu, budget_s):
+    """The oracle's FP64 integrator (OpenMP force on all host cores) from the
+    same initial conditions: the whole run when it ends within budget_s, else
+    its first block steps until budget_s has passed; interactions/s over those
+    steps and, for a partial run, the full run's time projected from the GPU
+    run's interaction count at that rate (stated)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.lib()
+    n = m.shape[0]
+    t0 = time.perf_counter()
+    orc = oracle.Integrator(m, x, v, eps, kmin=level_min, nthreads=threads)
+    init_s = time.perf_counter() - t0
+    t_end_ticks = int(round(t_end * oracle.TICKS_PER_UNIT))
+    steps, inter, done = 0, 0, False
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        tn, act = orc.step(t_end_ticks)
+        if len(act) == 0 or tn > t_end_ticks:
+            done = True
+            break
+        steps += 1
+        inter += len(act) * (n - 1)
+        if tn == t_end_ticks and int(orc.t.min()) == t_end_ticks:
+            done = True
+            break
+    el = time.perf_counter() - t0
+    rate = inter / el if el > 0 else 0.0
+    res = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "steps": steps,
+           "seconds": el, "startup_sweep_s": init_s, "whole_run": done}
+    if done:
+        res["sample"] = "the oracle's whole run (%d block steps, %.1f s after a %.1f s start-up sweep)" % (
+            steps, el, init_s)
+    else:
+        proj = gpu["interactions"] / rate if rate > 0 else None
+        res["sample"] = ("the oracle's first %d block steps of the same run (%.1f s; the GPU run took "
+                         "%d); whole run projected at %.0f s from the GPU run's interaction count"
+                         % (steps, el, gpu["steps"], proj or float("nan")))
+        res["projected_whole_run_s"] = proj
+    if gpu and rate > 0:
+        res["gpu_over_oracle"] = gpu["interactions_per_s"] / rate
+    return res
 
 
 def sampled_force_errors(ctx, nb, m, eps, k, seed):
