@@ -560,6 +560,19 @@ def oracle_blockstep_rate(m, x, v, eps, level_min, t_end, gpu, budget_s):
     threads = os.cpu_count() or 1
     oracle.lib()
     n = m.shape[0]
+    if float(n) * n > 5e8 * budget_s:
+        # the integrator's start-up sweep alone (n^2 FP64 pairs) would exceed the
+        # budget: time the oracle's force on a sample of the particles instead
+        rate, thr, na_s, secs = cpu_oracle_rate(m, x, v, eps, budget_s=budget_s / 2)
+        res = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle", "whole_run": False,
+               "sample": "the oracle's FP64 force (OpenMP) on %d of the %d particles against all j, "
+                         "%.1f s (its integrator's start-up sweep alone would exceed the %.0f s "
+                         "budget); whole run projected from the GPU run's interaction count"
+                         % (na_s, n, secs, budget_s)}
+        if gpu and rate > 0:
+            res["projected_whole_run_s"] = gpu["interactions"] / rate
+            res["gpu_over_oracle"] = gpu["interactions_per_s"] / rate
+        return res
     t0 = time.perf_counter()
     orc = oracle.Integrator(m, x, v, eps, kmin=level_min, nthreads=threads)
     init_s = time.perf_counter() - t0
