@@ -17,9 +17,11 @@
 //      |vx|+|vy|+|vz|);
 //   3. force partials: every CTA sums every block particle's pair terms over
 //      its own particles as j and writes them per (CTA, block particle);
-//   4. block particle a is corrected by CTA a mod (CTAs): its partials added in
-//      CTA order, FP64 corrector and Aarseth step.  The corrector's FP64 chain
-//      is long, so spreading the block evenly keeps every CTA's share short.
+//   4. block particle a is corrected by CTA a mod (CTAs): a warp adds its
+//      partials over the CTAs (lanes over CTAs, then a fixed shuffle tree),
+//      then one thread runs the FP64 corrector and Aarseth step.  The
+//      corrector's FP64 chain is long, so spreading the block evenly keeps
+//      every CTA's share short.
 // Everything that other CTAs wrote in the same launch (state included, since
 // a particle may be corrected by any CTA) is read past L1 (__ldcg).  Two summations: the
 // compensated double-single sums (TwoSum-promoted FP32 partials, FP64 across
@@ -231,6 +233,7 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
     __shared__ unsigned s_redu[kRunNT / 32];
     __shared__ int s_wtot[kRunNT / 32];
     __shared__ int s_ok, s_err;
+    __shared__ double s_res[kRunNT][kComp];   // phase 5: combined force of this CTA's block particles
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, r = blockIdx.x;
     const State &S = ra.s;
     const int n = ra.n;
@@ -352,36 +355,60 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
             const unsigned bounds[2] = {bm, bv};
             scale_ok = fixed_scale(bounds, ra.eps2f, Sc);
         }
-        for (long long a = r + (long long)ra.ncta * tid; scale_ok && a < na;
-             a += (long long)ra.ncta * kRunNT) {
-            double res[7];
-            if (MODE == NB_SUM_FIXED) {
-                const long long *part = reinterpret_cast<const long long *>(ra.part);
+        // this CTA's block particles are a = r + CTAs * k, k = 0, 1, ...: first
+        // warp w adds the partials of particles k = w, w + 8, ... over the CTAs
+        // (lane l takes CTAs l, l + 32, ... in order, then a fixed xor tree;
+        // exact in fixed point), then thread k corrects particle k
+        const long long cnt_r = na > r ? (na - 1 - r) / ra.ncta + 1 : 0;
+        for (long long k0 = 0; scale_ok && k0 < cnt_r; k0 += kRunNT) {
+            const int kn = (int)min((long long)kRunNT, cnt_r - k0);
+            for (int k = warp; k < kn; k += kRunNT / 32) {
+                const long long a = r + (long long)ra.ncta * (k0 + k);
+                if (MODE == NB_SUM_FIXED) {
+                    const long long *part = reinterpret_cast<const long long *>(ra.part);
 #pragma unroll
-                for (int c = 0; c < 7; ++c) {
-                    long long hi = 0;
-                    unsigned long long lo = 0;
-                    for (int q = 0; q < ra.ncta; ++q) {
-                        const long long *pp = part + 2 * (((long long)q * n + a) * kComp + c);
-                        const unsigned long long l2 = lo + (unsigned long long)__ldcg(&pp[1]);
-                        hi += __ldcg(&pp[0]) + (l2 < lo ? 1 : 0);
-                        lo = l2;
+                    for (int c = 0; c < 7; ++c) {
+                        long long hi = 0;
+                        unsigned long long lo = 0;
+                        for (int q = lane; q < ra.ncta; q += 32) {
+                            const long long *pp = part + 2 * (((long long)q * n + a) * kComp + c);
+                            const unsigned long long l2 = lo + (unsigned long long)__ldcg(&pp[1]);
+                            hi += __ldcg(&pp[0]) + (l2 < lo ? 1 : 0);
+                            lo = l2;
+                        }
+#pragma unroll
+                        for (int o = 16; o >= 1; o >>= 1) {
+                            const long long h2 = __shfl_xor_sync(kFullR, hi, o);
+                            const unsigned long long l2 = __shfl_xor_sync(kFullR, lo, o);
+                            const unsigned long long ls = lo + l2;
+                            hi += h2 + (ls < lo ? 1 : 0);
+                            lo = ls;
+                        }
+                        if (lane == 0)
+                            s_res[k][c] = __dmul_rn(i128_to_double(hi, lo),
+                                                    c < 3 ? Sc.inv[0] : (c < 6 ? Sc.inv[1] : Sc.inv[2]));
                     }
-                    res[c] = __dmul_rn(i128_to_double(hi, lo),
-                                       c < 3 ? Sc.inv[0] : (c < 6 ? Sc.inv[1] : Sc.inv[2]));
-                }
-            } else {
+                } else {
 #pragma unroll
-                for (int c = 0; c < 7; ++c) {
-                    double s = 0.0;
-                    for (int q = 0; q < ra.ncta; ++q) s += __ldcg(&ra.part[((long long)q * n + a) * kComp + c]);
-                    res[c] = s;
+                    for (int c = 0; c < 7; ++c) {
+                        double sum = 0.0;
+                        for (int q = lane; q < ra.ncta; q += 32)
+                            sum += __ldcg(&ra.part[((long long)q * n + a) * kComp + c]);
+#pragma unroll
+                        for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(kFullR, sum, o);
+                        if (lane == 0) s_res[k][c] = sum;
+                    }
                 }
             }
-            const double ap[3] = {res[0], res[1], res[2]}, kp[3] = {res[3], res[4], res[5]};
-            const int i = (int)__ldcg(&ra.act[a]);
-            if (!correct_particle<true>(S, i, n, tn, ap, kp, ra.eta, ra.level_min, ra.level_fixed))
-                atomicCAS(&ra.ctrl->err, 0, NB_ESTEP);
+            __syncthreads();
+            if (tid < kn) {
+                const double ap[3] = {s_res[tid][0], s_res[tid][1], s_res[tid][2]};
+                const double kp[3] = {s_res[tid][3], s_res[tid][4], s_res[tid][5]};
+                const int i = (int)__ldcg(&ra.act[r + (long long)ra.ncta * (k0 + tid)]);
+                if (!correct_particle<true>(S, i, n, tn, ap, kp, ra.eta, ra.level_min, ra.level_fixed))
+                    atomicCAS(&ra.ctrl->err, 0, NB_ESTEP);
+            }
+            __syncthreads();
         }
         ++steps;
         if (r == 0 && tid == 0) {
