@@ -184,9 +184,9 @@ int nb_step(nb_ctx *ctx, double *t_out, int32_t *n_active_out);
 /*
  * Block steps until every particle has reached t_end (which must be a multiple
  * of the largest step so that all particles meet there), or max_steps steps.
- * For n <= 8192 with precision NB_DS and summation NB_SUM_COMPENSATED or
- * NB_SUM_FIXED the whole loop runs in one persistent launch (one CTA per 32
- * to 128 particles, grid barriers between the stages of a step, no host
+ * For n <= 16384 with precision NB_DS and summation NB_SUM_COMPENSATED or
+ * NB_SUM_FIXED the whole loop runs in one persistent launch (up to 128 CTAs
+ * of 32 to 128 particles, grid barriers between the stages of a step, no host
  * synchronisation); otherwise, or with nb_opts.flags & NB_RUN_GRAPH, each step
  * is replayed from a captured CUDA graph of the per-stage kernels.  The two
  * forms take the same steps with the same arithmetic except the order in

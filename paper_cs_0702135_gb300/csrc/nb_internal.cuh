@@ -315,7 +315,7 @@ __device__ __forceinline__ ForcePlan load_plan(const ForceArgs &fa)
 // systems of up to kRunMaxN particles, kRunNT threads per CTA, one CTA per
 // `per` particles.
 constexpr int kRunNT = 256;
-constexpr int kRunMaxN = 8192;   // above it the per-stage graph, using every SM for the force, is faster
+constexpr int kRunMaxN = 16384;   // above it the per-stage graph, using every SM for the force, is faster
 struct RunArgs {
     State s;
     JDS j;

@@ -1,5 +1,5 @@
 """The persistent nb_run (the whole block-step loop in one launch for n <=
-8192) against the oracle and against the per-stage graph.
+16384) against the oracle and against the per-stage graph.
 
 With the fixed-point summation the sums are exact, so the persistent run, the
 per-stage graph and the oracle's integrator must agree bit for bit over whole
@@ -138,9 +138,10 @@ def test_persistent_run_reports_nb_estep(nb):
         nb.nb_free(ctx)
 
 
-@pytest.mark.parametrize("n", [1, 8192, 8193])
+@pytest.mark.parametrize("n", [1, 4097, 8193, 16384, 16385])
 def test_sizes_at_the_edges(nb, n):
-    # one particle; the largest persistent size; the first graph size
+    # one particle; the first sizes past 64 CTAs of 64 and of 64 CTAs of 128
+    # particles (new layouts); the largest persistent size; the first graph size
     m, x, v = plummer(n, 30, exact_virial_max=0)
     a = nb.Context(m, x, v, EPS, summation=nb.NB_SUM_FIXED)
     b = nb.Context(m, x, v, EPS, summation=nb.NB_SUM_FIXED, flags=nb.NB_RUN_GRAPH)
