@@ -29,6 +29,21 @@ int main() {
             std::printf("%d 0 0 0\n", regime_of(na, n, iblk));
             continue;
         }
+        if (kind == 'f') {   // whole force plan: precision = tile, split = split, slots = slots
+            ForceArgs fa{};
+            fa.n = n;
+            fa.precision = tile;
+            fa.summation = NB_SUM_COMPENSATED;
+            fa.jpar_max = tile == NB_FP64 ? kJparMaxActive64 : kJparMaxActive;
+            fa.small_max = tile == NB_FP64 ? 0 : kSmallMaxActive;
+            fa.split = split;
+            fa.slots_ipar = fa.slots_jpar = fa.slots_small = slots;
+            fa.part_cap = cap;
+            const ForcePlan f = make_force_plan(fa, na);
+            std::printf("%d %d %d %d %d %d %d %d\n", f.regime, f.ic, f.lanes, f.p.n_iblk, f.p.S,
+                        f.p.jslice, f.p.items, f.na);
+            continue;
+        }
         Plan p = kind == 'i' ? plan_ipar(na, n, iblk, tile, slots, split, cap)
                              : plan_jpar(na, n, tile, iblk, slots, cap);
         std::printf("%d %d %d %d\n", p.n_iblk, p.S, p.jslice, p.items);
@@ -58,6 +73,13 @@ def _run(exe, cases):
     inp = "\n".join(" ".join(str(v) for v in c) for c in cases)
     out = subprocess.run([str(exe)], input=inp, capture_output=True, text=True, check=True).stdout
     return [tuple(int(v) for v in line.split()) for line in out.strip().splitlines()]
+
+
+def _part_cap(n, slots, f64):
+    # the context's partial buffer: 16 slots of i-blocks, four slices of all
+    # n, or the j-parallel kernel's 8 slots of 4-i chunks, in 7-value records
+    iblk = 64 * (1 if f64 else 4)
+    return 7 * max(16 * slots * iblk, 4 * n, 8 * slots * 4)
 
 
 def test_ipar_plans(planner):
@@ -133,3 +155,33 @@ def test_regimes(planner):
     # small_max <= jpar_max disables the small-block kernel; jpar_max = 0 the j-parallel one
     cases = [("r", na, 0, 0, 0, 0, 0, 0) for na in (1, 100, 300)]
     assert [r[0] for r in _run(planner, cases)] == [2, 2, 2]
+
+
+def test_force_plans(planner):
+    # The plan a force launch runs with, for both precisions: the serving
+    # kernel, i per pass (one for DS blocks of one or two), the slice partials
+    # within the buffer, the combine's lanes, and the slices covering all j.
+    cases = []
+    for na, n, slots, prec, split in itertools.product(
+            [1, 2, 3, 5, 32, 33, 96, 97, 192, 193, 300, 513, 600, 4096, 65536],
+            [100, 3001, 65536, 1 << 20], [608, 1216, 2432], [0, 1], [0, 3]):
+        if na > n:
+            continue
+        cases.append(("f", na, n, 0, prec, slots, split, _part_cap(n, slots, prec == 1)))
+    for c, out in zip(cases, _run(planner, cases)):
+        _, na, n, _, prec, slots, split, cap = c
+        regime, ic, lanes, nib, S, js, items, fna = out
+        assert fna == na
+        jmax = 32 if prec == 1 else 96
+        if na <= jmax:
+            assert regime == 0, c
+            assert ic == (1 if prec == 0 and na <= 2 else 4), c
+            assert nib * ic * 7 * S <= cap, c          # j-parallel partials per chunk slot
+        else:
+            assert regime in (1, 2) and (prec == 0 or regime == 2), c
+            assert ic == 0
+            assert S == 1 or S * 7 * na <= cap, c
+            if split:
+                assert S <= split
+        assert (S - 1) * js < n <= S * js and items == nib * S, c
+        assert lanes in (1, 2, 4, 8, 16, 32) and (lanes == 1 or lanes <= S), c
