@@ -29,6 +29,14 @@ namespace {
 using namespace dev;
 
 constexpr int kVNT = 128;  // threads per CTA = partners per tile
+#ifndef NB_VJP_R
+#define NB_VJP_R 2
+#endif
+#ifndef NB_VJP_UNROLL
+#define NB_VJP_UNROLL 4
+#endif
+constexpr int kVKR = NB_VJP_R;          // DS: particles k per thread
+constexpr int kVUnroll = NB_VJP_UNROLL; // DS: partner unrolling
 
 // One particle's VJP record: (predicted) position and velocity, mass and the
 // cotangents of its acc and jerk, in the layout of the context's precision.
@@ -105,6 +113,7 @@ __device__ __forceinline__ void vjp_pair_ds(const VjpRec &P, const VjpRec &Kp, f
 template <bool SOFT>
 __global__ void __launch_bounds__(kVNT) k_force_vjp_ds(VjpArgs va)
 {
+    constexpr int R = kVKR;
     const Plan P = va.plan;
     __shared__ float4 s_ph[kVNT], s_pl[kVNT], s_v[kVNT], s_ab[kVNT], s_kb[kVNT];
     const float eps2 = (float)va.eps2;
@@ -113,14 +122,18 @@ __global__ void __launch_bounds__(kVNT) k_force_vjp_ds(VjpArgs va)
         const int ib = w % P.n_iblk, sl = w / P.n_iblk;
         const int j0 = sl * P.jslice;
         const int j1 = min(va.n, j0 + P.jslice);
-        const int kk = ib * kVNT + tid;
-        const int k = clamp_index(kk, va.n);
-        VjpRec K;
-        K.ph = va.rec.ph[k]; K.pl = va.rec.pl[k]; K.v = va.rec.v[k];
-        K.ab = va.rec.ab[k]; K.kb = va.rec.kb[k];
-        float hi[7], lo[7];
+        int kk[R], k[R];
+        VjpRec K[R];
+        float hi[R][7], lo[R][7];
 #pragma unroll
-        for (int c = 0; c < 7; ++c) hi[c] = lo[c] = 0.0f;
+        for (int r = 0; r < R; ++r) {
+            kk[r] = ib * kVNT * R + r * kVNT + tid;
+            k[r] = clamp_index(kk[r], va.n);
+            K[r].ph = va.rec.ph[k[r]]; K[r].pl = va.rec.pl[k[r]]; K[r].v = va.rec.v[k[r]];
+            K[r].ab = va.rec.ab[k[r]]; K[r].kb = va.rec.kb[k[r]];
+#pragma unroll
+            for (int c = 0; c < 7; ++c) hi[r][c] = lo[r][c] = 0.0f;
+        }
         for (int jt = j0; jt < j1; jt += kVNT) {
             __syncthreads();
             const int j = jt + tid;
@@ -131,39 +144,51 @@ __global__ void __launch_bounds__(kVNT) k_force_vjp_ds(VjpArgs va)
             s_ab[tid] = j < j1 ? va.rec.ab[j] : z;
             s_kb[tid] = j < j1 ? va.rec.kb[j] : z;
             __syncthreads();
-            float t[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const bool mine = (unsigned)(k - jt) < (unsigned)kVNT;
+            float t[R][7];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int c = 0; c < 7; ++c) t[r][c] = 0.0f;
+            bool mine = false;
+#pragma unroll
+            for (int r = 0; r < R; ++r) mine |= (unsigned)(k[r] - jt) < (unsigned)kVNT;
             if (__any_sync(0xffffffffu, mine)) {
                 for (int jj = 0; jj < kVNT; ++jj) {
                     VjpRec Pq;
                     Pq.ph = s_ph[jj]; Pq.pl = s_pl[jj]; Pq.v = s_v[jj]; Pq.ab = s_ab[jj]; Pq.kb = s_kb[jj];
-                    vjp_pair_ds<SOFT, true>(Pq, K, eps2, t, jt + jj, k);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) vjp_pair_ds<SOFT, true>(Pq, K[r], eps2, t[r], jt + jj, k[r]);
                 }
             } else {
-#pragma unroll 4
+#pragma unroll (kVUnroll)
                 for (int jj = 0; jj < kVNT; ++jj) {
                     VjpRec Pq;
                     Pq.ph = s_ph[jj]; Pq.pl = s_pl[jj]; Pq.v = s_v[jj]; Pq.ab = s_ab[jj]; Pq.kb = s_kb[jj];
-                    vjp_pair_ds<SOFT, false>(Pq, K, eps2, t);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) vjp_pair_ds<SOFT, false>(Pq, K[r], eps2, t[r]);
                 }
             }
 #pragma unroll
-            for (int c = 0; c < 7; ++c) two_sum_acc(hi[c], lo[c], t[c]);
-        }
-        if (kk < va.n) {
-            double r[7];
+            for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int c = 0; c < 7; ++c) r[c] = (double)hi[c] + (double)lo[c];
+                for (int c = 0; c < 7; ++c) two_sum_acc(hi[r][c], lo[r][c], t[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (kk[r] >= va.n) continue;
+            double res[7];
+#pragma unroll
+            for (int c = 0; c < 7; ++c) res[c] = (double)hi[r][c] + (double)lo[r][c];
             if (P.S == 1) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    va.xbar[3 * (long long)k + c] = r[c];
-                    va.vbar[3 * (long long)k + c] = r[3 + c];
+                    va.xbar[3 * (long long)k[r] + c] = res[c];
+                    va.vbar[3 * (long long)k[r] + c] = res[3 + c];
                 }
-                va.mbar[k] = r[6];
+                va.mbar[k[r]] = res[6];
             } else {
 #pragma unroll
-                for (int c = 0; c < 7; ++c) va.part[((long long)sl * 7 + c) * va.n + k] = r[c];
+                for (int c = 0; c < 7; ++c) va.part[((long long)sl * 7 + c) * va.n + k[r]] = res[c];
             }
         }
     }
@@ -385,7 +410,9 @@ int vjp_tile() { return kVNT; }
 int launch_force_vjp(const VjpArgs &va_in, int precision, bool softened, cudaStream_t st)
 {
     VjpArgs va = va_in;
-    va.plan = plan_ipar(va.n, va.n, kVNT, kVNT, va.slots, 0, va.part_cap);   // once, on the host
+    // once, on the host; the DS kernel owns kVKR particles per thread
+    va.plan = plan_ipar(va.n, va.n, kVNT * (precision == NB_FP64 ? 1 : kVKR), kVNT, va.slots, 0,
+                        va.part_cap);
     const Plan P = va.plan;
     const int g = P.items < va.slots ? P.items : va.slots;
     if (precision == NB_FP64) {
