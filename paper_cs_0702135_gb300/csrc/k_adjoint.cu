@@ -17,10 +17,10 @@
 //   A = m_k abar_p - m_p abar_k,   K = m_k kbar_p - m_p kbar_k:
 //   xbar_k += G(A, K),   vbar_k += H(K),
 //   mbar_k += -(abar_p.d + kbar_p.w)/r^3 + 3 s (kbar_p.d)/r^5,
-// with d = x_p - x_k.  One k-parallel sweep, no atomics; each thread owns one
-// k and streams the partners through shared memory in tiles, like the
-// forward i-parallel kernel (double-single positions, FP32 pair arithmetic,
-// TwoSum-promoted tile partials).
+// with d = x_p - x_k.  One k-parallel sweep, no atomics; each thread owns
+// kVKR particles k (one in the FP64 twin) and streams the partners through
+// shared memory in tiles, like the forward i-parallel kernel (double-single
+// positions, FP32 pair arithmetic, TwoSum-promoted tile partials).
 #include "nb_device.cuh"
 
 namespace nbk {
