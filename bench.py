@@ -579,7 +579,7 @@ def oracle_blockstep_rate(m, x, v, eps, level_min, t_end, gpu, budget_s):
     t_end_ticks = int(round(t_end * oracle.TICKS_PER_UNIT))
     steps, inter, done = 0, 0, False
     t0 = time.perf_counter()
-    while time.perf_counter() - t0 < budget_s:
+    while True:                       # at least one step, then until the budget is spent
         tn, act = orc.step(t_end_ticks)
         if len(act) == 0 or tn > t_end_ticks:
             done = True
@@ -588,6 +588,8 @@ def oracle_blockstep_rate(m, x, v, eps, level_min, t_end, gpu, budget_s):
         inter += len(act) * (n - 1)
         if tn == t_end_ticks and int(orc.t.min()) == t_end_ticks:
             done = True
+            break
+        if time.perf_counter() - t0 >= budget_s:
             break
     el = time.perf_counter() - t0
     rate = inter / el if el > 0 else 0.0

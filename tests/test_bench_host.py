@@ -1,0 +1,64 @@
+"""Host-side logic of bench.py that needs no GPU: the reference arm (the
+oracle timed on the host cores) and its JSON line, the DRAM-traffic lookup in
+the committed ncu summary (returned only while the kernel's sources are the
+ones that were profiled), the measured HBM peak, and the oracle integrator
+baseline of the block-step workload.
+"""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from synth import plummer  # noqa: E402
+
+
+def test_reference_arm_prints_the_contract_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--n", "4096", "--steps", "2", "--warmup", "1"],
+                         capture_output=True, text=True, check=True, timeout=600).stdout
+    line = json.loads(out.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["e2e"]["value"] == line["value"] and line["e2e"]["unit"] == line["unit"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+
+
+def test_traffic_is_reported_only_for_the_profiled_sources(monkeypatch):
+    full = bench.force_traffic_per_launch(1 << 20)
+    if full is None:
+        pytest.skip("the force kernel changed since its ncu summary was taken")
+    # O(N) traffic scales linearly with the launch size
+    assert bench.force_traffic_per_launch(1 << 19) == pytest.approx(full / 2)
+    monkeypatch.setattr(bench, "force_sources_sha256", lambda sources=None: "0" * 64)
+    assert bench.force_traffic_per_launch(1 << 20) is None
+
+
+def test_measured_hbm_peak(tmp_path, monkeypatch):
+    peak = bench.hbm_peak_gbs()
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            assert peak == pytest.approx(float(json.load(f)["hbm_gbs"]))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))      # no measured file there
+    assert bench.hbm_peak_gbs() == bench.HBM_GBS_FALLBACK
+
+
+def test_oracle_blockstep_baseline_whole_run_and_projection():
+    m, x, v = plummer(128, 2)
+    gpu = {"interactions": 10 ** 9, "steps": 100, "interactions_per_s": 1e11}
+    whole = bench.oracle_blockstep_rate(m, x, v, 1.0 / 256, 3, 0.125, gpu, 30.0)
+    assert whole["whole_run"] and whole["steps"] > 0 and whole["value"] > 0
+    assert whole["kind"] == "oracle" and "projected_whole_run_s" not in whole
+    part = bench.oracle_blockstep_rate(m, x, v, 1.0 / 256, 3, 0.125, gpu, 0.0)   # one step
+    assert not part["whole_run"] and part["steps"] == 1
+    assert part["projected_whole_run_s"] == pytest.approx(gpu["interactions"] / part["value"])
