@@ -59,6 +59,12 @@ def test_oracle_blockstep_baseline_whole_run_and_projection():
     whole = bench.oracle_blockstep_rate(m, x, v, 1.0 / 256, 3, 0.125, gpu, 30.0)
     assert whole["whole_run"] and whole["steps"] > 0 and whole["value"] > 0
     assert whole["kind"] == "oracle" and "projected_whole_run_s" not in whole
-    part = bench.oracle_blockstep_rate(m, x, v, 1.0 / 256, 3, 0.125, gpu, 0.0)   # one step
-    assert not part["whole_run"] and part["steps"] == 1
+    # a budget far below the run: at least one step, then the projection
+    part = bench.oracle_blockstep_rate(m, x, v, 1.0 / 256, 3, 0.125, gpu, 1e-4)
+    assert not part["whole_run"] and 1 <= part["steps"] < whole["steps"]
     assert part["projected_whole_run_s"] == pytest.approx(gpu["interactions"] / part["value"])
+    # a system whose integrator start-up alone exceeds the budget: the
+    # oracle's force on a sample instead
+    m2, x2, v2 = plummer(2048, 3)
+    samp = bench.oracle_blockstep_rate(m2, x2, v2, 1.0 / 256, 3, 0.125, gpu, 1e-3)
+    assert not samp["whole_run"] and "steps" not in samp and samp["value"] > 0
