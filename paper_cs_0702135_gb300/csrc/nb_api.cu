@@ -214,9 +214,11 @@ ForceOut res_out(nb_ctx *c)
     return o;
 }
 
-// Enqueues the force on `act`.  With na_dev the block size is read on the
-// device and both kernels are launched with persistent grids; otherwise only
-// the kernel that serves na_host is launched, sized to its work.
+// Enqueues the force on `act`.  With na_dev the block size and the plan are
+// read on the device (the scheduler wrote them): every force kernel of the
+// precision is launched with a persistent grid and all but the one serving the
+// block exit at once.  Otherwise the host plans, and only the kernel that
+// serves na_host is launched, sized to its work.
 void enqueue_force(nb_ctx *c, const int *act, int na_host, const int *na_dev, ForceOut out)
 {
     const ForceArgs fa = force_args(c, act, na_host, na_dev, out);
