@@ -170,7 +170,7 @@ def test_host_argument_errors(nb):
         nb.nb_free(ctx)
 
 
-@pytest.mark.parametrize("na", [1, 2, 3, 32, 256, 4096])
+@pytest.mark.parametrize("na", [1, 2, 3, 32, 96, 97, 256, 300, 577, 4096])
 def test_full_size_sampled(nb, na):
     # N = 2^20, eps = 1/1024: the benchmark's sweep configuration; 64 of the
     # active particles are checked one by one against the oracle.
