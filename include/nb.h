@@ -393,11 +393,15 @@ int nb_get_stats(nb_ctx *ctx, nb_stats *stats, int reset);
  * CUDA graph.  All calls share the array and each call writes every part of it
  * that it reads, so nothing carries over from one call to the next; but calls
  * whose GPU work overlaps (on two streams at once, or from two host threads)
- * race on it and must be serialised by the caller.
+ * race on it and must be serialised by the caller.  The looked-up address is
+ * kept for the life of the process: after cudaDeviceReset on a device, do not
+ * call this entry point again in that process (the address may be stale).
  *
  * Errors: NB_EINVAL (n < 1 or n > 2^31 - 1, n_active outside
  * [0, NB_NOALLOC_MAX_ACTIVE], eps negative or not finite, a NULL input),
- * NB_ECUDA (the address lookup or a launch failed).
+ * NB_ECUDA (a CUDA error was already pending when the call began -- it is
+ * left pending and nothing is launched -- or the address lookup or a launch
+ * failed).
  */
 int nb_force_few_noalloc(int64_t n, const double *d_m, const double *d_x, const double *d_v,
                          double eps, const int32_t *d_active_idx, int32_t n_active, double *d_acc,

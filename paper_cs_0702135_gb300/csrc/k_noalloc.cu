@@ -15,8 +15,10 @@
 // 256th j of the slice, positions are split into double-single form as they
 // are read, the CTA reduces with a warp-shuffle tree in double-single, and the
 // per-slice partial sums go to the scratch array; a second kernel sums the
-// slices in slice order.  Every partial is written before it is read in the
-// same call, so nothing in the scratch array needs clearing between calls.
+// slices in slice order.  Each thread adds its pair terms in FP32 runs of at
+// most eight and folds every run into double-single sums.  Every partial is
+// written before it is read in the same call, so nothing in the scratch array
+// needs clearing between calls.
 #include <climits>
 #include <cmath>
 #include <mutex>
@@ -30,6 +32,7 @@ constexpr int kNT = 256;                    // threads per CTA
 constexpr int kIC = 4;                      // active particles per CTA
 constexpr int kComp = 7;                    // acc xyz, jerk xyz, pot
 constexpr int kMaxSlices = 2048;            // j slices at most
+constexpr int kRun = 8;                     // FP32 pair terms per thread between promotions
 constexpr long long kScratchDoubles = (long long)kMaxSlices * kComp * NB_NOALLOC_MAX_ACTIVE;
 constexpr int kMaxDevices = 64;
 
@@ -123,21 +126,34 @@ __global__ void __launch_bounds__(kNT) k_few_partials(long long n, const double 
             ii[q] = i;
             ip[q] = load_point(m, x, v, i);
         }
+        // Plain FP32 runs of at most kRun pair terms per thread, each folded
+        // into the double-single sums (h, lo) by TwoSum, so the rounding error
+        // of a thread's sum does not grow with the slice length.
         float h[NV], lo[NV];
 #pragma unroll
         for (int e = 0; e < NV; ++e) h[e] = lo[e] = 0.0f;
-        for (long long j = j0 + tid; j < j1; j += kNT) {
-            const DSPoint jp = load_point(m, x, v, j);
+        for (long long jb = j0 + tid; jb < j1; jb += (long long)kNT * kRun) {
+            float t[NV];
 #pragma unroll
-            for (int q = 0; q < kIC; ++q) {
-                float a3[3] = {h[q * kComp], h[q * kComp + 1], h[q * kComp + 2]};
-                float k3[3] = {h[q * kComp + 3], h[q * kComp + 4], h[q * kComp + 5]};
-                float pp = h[q * kComp + 6];
-                pair(jp, ip[q], eps2, j == ii[q], a3, k3, pp);
-                h[q * kComp] = a3[0]; h[q * kComp + 1] = a3[1]; h[q * kComp + 2] = a3[2];
-                h[q * kComp + 3] = k3[0]; h[q * kComp + 4] = k3[1]; h[q * kComp + 5] = k3[2];
-                h[q * kComp + 6] = pp;
+            for (int e = 0; e < NV; ++e) t[e] = 0.0f;
+#pragma unroll 1
+            for (int u = 0; u < kRun; ++u) {
+                const long long j = jb + (long long)u * kNT;
+                if (j >= j1) break;
+                const DSPoint jp = load_point(m, x, v, j);
+#pragma unroll
+                for (int q = 0; q < kIC; ++q) {
+                    float a3[3] = {t[q * kComp], t[q * kComp + 1], t[q * kComp + 2]};
+                    float k3[3] = {t[q * kComp + 3], t[q * kComp + 4], t[q * kComp + 5]};
+                    float pp = t[q * kComp + 6];
+                    pair(jp, ip[q], eps2, j == ii[q], a3, k3, pp);
+                    t[q * kComp] = a3[0]; t[q * kComp + 1] = a3[1]; t[q * kComp + 2] = a3[2];
+                    t[q * kComp + 3] = k3[0]; t[q * kComp + 4] = k3[1]; t[q * kComp + 5] = k3[2];
+                    t[q * kComp + 6] = pp;
+                }
             }
+#pragma unroll
+            for (int e = 0; e < NV; ++e) ds_add(h[e], lo[e], t[e], 0.0f);
         }
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1)
@@ -228,6 +244,9 @@ extern "C" int nb_force_few_noalloc(int64_t n, const double *d_m, const double *
     if (!std::isfinite(eps) || eps < 0.0) return NB_EINVAL;
     if (n_active == 0) return NB_OK;
     if (!d_m || !d_x || !d_v || !d_active_idx) return NB_EINVAL;
+    // An error left pending by earlier work is not this call's: report it
+    // without launching and without clearing it.
+    if (cudaPeekAtLastError() != cudaSuccess) return NB_ECUDA;
     DeviceSetup s;
     const int rc = setup_current_device(&s);
     if (rc != NB_OK) return rc;
@@ -248,6 +267,7 @@ extern "C" int nb_force_few_noalloc(int64_t n, const double *d_m, const double *
     cudaStream_t st = (cudaStream_t)stream;
     k_few_partials<<<grid, kNT, 0, st>>>(n, d_m, d_x, d_v, (float)(eps * eps), d_active_idx,
                                          n_active, (int)S, jslice, s.scratch);
+    if (cudaGetLastError() != cudaSuccess) return NB_ECUDA;
     k_few_combine<<<(n_active * kComp + 255) / 256, 256, 0, st>>>(n_active, (int)S, s.scratch,
                                                                   d_acc, d_jerk, d_pot);
     return cudaGetLastError() == cudaSuccess ? NB_OK : NB_ECUDA;

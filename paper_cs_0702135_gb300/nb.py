@@ -130,6 +130,30 @@ def _dptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _dev(t, dtype, count, name, required=True):
+    """Device address of a torch CUDA tensor after checking that it is a
+    contiguous CUDA tensor of `dtype` ("float64" or "int32") holding at least
+    `count` elements, so the C side never reads or writes past its end.  An int
+    is taken as a raw device address that the caller vouches for; None is a
+    null pointer (a ValueError when the argument is required)."""
+    if t is None:
+        if required:
+            raise ValueError("%s is required" % name)
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    dt = str(getattr(t, "dtype", type(t).__name__)).replace("torch.", "")
+    if dt != dtype:
+        raise ValueError("%s must be a %s tensor, got %s" % (name, dtype, dt))
+    if not getattr(t, "is_cuda", False):
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if t.numel() < count:
+        raise ValueError("%s holds %d elements, %d needed" % (name, t.numel(), count))
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _f64(a, shape=None):
     a = np.ascontiguousarray(a, dtype=np.float64)
     if shape is not None and a.shape != shape:
@@ -190,8 +214,11 @@ def nb_force_into(ctx, active_idx, acc, jerk, pot):
 
 def nb_force_dev(ctx, d_active_idx, n_active, d_acc=None, d_jerk=None, d_pot=None):
     """Device-pointer variant: torch CUDA tensors (int32 indices, float64 outputs)."""
-    _check(ctx, lib().nb_force_dev(ctx, _dptr(d_active_idx), int(n_active), _dptr(d_acc),
-                                   _dptr(d_jerk), _dptr(d_pot)))
+    na = max(int(n_active), 0)
+    _check(ctx, lib().nb_force_dev(ctx, _dev(d_active_idx, "int32", na, "d_active_idx", na > 0),
+                                   int(n_active), _dev(d_acc, "float64", 3 * na, "d_acc", False),
+                                   _dev(d_jerk, "float64", 3 * na, "d_jerk", False),
+                                   _dev(d_pot, "float64", na, "d_pot", False)))
 
 
 def nb_correct(ctx, active_idx, t, acc=None, jerk=None):
@@ -302,9 +329,15 @@ def nb_force_few_noalloc(n, d_m, d_x, d_v, eps, d_active_idx, n_active, d_acc=No
     """Context-free force on at most NB_NOALLOC_MAX_ACTIVE particles from device
     arrays (torch CUDA tensors or addresses), for callers that may not allocate
     device memory; enqueued on `stream` (an int cudaStream_t, None = default)."""
-    rc = lib().nb_force_few_noalloc(int(n), _dptr(d_m), _dptr(d_x), _dptr(d_v), float(eps),
-                                    _dptr(d_active_idx), int(n_active), _dptr(d_acc), _dptr(d_jerk),
-                                    _dptr(d_pot), None if not stream else ctypes.c_void_p(stream))
+    n, na = int(n), int(n_active)
+    nn, nk = max(n, 0), max(na, 0)
+    args = (_dev(d_m, "float64", nn, "d_m"), _dev(d_x, "float64", 3 * nn, "d_x"),
+            _dev(d_v, "float64", 3 * nn, "d_v"), float(eps),
+            _dev(d_active_idx, "int32", nk, "d_active_idx"), na,
+            _dev(d_acc, "float64", 3 * nk, "d_acc", False),
+            _dev(d_jerk, "float64", 3 * nk, "d_jerk", False),
+            _dev(d_pot, "float64", nk, "d_pot", False))
+    rc = lib().nb_force_few_noalloc(n, *args, None if not stream else ctypes.c_void_p(stream))
     if rc != NB_OK:
         raise NbError(rc, "nb_force_few_noalloc rejected n=%d n_active=%d eps=%r (limit %d)"
                       % (n, n_active, eps, NB_NOALLOC_MAX_ACTIVE))

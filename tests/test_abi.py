@@ -121,3 +121,28 @@ def test_default_opts_rejects_unknown_fields(built):
     import paper_cs_0702135_gb300 as nb
     with pytest.raises(TypeError):
         nb.nb_default_opts(sumation=1)
+
+
+def test_device_wrappers_check_tensors_before_the_call():
+    # The device-pointer wrappers refuse tensors of the wrong dtype, on the
+    # host, non-contiguous or too short before anything reaches the library
+    # (a float32 position array would otherwise be read past its end, an
+    # int64 index array as pairs of int32).
+    torch = pytest.importorskip("torch")
+    import paper_cs_0702135_gb300 as nb
+    n = 10
+    raw = 1 << 20               # an int is a raw device address: not inspected
+    x = torch.zeros((n, 3), dtype=torch.float64)
+    idx = torch.zeros(3, dtype=torch.int32)
+    cases = [(raw, x.float(), raw, "d_x must be a float64"),
+             (raw, raw, idx.long(), "d_active_idx must be a int32"),
+             (raw, x, raw, "d_x must be a CUDA"),
+             (raw, raw, idx, "d_active_idx must be a CUDA")]
+    for dm, dx, di, what in cases:
+        with pytest.raises(ValueError, match=what):
+            nb.nb_force_few_noalloc(n, dm, dx, raw, 0.1, di, 3, raw)
+    with pytest.raises(ValueError, match="d_active_idx must be a int32"):
+        nb.nb_force_dev(None, idx.long(), 3, raw)
+    assert nb.nb._dev(raw, "float64", 3, "d_x").value == raw
+    with pytest.raises(ValueError, match="required"):
+        nb.nb._dev(None, "float64", 3, "d_x")
