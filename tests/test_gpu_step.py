@@ -86,27 +86,58 @@ def _level_from_forces(before, i, tn, a_new, k_new, eta=0.01, kmin=3):
     return oracle.next_level(int(before["lev"][i]), kq, tn, kmin), raw
 
 
+# Block steps of the DS path that must match the oracle bit for bit (block time,
+# block and every level) before the first level differs.  The kernels sum in a
+# fixed order, so the count is the same on every run: on the GB300 the first
+# level differs at step 6 (particle 923), and over the 64 steps 4 of the
+# levels set differ (steps 6, 10, 18, 38), each a borderline case.
+DS_EXACT_STEPS_FLOOR = 6
+# Levels the DS path may set differently from the oracle over the 64 steps
+# (each one checked to be a borderline case of the oracle's own rules).
+DS_EXEMPT_MAX = 8
+
+
+def _exempt_startup(st, it, i):
+    """Checks that the GPU's start-up level of particle i is the one the
+    oracle's initial-step rule gives for the GPU's start-up forces, and that the
+    two raw initial steps lie on opposite sides of a power of two."""
+    raw_g = oracle.initial_dt(st["a"][i], st["k"][i], 0.01)
+    raw_o = oracle.initial_dt(it.a[i], it.k[i], 0.01)
+    rc, want = oracle.level_of(raw_g, 3)
+    assert rc == 0 and st["level"][i] == want, ("start-up", i)
+    assert math.floor(math.log2(raw_g)) != math.floor(math.log2(raw_o)), ("start-up", i)
+
+
 @pytest.mark.parametrize("precision", [1, 0])
 def test_first_64_steps_active_sets(nb, precision):
     # Config: Plummer N = 1024, eps = 1/256, eta = 0.01.  The FP64 GPU path must
     # pick the same block time, block and levels as the oracle for 64 steps.
-    # The DS path too, until a level differs; a differing level must then be
-    # exactly the level that the oracle's own corrector and criterion give for
-    # the DS forces (the step criterion works on a2, a3, differences of forces
-    # across the step, which magnify the 1e-7 FP32 force error by orders of
-    # magnitude), and from there on the runs are compared statistically
-    # (energy, block counts) by the other tests.
+    # The DS path forms its forces in FP32 pair arithmetic, and the step
+    # criterion works on a2, a3 (differences of forces across the step), which
+    # magnify the 1e-7 force error by orders of magnitude: a level may then
+    # differ.  Every such level must be exactly the one that the oracle's own
+    # initial-step rule (start-up) or corrector and criterion (block steps) give
+    # for the DS forces from the GPU's state, with the oracle's and the GPU's
+    # raw steps on opposite sides of a power of two.  The oracle then takes
+    # that level (its positions, velocities and forces stay its own), so every
+    # one of the 64 block times and blocks is still compared bit for bit; the
+    # steps before the first differing level are counted and bounded below.
     m, x, v = plummer(1024, 1)
     it = oracle.Integrator(m, x, v, EPS)
     ctx = nb.nb_init(m, x, v, EPS, nb.nb_default_opts(precision=precision))
+    exempt = []
+    exact_steps = None
+    levels_set = 0
     try:
         st = nb.nb_get_state(ctx)
-        if precision == 1:
-            assert np.array_equal(st["level"], it.lev)
-        else:
-            assert np.mean(st["level"] == it.lev) > 0.99
-            if not np.array_equal(st["level"], it.lev):
-                return
+        diff = np.nonzero(st["level"] != it.lev)[0]
+        assert precision == 0 or diff.size == 0, ("FP64 start-up levels differ", diff)
+        for i in diff:
+            _exempt_startup(st, it, i)
+            it.lev[i] = st["level"][i]
+            exempt.append((-1, int(i)))
+        if diff.size:
+            exact_steps = 0
         for step in range(64):
             before = dict(x=it.x.copy(), v=it.v.copy(), a=it.a.copy(), k=it.k.copy(), t=it.t.copy(),
                           lev=it.lev.copy())
@@ -117,9 +148,13 @@ def test_first_64_steps_active_sets(nb, precision):
             gact, tt = nb.nb_get_active(ctx)
             assert tt == tn and np.array_equal(gact, act), step
             g = nb.nb_get_state(ctx)
+            assert np.array_equal(g["t"], it.t), step
+            levels_set += len(act)
             diff = np.nonzero(g["level"] != it.lev)[0]
             if diff.size:
                 assert precision == 0, ("FP64 levels differ", step, diff)
+                if exact_steps is None:
+                    exact_steps = step
                 for i in diff:
                     want, raw_g = _level_from_forces(g_before, i, tn, g["a"][i], g["k"][i])
                     _, raw_o = _level_from_forces(before, i, tn, it.a[i], it.k[i])
@@ -127,9 +162,20 @@ def test_first_64_steps_active_sets(nb, precision):
                     # the two raw steps straddle a power of two
                     assert math.floor(math.log2(raw_g)) != math.floor(math.log2(raw_o)), (step, i)
                     assert np.linalg.norm(g["a"][i] - it.a[i]) <= 2e-6 * np.linalg.norm(it.a[i]) * 10
-                return
+                    it.lev[i] = g["level"][i]
+                    exempt.append((step, int(i)))
     finally:
         nb.nb_free(ctx)
+    if exact_steps is None:
+        exact_steps = 64
+    print("precision %d: %d of 64 block steps bit-exact before the first differing level; all 64 "
+          "block times and blocks equal; %d of %d levels set equal, %d exempted %s"
+          % (precision, exact_steps, levels_set - len(exempt), levels_set, len(exempt), exempt))
+    if precision == 1:
+        assert exact_steps == 64 and not exempt
+    else:
+        assert exact_steps >= DS_EXACT_STEPS_FLOOR, exact_steps
+        assert len(exempt) <= DS_EXEMPT_MAX, exempt
 
 
 @pytest.mark.parametrize("precision", [0, 1])
