@@ -46,6 +46,7 @@ SEED = 3
 LEVEL = 10                         # shared step 2^-10
 SWEEP_LADDER = [1, 256, 4096, 65536]
 FP64_SAMPLE = 4096
+ACCURACY_SAMPLE_FULL = 128         # sampled i of the headline accuracy check
 L2_FLUSH_BYTES = 256 << 20
 FP32_LANES_PER_SM = 128
 MAX_SM_MHZ_FALLBACK = 2070.0
@@ -62,6 +63,8 @@ def parse_args():
     p.add_argument("--impl", default="mine", choices=["mine", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT)
     p.add_argument("--no-extras", action="store_true", help="skip ladder, FP64 arm, e2e, CPU baseline")
+    p.add_argument("--configs", default="1,2,3,4,5",
+                   help="default workload: the configurations run after the headline (empty: none)")
     p.add_argument("--workload", default="full_active_step",
                    choices=["full_active_step", "blockstep", "adjoint", "ensemble", "replay", "summation",
                             "sweep"],
@@ -75,6 +78,8 @@ def parse_args():
     p.add_argument("--n-max", type=int, default=524288, help="replay: largest N of the ladder")
     p.add_argument("--baseline-sample", type=int, default=32,
                    help="ensemble: clusters timed one by one through the single-system path")
+    p.add_argument("--oracle-outliers", type=int, default=0,
+                   help="ensemble: re-run this many worst clusters (<= 512 bodies) with the oracle")
     p.add_argument("--oracle-n", type=int, default=1024, help="adjoint: size of the CPU FP64 comparison")
     p.add_argument("--cpu-budget", type=float, default=20.0,
                    help="blockstep: seconds of the oracle's integrator timed beside the GPU run")
@@ -344,6 +349,8 @@ def run_mine(args):
     extras = {}
     if not args.no_extras and rank == 0:
         extras = run_extras(args, nb, ctx, m, x, v, stream, dev, torch, sample_active)
+        if world == 1 and args.configs:
+            extras["configs"] = run_configs(args, nb, torch, stream)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -435,7 +442,26 @@ def run_extras(args, nb, ctx, m, x, v, stream, dev, torch, sample_active):
     for _ in range(3):
         c64.nb_force_dev(idx, na, acc, None, None)
     st = c64.nb_get_stats(reset=True)
+    c64.nb_set_profiling(False)
+    # Accuracy of both GPU forms against the FP64 oracle on sampled particles
+    # of the initial state (per-particle metric of the parity tests).
+    import oracle
+    ia = sample_active(n, min(ACCURACY_SAMPLE_FULL, n), SEED + 29)
+    ref = oracle.force(m, x, v, EPS, ia, nthreads=os.cpu_count() or 1)
+    sa, sk = pair_magnitude_sums(m, x, v, EPS, ia, chunk=8)
+    cds = nb.Context(m, x, v, EPS, flags=nb.NB_INIT_NO_FORCE, stream=stream.cuda_stream)
+    acc_rows = {}
+    for name, c in (("ds", cds), ("fp64_gpu", c64)):
+        e = force_error_stats(c.nb_force(ia), ref, sa, sk)
+        acc_rows[name] = {"max_err_acc": e[0], "max_err_jerk": e[1], "max_err_pot": e[2],
+                          "p99_raw_rel_acc": e[3]}
+    cds.nb_free()
     c64.nb_free()
+    acc_rows["sample"] = ("%d i drawn uniformly (seed %d) against all %d j at t = 0; err = |d| / "
+                          "max(|ref|, S/10), S the sum of pair magnitudes (pot: relative)"
+                          % (len(ia), SEED + 29, n))
+    acc_rows["tolerance"] = {"acc": 2e-6, "jerk": 1e-5, "pot": 2e-6}
+    out["accuracy_vs_oracle"] = acc_rows
     fs64 = st["force_ms"] / 1e3 / max(1, st["force_launches"])
     r64 = na * (n - 1) / fs64
     rds = ladder[str(na)]["interactions_per_s"] if str(na) in ladder else None
@@ -450,6 +476,54 @@ def run_extras(args, nb, ctx, m, x, v, stream, dev, torch, sample_active):
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "sample": "oracle direct-sum force (FP64, OpenMP) on %d of the %d "
                                          "active i against all j, %.1f s" % (na_s, n, secs)}
+    return out
+
+
+CONFIG_NAMES = {
+    1: "plummer_N1024_eps1/256_t0-1_blockstep",
+    2: "plummer_N65536_eps1/256_t0-0.25_blockstep",
+    3: "plummer_N1048576_eps1/1024_t0-1/16_blockstep",
+    4: "adjoint_plummer_N16384_eps1/256_dt1/1024_steps256_ckpt16",
+    5: "ensemble_4096_plummer_salpeter_N32-4096_eps1/256_t1",
+}
+
+
+def run_configs(args, nb, torch, stream):
+    """Every workload configuration of the benchmark suite, each with its own
+    clock (wall seconds of the entry), after the headline measurement:
+    1. N = 1024 to t = 1, DS and FP64 GPU, the oracle's whole run beside it;
+    2. N = 65536 to t = 1/4, DS and FP64 GPU, block-size histogram, sampled
+       force errors against the oracle at 16 checkpoints, energies against the
+       oracle's pair sums;
+    3. N = 2^20 (eps = 1/1024) to t = 1/16, DS;
+    4. the differentiable run (adjoint, FD and oracle checks);
+    5. the batched ensemble of 4096 clusters, its worst clusters re-run by the
+       oracle."""
+    out = {}
+    want = sorted({int(c) for c in args.configs.split(",") if c.strip()})
+    for c in want:
+        t0 = time.perf_counter()
+        if c == 1:
+            r = blockstep_config(nb, torch, stream, 1024, 1, 1.0 / 256, 1.0, [nb.NB_DS, nb.NB_FP64],
+                                 cpu_budget=20.0, energy_vs_oracle=True)
+        elif c == 2:
+            r = blockstep_config(nb, torch, stream, 65536, 2, 1.0 / 256, 0.25, [nb.NB_DS, nb.NB_FP64],
+                                 sample_errors=1024, cpu_budget=10.0, energy_vs_oracle=True)
+        elif c == 3:
+            r = blockstep_config(nb, torch, stream, 1 << 20, 3, 1.0 / 1024, 1.0 / 16, [nb.NB_DS],
+                                 block_sizes=False, cpu_budget=10.0)
+            ds = r["ds"]
+            peak = fp32_peak_tflops(torch.cuda.get_device_properties(0).multi_processor_count,
+                                    MAX_SM_MHZ_FALLBACK)
+            ds["pct_fp32_peak"] = 100.0 * ds["gflops"] / 1e3 / peak
+        elif c == 4:
+            r = adjoint_config(nb, torch, 16384, 32, 1024)
+        elif c == 5:
+            r = ensemble_config(nb, torch, 4096, 32, oracle_outliers=5, oracle_n_max=512)
+        else:
+            continue
+        r["wall_s"] = time.perf_counter() - t0
+        out["%d_%s" % (c, CONFIG_NAMES[c])] = r
     return out
 
 
@@ -478,27 +552,22 @@ def e2e_host_api(ctx, nb, n, k_e2e, torch, dev):
             "steps": k_e2e, "api": "nb_predict + nb_force (host arrays) + nb_correct"}
 
 
-def run_blockstep(args):
+def blockstep_config(nb, torch, stream, n, seed, eps, t_end, precisions, block_sizes=True,
+                     sample_errors=0, cpu_budget=20.0, energy_vs_oracle=False):
     """A Plummer run with individual block steps on the device (nb_run, graph
-    replay): interactions/s over the whole run, |dE/E|, the block-size
-    distribution (from a step-by-step replay of the same run), DS and FP64."""
-    import torch
-    import paper_cs_0702135_gb300 as nb
-    from synth import plummer, sample_active
-    n = args.n
-    eps = args.eps if args.eps is not None else 1.0 / 256
-    seed = args.seed if args.seed is not None else 2
+    replay or the persistent launch): interactions/s over the whole run,
+    |dE/E|, and for the DS path the block-size distribution (from a
+    step-by-step replay of the same run) and, with sample_errors > 0, the
+    force on that many sampled particles at 16 checkpoints against the FP64
+    oracle.  Beside it the oracle's own integrator on the host cores."""
+    from synth import plummer
     level_min = 3
-    while (2.0 ** -level_min) > args.t_end or (args.t_end / 2.0 ** -level_min) % 1:
+    while (2.0 ** -level_min) > t_end or (t_end / 2.0 ** -level_min) % 1:
         level_min += 1
-    torch.cuda.set_device(0)
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
     m, x, v = plummer(n, seed)
-    precs = {"ds": [nb.NB_DS], "fp64": [nb.NB_FP64], "both": [nb.NB_DS, nb.NB_FP64]}[args.precision]
-    out = {"workload": "blockstep_plummer_N%d_eps%g_t%g" % (n, eps, args.t_end), "N": n, "eps": eps,
-           "seed": seed, "t_end": args.t_end, "level_min": level_min, "eta": 0.01}
-    for prec in precs:
+    out = {"workload": "blockstep_plummer_N%d_eps%g_t%g" % (n, eps, t_end), "N": n, "eps": eps,
+           "seed": seed, "t_end": t_end, "level_min": level_min, "eta": 0.01}
+    for prec in precisions:
         name = "ds" if prec == nb.NB_DS else "fp64"
         ctx = nb.Context(m, x, v, eps, precision=prec, level_min=level_min, stream=stream.cuda_stream)
         e0 = sum(ctx.nb_energy())
@@ -506,23 +575,33 @@ def run_blockstep(args):
         ctx.nb_get_stats(reset=True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        steps, inter = ctx.nb_run(args.t_end)
+        steps, inter = ctx.nb_run(t_end)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         launches = ctx.nb_get_stats(reset=True)["kernel_launches"]
         e1 = sum(ctx.nb_energy())
         res = {"steps": steps, "interactions": inter, "seconds": el, "interactions_per_s": inter / el,
                "gflops": 60 * inter / el / 1e9, "us_per_step": 1e6 * el / max(1, steps),
+               "energy_t0": e0, "energy_t_end": e1,
                "energy_rel_err": abs(e1 - e0) / abs(e0), "kernel_launches": launches}
-        if prec == nb.NB_DS:
+        if energy_vs_oracle:
+            # the GPU's energy (a full force sweep in the context's precision)
+            # against the oracle's FP64 pair sum of the same state
+            import oracle
+            thr = os.cpu_count() or 1
+            sT = ctx.nb_get_state()
+            o0 = sum(oracle.energy(m, st0["x"], st0["v"], eps, thr))
+            o1 = sum(oracle.energy(m, sT["x"], sT["v"], eps, thr))
+            res["energy_vs_oracle_rel"] = {"t0": abs(e0 - o0) / abs(o0), "t_end": abs(e1 - o1) / abs(o1)}
+        if prec == nb.NB_DS and (block_sizes or sample_errors):
             # replay the same run step by step for the block sizes (and sampled errors)
             ctx.nb_set_state(st0["x"], st0["v"], st0["a"], st0["k"], st0["t"], st0["level"])
             sizes = []
-            checks = set(np.linspace(0, steps - 1, 16).astype(int).tolist()) if args.sample_errors else set()
+            checks = set(np.linspace(0, steps - 1, 16).astype(int).tolist()) if sample_errors else set()
             errs = []
             for s_ in range(steps):
                 if s_ in checks:
-                    errs.append(sampled_force_errors(ctx, nb, m, eps, args.sample_errors, seed + s_))
+                    errs.append(sampled_force_errors(ctx, nb, m, eps, sample_errors, seed + s_))
                 tb, na = ctx.nb_step()
                 sizes.append(na)
             sizes = np.array(sizes)
@@ -533,20 +612,38 @@ def run_blockstep(args):
                                "max": int(sizes.max()), "min": int(sizes.min()),
                                "hist_log2_bins": {str(e): int(h) for e, h in zip(edges, hist) if h},
                                "paper_fit_n_block": 0.20 * n ** 0.81,
-                               "paper_fit_steps": 247 * n ** 0.35 * args.t_end}
+                               "paper_fit_steps": 247 * n ** 0.35 * t_end}
             if errs:
-                res["sampled_errors"] = {"checkpoints": len(errs), "per_checkpoint_i": args.sample_errors,
-                                         "max_err_acc": max(e[0] for e in errs),
-                                         "max_err_jerk": max(e[1] for e in errs),
-                                         "max_err_pot": max(e[2] for e in errs),
-                                         "p99_raw_rel_acc": max(e[3] for e in errs)}
+                res["sampled_errors"] = {
+                    "checkpoints": len(errs), "per_checkpoint_i": sample_errors,
+                    "metric": "|d|/max(|ref|, S/10) per particle, S = sum of pair magnitudes; pot relative",
+                    "max_err_acc": max(e[0] for e in errs), "max_err_jerk": max(e[1] for e in errs),
+                    "max_err_pot": max(e[2] for e in errs), "p99_raw_rel_acc": max(e[3] for e in errs),
+                    "within_tolerance": bool(max(e[0] for e in errs) <= 2e-6
+                                             and max(e[1] for e in errs) <= 1e-5
+                                             and max(e[2] for e in errs) <= 2e-6)}
         out[name] = res
         ctx.nb_free()
     if "ds" in out and "fp64" in out:
         out["ds_over_fp64"] = out["ds"]["interactions_per_s"] / out["fp64"]["interactions_per_s"]
-    if not args.no_extras:
-        out["cpu_baseline"] = oracle_blockstep_rate(m, x, v, eps, level_min, args.t_end,
-                                                    out.get("ds", out.get("fp64")), args.cpu_budget)
+    if cpu_budget > 0:
+        out["cpu_baseline"] = oracle_blockstep_rate(m, x, v, eps, level_min, t_end,
+                                                    out.get("ds", out.get("fp64")), cpu_budget)
+    return out
+
+
+def run_blockstep(args):
+    import torch
+    import paper_cs_0702135_gb300 as nb
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    precs = {"ds": [nb.NB_DS], "fp64": [nb.NB_FP64], "both": [nb.NB_DS, nb.NB_FP64]}[args.precision]
+    out = blockstep_config(nb, torch, stream, args.n,
+                           args.seed if args.seed is not None else 2,
+                           args.eps if args.eps is not None else 1.0 / 256, args.t_end, precs,
+                           sample_errors=args.sample_errors,
+                           cpu_budget=0.0 if args.no_extras else args.cpu_budget)
     print(json.dumps(out), flush=True)
 
 
@@ -576,6 +673,7 @@ def oracle_blockstep_rate(m, x, v, eps, level_min, t_end, gpu, budget_s):
     t0 = time.perf_counter()
     orc = oracle.Integrator(m, x, v, eps, kmin=level_min, nthreads=threads)
     init_s = time.perf_counter() - t0
+    e0 = orc.energy() if n <= 16384 else None
     t_end_ticks = int(round(t_end * oracle.TICKS_PER_UNIT))
     steps, inter, done = 0, 0, False
     t0 = time.perf_counter()
@@ -598,6 +696,10 @@ def oracle_blockstep_rate(m, x, v, eps, level_min, t_end, gpu, budget_s):
     if done:
         res["sample"] = "the oracle's whole run (%d block steps, %.1f s after a %.1f s start-up sweep)" % (
             steps, el, init_s)
+        if e0 is not None:
+            res["energy_rel_err"] = abs(orc.energy() - e0) / abs(e0)
+        if gpu:
+            res["gpu_steps_over_oracle_steps"] = gpu["steps"] / max(1, steps)
     else:
         proj = gpu["interactions"] / rate if rate > 0 else None
         res["sample"] = ("the oracle's first %d block steps of the same run (%.1f s; the GPU run took "
@@ -609,6 +711,40 @@ def oracle_blockstep_rate(m, x, v, eps, level_min, t_end, gpu, budget_s):
     return res
 
 
+def pair_magnitude_sums(m, x, v, eps, idx, chunk=16):
+    """Per listed i: S_a = sum_j |m_j dx / r^3| and S_k = sum_j |jerk_ij| (j != i),
+    the scales of the per-particle force error metric; chunked over i."""
+    sa = np.empty(len(idx))
+    sk = np.empty(len(idx))
+    for s0 in range(0, len(idx), chunk):
+        ii = np.asarray(idx[s0:s0 + chunk])
+        d = x[None, :, :] - x[ii, None, :]
+        w = v[None, :, :] - v[ii, None, :]
+        r2 = np.einsum("ijk,ijk->ij", d, d) + eps * eps
+        rv = np.einsum("ijk,ijk->ij", d, w)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            r3 = r2 ** -1.5
+            fa = m[None, :] * np.sqrt(r2 - eps * eps) * r3
+            kk = m[None, :, None] * (w * r3[..., None] - 3 * (rv * r3 / r2)[..., None] * d)
+            fk = np.linalg.norm(kk, axis=2)
+        rows = np.arange(len(ii))
+        fa[rows, ii] = 0.0
+        fk[rows, ii] = 0.0
+        sa[s0:s0 + len(ii)] = np.nansum(fa, axis=1)
+        sk[s0:s0 + len(ii)] = np.nansum(fk, axis=1)
+    return sa, sk
+
+
+def force_error_stats(got, ref, sa, sk):
+    """(max err_a, max err_k, max err_pot, p99 raw |da|/|a|): err_a = |da| /
+    max(|a|, S_a/10), the same for the jerk; the potential's plain relative error."""
+    ea = np.linalg.norm(got[0] - ref[0], axis=1) / np.maximum(np.linalg.norm(ref[0], axis=1), sa / 10)
+    ek = np.linalg.norm(got[1] - ref[1], axis=1) / np.maximum(np.linalg.norm(ref[1], axis=1), sk / 10)
+    ep = np.abs(got[2] - ref[2]) / np.abs(ref[2])
+    raw = np.linalg.norm(got[0] - ref[0], axis=1) / np.linalg.norm(ref[0], axis=1)
+    return float(ea.max()), float(ek.max()), float(ep.max()), float(np.percentile(raw, 99))
+
+
 def sampled_force_errors(ctx, nb, m, eps, k, seed):
     """Force on k sampled particles at the current (synchronised-or-not) state,
     DS GPU vs the FP64 oracle on the same predicted positions."""
@@ -617,9 +753,7 @@ def sampled_force_errors(ctx, nb, m, eps, k, seed):
     st = ctx.nb_get_state()
     t_now = int(st["t"].max())
     n = m.shape[0]
-    # predict everything to the latest particle time with the oracle's predictor
-    xp = np.empty_like(st["x"])
-    vp = np.empty_like(st["v"])
+    # predict everything to the latest particle time (FP64, the predictor of Section 2)
     dt = (t_now - st["t"]) / float(1 << 40)
     h = dt / 2.0
     q = dt / 3.0
@@ -629,18 +763,8 @@ def sampled_force_errors(ctx, nb, m, eps, k, seed):
     ctx.nb_predict(t_now / float(1 << 40))
     got = ctx.nb_force(idx)
     ref = oracle.force(m, xp, vp, eps, idx, nthreads=os.cpu_count() or 1)
-    d = xp[None, :, :] - xp[idx, None, :]
-    r2 = np.einsum("ijk,ijk->ij", d, d) + eps * eps
-    sa = np.sum(m[None, :] * np.sqrt(r2 - eps * eps) / r2 ** 1.5, axis=1)
-    w = vp[None, :, :] - vp[idx, None, :]
-    rv = np.einsum("ijk,ijk->ij", d, w)
-    kk = m[None, :, None] * (w / r2[..., None] ** 1.5 - 3 * rv[..., None] * d / r2[..., None] ** 2.5)
-    sk = np.sum(np.linalg.norm(kk, axis=2), axis=1)
-    ea = np.linalg.norm(got[0] - ref[0], axis=1) / np.maximum(np.linalg.norm(ref[0], axis=1), sa / 10)
-    ek = np.linalg.norm(got[1] - ref[1], axis=1) / np.maximum(np.linalg.norm(ref[1], axis=1), sk / 10)
-    ep = np.abs(got[2] - ref[2]) / np.abs(ref[2])
-    raw = np.linalg.norm(got[0] - ref[0], axis=1) / np.linalg.norm(ref[0], axis=1)
-    return float(ea.max()), float(ek.max()), float(ep.max()), float(np.percentile(raw, 99))
+    sa, sk = pair_magnitude_sums(m, xp, vp, eps, idx)
+    return force_error_stats(got, ref, sa, sk)
 
 
 def run_adjoint(args):
@@ -653,10 +777,15 @@ def run_adjoint(args):
     sequential oracle finishes (stated)."""
     import torch
     import paper_cs_0702135_gb300 as nb
-    from synth import plummer
-    n = args.n if args.n != N_DEFAULT else 16384
-    eps, level, steps, ck = 1.0 / 256, 10, 256, 16
     torch.cuda.set_device(0)
+    out = adjoint_config(nb, torch, args.n if args.n != N_DEFAULT else 16384, args.fd_coords,
+                         args.oracle_n)
+    print(json.dumps(out), flush=True)
+
+
+def adjoint_config(nb, torch, n, fd_coords, oracle_n):
+    from synth import plummer
+    eps, level, steps, ck = 1.0 / 256, 10, 256, 16
     m, x, v = plummer(n, 4)
     tgt = plummer(n, 5)[1]
     out = {"workload": "adjoint_plummer_N%d_eps1/256_dt1/1024_steps%d_ckpt%d" % (n, steps, ck),
@@ -696,7 +825,8 @@ def run_adjoint(args):
     r = np.random.default_rng(7)
     h = 1e-6
     rows = []
-    for q in range(args.fd_coords):
+    t_fd = time.perf_counter()
+    for q in range(fd_coords):
         kind = ("x", "v", "m")[q % 3]
         i = int(r.integers(n))
         c3 = int(r.integers(3))
@@ -712,18 +842,18 @@ def run_adjoint(args):
             lm = run(nb.NB_FP64, xx, vv, mm, False); an_ds, an64 = gm[i], hm[i]
         fd = (lp - lm) / (2 * h)
         rows.append((kind, fd, an_ds, an64))
+    t_fd = time.perf_counter() - t_fd
     scale = max([abs(r_[1]) for r_ in rows] + [1e-300])
-    out["fd_check"] = {} if not rows else {"coords": len(rows), "h": h,
+    out["fd_check"] = {} if not rows else {"coords": len(rows), "h": h, "seconds": t_fd,
                        "max_abs_err_ds_over_max_fd": max(abs(r_[2] - r_[1]) for r_ in rows) / scale,
                        "max_abs_err_fp64_over_max_fd": max(abs(r_[3] - r_[1]) for r_ in rows) / scale,
                        "median_rel_err_ds": float(np.median([abs(r_[2] - r_[1]) / max(abs(r_[1]), 1e-30) for r_ in rows])),
                        "median_rel_err_fp64": float(np.median([abs(r_[3] - r_[1]) / max(abs(r_[1]), 1e-30) for r_ in rows]))}
     # CPU FP64 oracle adjoint at a smaller N (the oracle's pair loops are sequential)
-    if args.oracle_n <= 0:
-        print(json.dumps(out), flush=True)
-        return
+    if oracle_n <= 0:
+        return out
     import oracle
-    no = args.oracle_n
+    no = oracle_n
     mo, xo, vo = plummer(no, 4)
     to = plummer(no, 5)[1]
     t0 = time.perf_counter()
@@ -740,7 +870,7 @@ def run_adjoint(args):
                                 "ds_rel_err_x": float(np.linalg.norm(gxo - oxb) / np.linalg.norm(oxb)),
                                 "ds_rel_err_v": float(np.linalg.norm(gvo - ovb) / np.linalg.norm(ovb)),
                                 "ds_rel_err_m": float(np.linalg.norm(gmo - omb) / np.linalg.norm(omb))}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def run_ensemble(args):
@@ -753,11 +883,15 @@ def run_ensemble(args):
     clusters and scaled to all of them."""
     import torch
     import paper_cs_0702135_gb300 as nb
-    from synth import ensemble
     torch.cuda.set_device(0)
-    C = args.clusters
+    print(json.dumps(ensemble_config(nb, torch, args.clusters, args.baseline_sample,
+                                     oracle_outliers=args.oracle_outliers)), flush=True)
+
+
+def ensemble_config(nb, torch, C, baseline_sample, oracle_outliers=0, oracle_n_max=512):
+    from synth import ensemble
     t0 = time.perf_counter()
-    cl = ensemble(C, 5)
+    cl = ensemble(C, 5, workers=min(16, os.cpu_count() or 1))
     gen_s = time.perf_counter() - t0
     off = np.zeros(C + 1, dtype=np.int64)
     for c, (m, _, _) in enumerate(cl):
@@ -789,12 +923,13 @@ def run_ensemble(args):
            "energy_rel_err": {"median": float(np.median(dE)), "p90": float(np.percentile(dE, 90)),
                               "max": float(dE.max()), "frac_le_1e-6": float(np.mean(dE <= 1e-6))},
            "all_at_t_end": bool(np.all(st["t"] == (1 << 40)))}
+    if oracle_outliers > 0:
+        out["oracle_outliers"] = ensemble_outliers_vs_oracle(cl, dE, eps, oracle_outliers, oracle_n_max)
     # per-cluster launches: the single-system path, one cluster at a time
-    if args.baseline_sample <= 0:
-        print(json.dumps(out), flush=True)
-        return
+    if baseline_sample <= 0:
+        return out
     r = np.random.default_rng(55)
-    pick = np.sort(r.choice(C, size=min(args.baseline_sample, C), replace=False))
+    pick = np.sort(r.choice(C, size=min(baseline_sample, C), replace=False))
     tb, ib = 0.0, 0
     for c in pick:
         mc, xc, vc = cl[c]
@@ -811,7 +946,28 @@ def run_ensemble(args):
                                    "extrapolated_seconds": tb * C / len(pick),
                                    "clusters_per_s": len(pick) / tb,
                                    "ensemble_speedup_clusters_per_s": (C / el) / (len(pick) / tb)}
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def ensemble_outliers_vs_oracle(cl, dE, eps, k, n_max):
+    """The k clusters of at most n_max bodies with the largest GPU |dE/E|,
+    each integrated to t = 1 by the oracle's FP64 integrator on the host
+    cores: the oracle's own |dE/E| beside the GPU's."""
+    import oracle
+    thr = os.cpu_count() or 1
+    cand = [c for c in np.argsort(-dE) if cl[c][0].shape[0] <= n_max][:k]
+    rows = []
+    for c in cand:
+        m, x, v = cl[c]
+        t0 = time.perf_counter()
+        it = oracle.Integrator(m, x, v, 1.0 / 256, nthreads=thr)
+        e0 = it.energy()
+        steps, _, _ = it.run(1.0)
+        d_orc = abs(it.energy() - e0) / abs(e0)
+        rows.append({"cluster": int(c), "N": int(m.shape[0]), "m_max": float(m.max()),
+                     "gpu_rel_err": float(dE[c]), "oracle_rel_err": d_orc, "oracle_steps": steps,
+                     "oracle_seconds": time.perf_counter() - t0})
+    return rows
 
 
 # Wall-clock seconds for 0.25 N-body time units (t = 0.25 -> 0.5), equal-mass

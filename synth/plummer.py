@@ -169,21 +169,28 @@ def salpeter_masses(n: int, seed: int, stream_offset: int = 0, slope: float = -2
     return m / m.sum()
 
 
+def _ensemble_cluster(job):
+    nc, sub, q = job
+    m = salpeter_masses(nc, sub)
+    return plummer(nc, sub, masses=m, virial_ratio=q, exact_virial_max=1024, sample_pairs=200000)
+
+
 def ensemble(n_clusters: int, seed: int, n_lo: int = 32, n_hi: int = 4096,
-             q_lo: float = 0.3, q_hi: float = 0.7):
+             q_lo: float = 0.3, q_hi: float = 0.7, workers: int = 1):
     """Independent clusters: N log-uniform in [n_lo, n_hi], Salpeter masses,
     virial ratio uniform in [q_lo, q_hi].  Returns a list of (m, x, v).  Clusters
-    above 1024 bodies are scaled with W estimated from 2e5 sampled pairs."""
+    above 1024 bodies are scaled with W estimated from 2e5 sampled pairs.
+    Every cluster draws from its own counter-based streams, so ``workers`` > 1
+    (processes started by spawn) gives the same clusters."""
     c = np.arange(n_clusters, dtype=np.int64)
     un = rng.uniform(seed, _S_ENS_N, c)
     sizes = np.floor(np.exp(math.log(n_lo) + un * (math.log(n_hi + 1) - math.log(n_lo)))).astype(np.int64)
     sizes = np.clip(sizes, n_lo, n_hi)
     uq = rng.uniform(seed, _S_ENS_Q, c)
-    out = []
-    for ci in range(n_clusters):
-        nc = int(sizes[ci])
-        sub = (seed * 1000003 + ci) & 0x7FFFFFFFFFFFFFFF
-        m = salpeter_masses(nc, sub)
-        out.append(plummer(nc, sub, masses=m, virial_ratio=float(q_lo + uq[ci] * (q_hi - q_lo)),
-                           exact_virial_max=1024, sample_pairs=200000))
-    return out
+    jobs = [(int(sizes[ci]), (seed * 1000003 + ci) & 0x7FFFFFFFFFFFFFFF,
+             float(q_lo + uq[ci] * (q_hi - q_lo))) for ci in range(n_clusters)]
+    if workers > 1 and n_clusters > 1:
+        import multiprocessing
+        with multiprocessing.get_context("spawn").Pool(workers) as pool:
+            return pool.map(_ensemble_cluster, jobs, chunksize=max(1, n_clusters // (8 * workers)))
+    return [_ensemble_cluster(j) for j in jobs]

@@ -94,3 +94,14 @@ def test_salpeter_and_ensemble():
         assert 32 <= m.shape[0] <= 4096
         q = kinetic_energy(m, v) / -unsoftened_potential_energy(m, x)
         assert 0.3 - 1e-9 <= q <= 0.7 + 1e-9
+
+
+def test_ensemble_workers_give_the_same_clusters():
+    # clusters come from their own counter-based streams: a process pool
+    # (spawned) must reproduce the sequential generator bit for bit
+    seq = ensemble(12, 4, n_lo=32, n_hi=1500)
+    par = ensemble(12, 4, n_lo=32, n_hi=1500, workers=2)
+    assert len(seq) == len(par)
+    for a, b in zip(seq, par):
+        for p, q in zip(a, b):
+            assert np.array_equal(p, q)
