@@ -398,8 +398,11 @@ def time_sweeps(ctx, n, nas, dev, torch, sample_active, flush):
         times, launches = [], 0
         t0 = time.perf_counter()
         for _ in range(reps):
-            flush.zero_()
+            # (the stats reset synchronises: it goes first, so the flush is
+            # still running when the force is enqueued and no host gap falls
+            # between the CUDA events around the force kernels)
             ctx.nb_get_stats(reset=True)
+            flush.zero_()
             ctx.nb_force_dev(idx, na, acc, jerk, pot)
             st = ctx.nb_get_stats(reset=True)
             times.append(st["force_ms"] / 1e3 / max(1, st["force_launches"]))

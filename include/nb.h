@@ -121,6 +121,15 @@ int nb_init(nb_ctx **ctx, int64_t n, const double *m, const double *x, const dou
             double eps, const nb_opts *opts);
 
 /*
+ * nb_init with device arrays d_m[n], d_x[n][3], d_v[n][3] (FP64, owned by the
+ * caller, copied in on the context's stream: pass the stream that produced
+ * them in opts->stream, or synchronise first).  The finiteness and mass
+ * checks run on the device; a failure is NB_EINVAL.  Otherwise as nb_init.
+ */
+int nb_init_dev(nb_ctx **ctx, int64_t n, const double *d_m, const double *d_x, const double *d_v,
+                double eps, const nb_opts *opts);
+
+/*
  * Predicts every particle to time t (Section 2 predictor, FP64):
  *   x_p = x + (v + (dt/2)(a + (dt/3) k)) dt,  v_p = v + (a + (dt/2) k) dt,
  * with each particle's own dt = t - t_i, and stores the result in the force
@@ -151,8 +160,11 @@ int nb_force(nb_ctx *ctx, const int32_t *active_idx, int32_t n_active, double *a
 /*
  * As nb_force with device pointers: d_active_idx[n_active] int32, outputs
  * d_acc[n_active][3], d_jerk[n_active][3], d_pot[n_active] (any may be NULL).
- * Indices are validated on the device; a bad index makes this call return
- * NB_EINVAL after a synchronisation of the context's stream.
+ * Indices are validated on the device while the force runs (the force
+ * kernels clamp every index into [0, n), so a bad index only wastes work); the
+ * call then synchronises the context's stream once and returns NB_EINVAL for
+ * a bad or repeated index, leaving the outputs untouched.  On success the
+ * copies into the outputs are enqueued on the context's stream.
  */
 int nb_force_dev(nb_ctx *ctx, const int32_t *d_active_idx, int32_t n_active, double *d_acc,
                  double *d_jerk, double *d_pot);
@@ -226,6 +238,14 @@ int nb_get_state(nb_ctx *ctx, double *x, double *v, double *a, double *k, int64_
                  int32_t *level);
 
 /*
+ * nb_get_state into device arrays of the same layouts (any may be NULL),
+ * enqueued on the context's stream; the call does not wait for the copies.
+ * Errors: NB_ECUDA.
+ */
+int nb_get_state_dev(nb_ctx *ctx, double *d_x, double *d_v, double *d_a, double *d_k,
+                     int64_t *d_t_ticks, int32_t *d_level);
+
+/*
  * Restore: replaces the state with host arrays of the layouts above (all
  * required).  Levels must lie in [level_min, 40] and every t_ticks[i] must be
  * a non-negative multiple of 2^(40 - level[i]).  Resuming from a state saved
@@ -281,6 +301,14 @@ int nb_force_vjp(nb_ctx *ctx, const double *abar, const double *kbar, double *xb
 int nb_traj_forward(nb_ctx *ctx, int64_t steps, int64_t checkpoint_every);
 int nb_traj_backward(nb_ctx *ctx, const double *xbar_T, const double *vbar_T, double *xbar0,
                      double *vbar0, double *mbar);
+
+/*
+ * nb_traj_backward with device arrays for the cotangents and the gradients
+ * (layouts as above; the cotangents' finiteness is checked on the device).
+ * Returns after the gradients are written.  Errors as nb_traj_backward.
+ */
+int nb_traj_backward_dev(nb_ctx *ctx, const double *d_xbar_T, const double *d_vbar_T,
+                         double *d_xbar0, double *d_vbar0, double *d_mbar);
 
 /*
  * Ensembles: many independent systems ("clusters") integrated together, each

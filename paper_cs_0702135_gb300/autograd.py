@@ -1,9 +1,13 @@
 """torch.autograd.Function over the library's differentiable Hermite trajectory.
 
-Argument marshalling only: the forward pass is nb_traj_forward (fixed shared
-step, checkpoints on the device) and the backward pass nb_traj_backward
-(recomputation per checkpoint segment, transposed corrector and predictor,
-hand-written force VJP kernel).  Leaves are float64 tensors.
+Argument marshalling only: the forward pass is nb_init_dev + nb_traj_forward
+(fixed shared step, checkpoints on the device) + nb_get_state_dev, the backward
+pass nb_traj_backward_dev (recomputation per checkpoint segment, transposed
+corrector and predictor, hand-written force VJP kernel).  Leaves are float64
+CUDA tensors; state, cotangents and gradients stay on the device, and the
+library runs on the leaves' current torch stream.  The library context lives
+from the forward pass to the end of the backward pass (or until the graph is
+freed), so a second backward through the same trajectory is refused.
 """
 from __future__ import annotations
 
@@ -17,23 +21,40 @@ class HermiteTrajectory(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, x0, v0, m, eps, level, steps, checkpoint_every, precision=nb.NB_DS):
-        c = nb.Context(m.detach().cpu().numpy(), x0.detach().cpu().numpy(),
-                       v0.detach().cpu().numpy(), float(eps), level_fixed=int(level),
-                       precision=int(precision), flags=nb.NB_INIT_NO_FORCE)
-        c.nb_traj_forward(int(steps), int(checkpoint_every))
-        st = c.nb_get_state()
+        if x0.device.type != "cuda":
+            raise ValueError("hermite_trajectory needs CUDA tensors")
+        stream = torch.cuda.current_stream(x0.device).cuda_stream
+        xc, vc, mc = (t.detach().to(torch.float64).contiguous() for t in (x0, v0, m))
+        c = nb.Context.from_device(mc, xc, vc, float(eps), level_fixed=int(level),
+                                   precision=int(precision), flags=nb.NB_INIT_NO_FORCE, stream=stream)
+        try:
+            c.nb_traj_forward(int(steps), int(checkpoint_every))
+            xT, vT = torch.empty_like(xc), torch.empty_like(vc)
+            c.nb_get_state_dev(d_x=xT, d_v=vT)
+        except Exception:
+            c.nb_free()
+            raise
         ctx.nbctx = c
-        ctx.device = x0.device
-        return (torch.from_numpy(st["x"]).to(x0.device), torch.from_numpy(st["v"]).to(x0.device))
+        return xT, vT
 
     @staticmethod
     def backward(ctx, gx, gv):
-        xb, vb, mb = ctx.nbctx.nb_traj_backward(
-            gx.detach().cpu().numpy() if gx is not None else torch.zeros(1).numpy(),
-            gv.detach().cpu().numpy() if gv is not None else None)
-        d = ctx.device
-        return (torch.from_numpy(xb).to(d), torch.from_numpy(vb).to(d), torch.from_numpy(mb).to(d),
-                None, None, None, None, None)
+        c = ctx.nbctx
+        if c is None:
+            raise RuntimeError("hermite_trajectory: the trajectory was already differentiated once")
+        ctx.nbctx = None
+        try:
+            n = c.n
+            dev = gx.device if gx is not None else gv.device
+            z = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+            gxc = z if gx is None else gx.to(torch.float64).contiguous()
+            gvc = None if gv is None else gv.to(torch.float64).contiguous()
+            xb, vb = torch.empty_like(z), torch.empty_like(z)
+            mb = torch.empty(n, dtype=torch.float64, device=dev)
+            c.nb_traj_backward_dev(gxc, gvc, xb, vb, mb)
+        finally:
+            c.nb_free()
+        return xb, vb, mb, None, None, None, None, None
 
 
 def hermite_trajectory(x0, v0, m, eps, level, steps, checkpoint_every, precision=nb.NB_DS):

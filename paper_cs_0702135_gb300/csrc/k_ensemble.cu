@@ -70,6 +70,9 @@ struct EnsArgs {
     int qcap;                 // queue capacity: P + C (at most n_c + 1 items per cluster)
     int *pred_left;           // [C] prediction chunks of the cluster not yet done
     float4 *jph, *jpl, *jv;   // [P] predicted double-single records
+    // [P] single-precision mirror of the FP64 state for the j predictor:
+    // position as double-single (x_hi + mass, x_lo), velocity, acceleration, jerk
+    float4 *mh, *ml, *mv, *ma, *mk;
     int *act;                 // [P] active particles of each cluster (local indices)
     int *na;                  // [C] block sizes
     long long *tnext;         // [C] block times
@@ -101,6 +104,67 @@ struct MinLL {
 
 enum EnsMode { kEnsStep = 0, kEnsForce = 1, kEnsInit = 2 };
 
+// (hi, lo) += d in double-single: TwoSum of hi and d, then renormalised.
+__device__ __forceinline__ void ds_add_f(float hi, float lo, float d, float &ho, float &lout)
+{
+    const float s = hi + d;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (d - bb);
+    const float l2 = lo + e;
+    ho = s + l2;
+    lout = l2 - (ho - s);
+}
+
+// j record of particle gi at block time tn from the single-precision mirror:
+// the predictor's Taylor increments (Section 2) in FP32,
+//   dx = (v + (dt/2)(a + (dt/3) k)) dt,   v_p = v + (a + (dt/2) k) dt,
+// and the position accumulated in double-single, x_p = (x_hi + x_lo) + dx.
+// The FP64 state itself is predicted in FP64 by the corrector.
+__device__ __forceinline__ void ens_predict_j32(const EnsArgs &ea, long long gi, long long tn)
+{
+    const float dt = (float)(tn - ea.s.t[gi]) * 0x1p-40f;
+    const float h = 0.5f * dt, q = dt * (1.0f / 3.0f);
+    const float4 xh = ea.mh[gi], xl = ea.ml[gi], v = ea.mv[gi], a = ea.ma[gi], k = ea.mk[gi];
+    float4 ph, pl, pv;
+    ds_add_f(xh.x, xl.x, fmaf(h, fmaf(q, k.x, a.x), v.x) * dt, ph.x, pl.x);
+    ds_add_f(xh.y, xl.y, fmaf(h, fmaf(q, k.y, a.y), v.y) * dt, ph.y, pl.y);
+    ds_add_f(xh.z, xl.z, fmaf(h, fmaf(q, k.z, a.z), v.z) * dt, ph.z, pl.z);
+    pv.x = fmaf(fmaf(h, k.x, a.x), dt, v.x);
+    pv.y = fmaf(fmaf(h, k.y, a.y), dt, v.y);
+    pv.z = fmaf(fmaf(h, k.z, a.z), dt, v.z);
+    ph.w = xh.w;
+    pl.w = 0.0f;
+    pv.w = 0.0f;
+    ea.jph[gi] = ph;
+    ea.jpl[gi] = pl;
+    ea.jv[gi] = pv;
+}
+
+// The single-precision mirror of particle gi from its FP64 state.
+__device__ __forceinline__ void ens_write_mirror(const EnsArgs &ea, long long gi)
+{
+    const State &S = ea.s;
+    const long long P = S.n;
+    float hi[3], lo[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) split_ds(S.x[c * P + gi], hi[c], lo[c]);
+    ea.mh[gi] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(S.m[gi]));
+    ea.ml[gi] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+    ea.mv[gi] = make_float4(__double2float_rn(S.v[gi]), __double2float_rn(S.v[P + gi]),
+                            __double2float_rn(S.v[2 * P + gi]), 0.0f);
+    ea.ma[gi] = make_float4(__double2float_rn(S.a[gi]), __double2float_rn(S.a[P + gi]),
+                            __double2float_rn(S.a[2 * P + gi]), 0.0f);
+    ea.mk[gi] = make_float4(__double2float_rn(S.k[gi]), __double2float_rn(S.k[P + gi]),
+                            __double2float_rn(S.k[2 * P + gi]), 0.0f);
+}
+
+__global__ void k_ens_mirror(EnsArgs ea)
+{
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < ea.s.n;
+         gi += (long long)gridDim.x * blockDim.x)
+        ens_write_mirror(ea, gi);
+}
+
 // Phase A for the cluster of rank q: schedule, predict, compact, publish.
 template <int NT, int MODE>
 __device__ __forceinline__ void ens_a_cluster(const EnsArgs &ea, int q, long long *s_red, int *s_wtot)
@@ -130,16 +194,18 @@ __device__ __forceinline__ void ens_a_cluster(const EnsArgs &ea, int q, long lon
         bool f = false;
         if (i < n && !split) {
             const long long gi = o + i;
-            const double dt = MODE == kEnsStep ? ticks_to_time(tn - S.t[gi]) : 0.0;
-            double xp[3], vp[3];
-            predict3(S, gi, P, dt, xp, vp);
-            float hi[3], lo[3];
+            if (MODE == kEnsStep) {
+                ens_predict_j32(ea, gi, tn);
+            } else {
+                // start-up and force-only passes: the stored state itself (dt = 0)
+                float hi[3], lo[3];
 #pragma unroll
-            for (int cc = 0; cc < 3; ++cc) split_ds(xp[cc], hi[cc], lo[cc]);
-            ea.jph[gi] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(S.m[gi]));
-            ea.jpl[gi] = make_float4(lo[0], lo[1], lo[2], 0.0f);
-            ea.jv[gi] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
-                                    __double2float_rn(vp[2]), 0.0f);
+                for (int cc = 0; cc < 3; ++cc) split_ds(S.x[cc * P + gi], hi[cc], lo[cc]);
+                ea.jph[gi] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(S.m[gi]));
+                ea.jpl[gi] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+                ea.jv[gi] = make_float4(__double2float_rn(S.v[gi]), __double2float_rn(S.v[P + gi]),
+                                        __double2float_rn(S.v[2 * P + gi]), 0.0f);
+            }
         }
         if (i < n) {
             const long long gi = o + i;
@@ -230,16 +296,17 @@ __device__ __forceinline__ void ens_predict_chunk(const EnsArgs &ea, int c, int 
     const int i1 = min(n, (p + 1) * kEnsPredChunk);
     for (int i = p * kEnsPredChunk + tid; i < i1; i += NT) {
         const long long gi = o + i;
-        const double dt = MODE == kEnsStep ? ticks_to_time(tn - S.t[gi]) : 0.0;
-        double xp[3], vp[3];
-        predict3(S, gi, P, dt, xp, vp);
-        float hi[3], lo[3];
+        if (MODE == kEnsStep) {
+            ens_predict_j32(ea, gi, tn);
+        } else {
+            float hi[3], lo[3];
 #pragma unroll
-        for (int cc = 0; cc < 3; ++cc) split_ds(xp[cc], hi[cc], lo[cc]);
-        ea.jph[gi] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(S.m[gi]));
-        ea.jpl[gi] = make_float4(lo[0], lo[1], lo[2], 0.0f);
-        ea.jv[gi] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
-                                __double2float_rn(vp[2]), 0.0f);
+            for (int cc = 0; cc < 3; ++cc) split_ds(S.x[cc * P + gi], hi[cc], lo[cc]);
+            ea.jph[gi] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(S.m[gi]));
+            ea.jpl[gi] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+            ea.jv[gi] = make_float4(__double2float_rn(S.v[gi]), __double2float_rn(S.v[P + gi]),
+                                    __double2float_rn(S.v[2 * P + gi]), 0.0f);
+        }
     }
     __threadfence();
     __syncthreads();
@@ -320,11 +387,26 @@ __device__ __forceinline__ void ens_b_item(const EnsArgs &ea, int c, int k, floa
             ds_add(hi[cc], lo[cc], h2, l2);
         }
     }
-    if (!valid || lig != 0) return;
     double res[7];
 #pragma unroll
     for (int cc = 0; cc < 7; ++cc) res[cc] = (double)hi[cc] + (double)lo[cc];
     const long long gi = o + i;
+    if (MODE == kEnsStep && g >= 4) {
+        // every lane of the group holds the sums: its first four lanes correct
+        // the particle together (the same FP64 operations as one lane would);
+        // the CTA's other lanes run along inactive, as the quads need
+        const int qd = lig & 3, cq = qd < 3 ? qd : 2;
+        const bool active = valid && lig < 4;
+        const bool ok = correct_particle_quad(S, gi, P, __ldcg(&ea.tnext[c]), res[cq], res[3 + cq],
+                                              ea.eta, ea.level_min, 0, active);
+        __syncwarp();
+        if (active && qd == 0) {
+            if (!ok) atomicCAS(ea.err, 0, NB_ESTEP);
+            ens_write_mirror(ea, gi);
+        }
+        return;
+    }
+    if (!valid || lig != 0) return;
     if (MODE == kEnsForce) {
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
@@ -353,6 +435,7 @@ __device__ __forceinline__ void ens_b_item(const EnsArgs &ea, int c, int k, floa
     const double ap[3] = {res[0], res[1], res[2]}, kp[3] = {res[3], res[4], res[5]};
     if (!correct_particle(S, gi, P, __ldcg(&ea.tnext[c]), ap, kp, ea.eta, ea.level_min, 0))
         atomicCAS(ea.err, 0, NB_ESTEP);
+    ens_write_mirror(ea, gi);
 }
 
 // One ensemble block step (or start-up, or force-only pass): phase A over the
@@ -479,6 +562,7 @@ struct nb_ens {
     int *d_lev = nullptr;
     int *d_work = nullptr, *d_done = nullptr, *d_err = nullptr;  // d_work: [4] counters A, B, queue, A done
     float4 *d_jph = nullptr, *d_jpl = nullptr, *d_jv = nullptr;
+    float4 *d_mirror = nullptr;  // [5 P]: x_hi + m, x_lo, v, a, k in single precision
     int *d_act = nullptr, *d_na = nullptr, *d_qc = nullptr, *d_qk = nullptr, *d_pred = nullptr;
     long long *d_tnext = nullptr;
     long long qcap = 0;
@@ -552,6 +636,11 @@ EnsArgs ens_args(nb_ens *e)
     a.jph = e->d_jph;
     a.jpl = e->d_jpl;
     a.jv = e->d_jv;
+    a.mh = e->d_mirror;
+    a.ml = e->d_mirror + e->P;
+    a.mv = e->d_mirror + 2 * e->P;
+    a.ma = e->d_mirror + 3 * e->P;
+    a.mk = e->d_mirror + 4 * e->P;
     a.act = e->d_act;
     a.na = e->d_na;
     a.tnext = e->d_tnext;
@@ -610,6 +699,16 @@ int enqueue_ens(nb_ens *e, const EnsArgs &a)
 // One ensemble block step.
 int enqueue_ens_step(nb_ens *e) { return enqueue_ens<kEnsStep>(e, ens_args(e)); }
 
+// Refreshes the single-precision mirror after the FP64 state was set from outside a step.
+int enqueue_mirror(nb_ens *e)
+{
+    k_ens_mirror<<<(int)std::min<long long>(8LL * e->sms, (e->P + 255) / 256), 256, 0, e->st>>>(
+        ens_args(e));
+    ECK(cudaGetLastError());
+    e->launches += 1;
+    return NB_OK;
+}
+
 int ens_sync(nb_ens *e)
 {
     int h_err = 0;
@@ -647,6 +746,7 @@ void ens_release(nb_ens *e)
     void *ptrs[] = {e->d_off, e->d_order, e->d_x, e->d_v, e->d_a, e->d_k, e->d_m, e->d_t,
                     e->d_lev, e->d_work, e->d_done, e->d_err, e->d_steps, e->d_inter,
                     e->d_stage, e->d_backup, e->d_tbak, e->d_lbak, e->d_jph, e->d_jpl, e->d_jv,
+                    e->d_mirror,
                     e->d_act, e->d_na, e->d_qc, e->d_qk, e->d_tnext, e->d_pred};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -717,7 +817,8 @@ int ens_init_impl(nb_ens *e, int32_t C, const int64_t *off, const double *m, con
         (rc = ealloc(e, &e->d_jpl, P)) || (rc = ealloc(e, &e->d_jv, P)) ||
         (rc = ealloc(e, &e->d_act, P)) || (rc = ealloc(e, &e->d_na, C)) ||
         (rc = ealloc(e, &e->d_tnext, C)) || (rc = ealloc(e, &e->d_qc, P + C)) ||
-        (rc = ealloc(e, &e->d_qk, P + C)) || (rc = ealloc(e, &e->d_pred, C)))
+        (rc = ealloc(e, &e->d_qk, P + C)) || (rc = ealloc(e, &e->d_pred, C)) ||
+        (rc = ealloc(e, &e->d_mirror, 5 * P)))
         return rc;
     e->S.x = e->d_x;
     e->S.v = e->d_v;
@@ -747,6 +848,7 @@ int ens_init_impl(nb_ens *e, int32_t C, const int64_t *off, const double *m, con
     // start-up: force on every particle of every cluster, initial steps
     if ((rc = enqueue_ens<kEnsInit>(e, ens_args(e)))) return rc;
     ECK(cudaGetLastError());
+    if ((rc = enqueue_mirror(e))) return rc;
     return ens_sync(e);
 }
 
@@ -897,7 +999,7 @@ int nb_ens_tune(nb_ens *e, int launches_per_candidate, int *threads_out, int *gm
                             sizeof(long long) * C, cudaMemcpyDeviceToDevice, e->st));
         ECK(cudaMemcpyAsync(restore ? e->d_inter : cb + C, restore ? cb + C : e->d_inter,
                             sizeof(long long) * C, cudaMemcpyDeviceToDevice, e->st));
-        return NB_OK;
+        return restore ? enqueue_mirror(e) : NB_OK;
     };
     if ((rc = save(false))) return rc;
     cudaEvent_t e0, e1;
@@ -1021,6 +1123,8 @@ int nb_ens_set_state(nb_ens *e, const double *x, const double *v, const double *
     ECK(cudaMemcpyAsync(e->d_t, t, sizeof(long long) * P, cudaMemcpyHostToDevice, e->st));
     ECK(cudaMemcpyAsync(e->d_lev, level, sizeof(int) * P, cudaMemcpyHostToDevice, e->st));
     ECK(cudaMemsetAsync(e->d_done, 0, sizeof(int) * e->C, e->st));
+    int rc = enqueue_mirror(e);
+    if (rc) return rc;
     return ens_sync(e);
 }
 

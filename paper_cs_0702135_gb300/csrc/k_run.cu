@@ -401,7 +401,21 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
                 }
             }
             __syncthreads();
-            if (tid < kn) {
+            if (kn <= kRunQuadMax) {
+                // few particles: four lanes each (the same FP64 operations,
+                // about half the FP64 instructions per particle)
+                if (warp * 8 < kn) {
+                    const int kq = tid >> 2, qd = tid & 3;
+                    const bool active = kq < kn;
+                    const int kk = active ? kq : kn - 1;
+                    const int c = qd < 3 ? qd : 2;
+                    const int i = (int)__ldcg(&ra.act[r + (long long)ra.ncta * (k0 + kk)]);
+                    const bool ok = correct_particle_quad<true>(S, i, n, tn, s_res[kk][c],
+                                                                s_res[kk][3 + c], ra.eta,
+                                                                ra.level_min, ra.level_fixed, active);
+                    if (active && qd == 0 && !ok) atomicCAS(&ra.ctrl->err, 0, NB_ESTEP);
+                }
+            } else if (tid < kn) {
                 const double ap[3] = {s_res[tid][0], s_res[tid][1], s_res[tid][2]};
                 const double kp[3] = {s_res[tid][3], s_res[tid][4], s_res[tid][5]};
                 const int i = (int)__ldcg(&ra.act[r + (long long)ra.ncta * (k0 + tid)]);

@@ -8,6 +8,7 @@
 // is contracted and the same inputs give the same bits as any IEEE FP64
 // evaluation of those formulas in that order.  This is what lets integer block
 // levels be compared bit for bit with a CPU evaluation.
+#include <algorithm>
 #include <climits>
 
 #include "nb_device.cuh"
@@ -50,16 +51,36 @@ __global__ void k_predict(State s, long long t_val, const long long *t_ptr, cons
     }
 }
 
-// Hermite corrector and Aarseth step for the block (Section 2), one thread
-// per active particle; the arithmetic is correct_particle's.
-__global__ void k_correct(State s, const int *act, int na_host, const int *na_dev, long long t_val,
-                          const long long *t_ptr, const double *acc_new, const double *jerk_new,
-                          double eta, int level_min, int level_fixed, int *err)
+// Hermite corrector and Aarseth step for the block (Section 2); the
+// arithmetic is correct_particle's.  One warp per CTA: blocks of at most
+// quad_max particles take four lanes per particle (correct_particle_quad),
+// eight particles per warp, so a small block spreads over many SMs' FP64
+// pipes; larger blocks take one thread per particle.
+__global__ void __launch_bounds__(32) k_correct(State s, const int *act, int na_host,
+                                                const int *na_dev, long long t_val,
+                                                const long long *t_ptr, const double *acc_new,
+                                                const double *jerk_new, double eta, int level_min,
+                                                int level_fixed, int quad_max, int *err)
 {
     const int na = na_dev ? *na_dev : na_host;
     if (na <= 0) return;
     const long long tn = t_ptr ? *t_ptr : t_val;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < na; b += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x;
+    if (na <= quad_max) {
+        const int tasks = (na + 7) / 8;
+        for (int w = blockIdx.x; w < tasks; w += gridDim.x) {
+            const int b = w * 8 + (lane >> 2), q = lane & 3;
+            const bool active = b < na;
+            const long long bb = active ? b : na - 1;
+            const int c = q < 3 ? q : 2;
+            const bool ok = correct_particle_quad(s, act[bb], s.n, tn, acc_new[3 * bb + c],
+                                                  jerk_new[3 * bb + c], eta, level_min, level_fixed,
+                                                  active);
+            if (active && q == 0 && !ok) raise_err(err, NB_ESTEP);
+        }
+        return;
+    }
+    for (int b = blockIdx.x * 32 + lane; b < na; b += gridDim.x * 32) {
         double ap[3], kp[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -272,6 +293,15 @@ __global__ void k_validate(const int *idx, int na, int n, unsigned int *bitmap, 
     }
 }
 
+__global__ void k_check_input(const double *p, long long cnt, bool nonneg, int *err)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < cnt;
+         e += (long long)gridDim.x * blockDim.x) {
+        const double q = p[e];
+        if (!isfinite(q) || (nonneg && q < 0.0)) raise_err(err, kErrInput);
+    }
+}
+
 __global__ void k_gather_state(State s, double *x, double *v, double *a, double *k)
 {
     const int n = s.n;
@@ -322,11 +352,16 @@ void launch_predict(const State &s, long long t_val, const long long *t_ptr, con
 
 void launch_correct(const State &s, const int *act, int na_host, const int *na_dev, long long t_val,
                     const long long *t_ptr, const double *acc_new, const double *jerk_new,
-                    double eta, int level_min, int level_fixed, int *err, cudaStream_t st)
+                    double eta, int level_min, int level_fixed, int *err, int sms, cudaStream_t st)
 {
-    const int g = na_dev ? grid_for(s.n, 128) : grid_for(na_host, 128);
-    k_correct<<<g, 128, 0, st>>>(s, act, na_host, na_dev, t_val, t_ptr, acc_new, jerk_new, eta,
-                                 level_min, level_fixed, err);
+    // quad_max: where eight particles per warp stop beating 32 (a warp per
+    // SM of each form; measured on whole block-step runs)
+    const int quad_max = kCorrectQuadPerSM * (sms > 0 ? sms : 1);
+    const long long cap = na_dev ? (long long)s.n : (long long)na_host;
+    const long long tasks = std::max((cap + 31) / 32, (std::min<long long>(cap, quad_max) + 7) / 8);
+    const int g = (int)std::max(1LL, std::min(tasks, 8192LL));
+    k_correct<<<g, 32, 0, st>>>(s, act, na_host, na_dev, t_val, t_ptr, acc_new, jerk_new, eta,
+                                level_min, level_fixed, quad_max, err);
 }
 
 void launch_initial_steps(const State &s, const double *acc, const double *jerk, double eta_init,
@@ -374,6 +409,12 @@ void launch_scatter_state(const State &s, const double *x, const double *v, cons
                           const double *k, cudaStream_t st)
 {
     k_scatter_state<<<grid_for(s.n, 256), 256, 0, st>>>(s, x, v, a, k);
+}
+
+void launch_check_input(const double *p, long long cnt, bool nonneg, int *err, cudaStream_t st)
+{
+    if (cnt <= 0 || !p) return;
+    k_check_input<<<grid_for(cnt, 256), 256, 0, st>>>(p, cnt, nonneg, err);
 }
 
 void launch_iota(int *p, int n, cudaStream_t st)

@@ -170,6 +170,8 @@ int sync_ctrl(nb_ctx *c)
         if (e == NB_EINVAL) return fail(c, NB_EINVAL, "invalid particle index (device check)");
         if (e == NB_ETIMEOUT)
             return fail(c, NB_ETIMEOUT, "a bounded device wait ran out");
+        if (e == kErrInput)
+            return fail(c, NB_EINVAL, "non-finite input or negative mass (device check)");
         if (e == kErrFixedScale)
             return fail(c, NB_EINVAL, "fixed-point summation: masses, velocities or eps put the "
                                       "fixed-point units outside the single-precision range");
@@ -278,7 +280,7 @@ void enqueue_step(nb_ctx *c)
     enqueue_force(c, c->d_act, 0, &c->d_ctrl->n_active, res_out(c));
     launch_correct(c->S, c->d_act, 0, &c->d_ctrl->n_active, 0, &c->d_ctrl->t_next, c->d_res,
                    c->d_res + 3LL * c->n, c->o.eta, c->o.level_min, c->o.level_fixed,
-                   &c->d_ctrl->err, c->st);
+                   &c->d_ctrl->err, c->sms, c->st);
     c->launches += 3 + 1 + 1;  // scheduler, predictor, corrector (force counted above)
 }
 
@@ -498,8 +500,9 @@ void nb_free(nb_ctx *c)
     delete c;
 }
 
+// dev: m, x, v are device arrays (checked on the device) instead of host arrays.
 static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, const double *v,
-                     double eps, const nb_opts *opts)
+                     double eps, const nb_opts *opts, bool dev)
 {
     nb_opts o;
     nb_default_opts(&o);
@@ -529,10 +532,12 @@ static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, con
         if (!(e2 >= 0x1p-126f) || std::isinf(e2))
             return fail(c, NB_EINVAL, "NB_SUM_FIXED needs eps^2 to be a normal single-precision number");
     }
-    if (!finite_all(m, n) || !finite_all(x, 3 * n) || !finite_all(v, 3 * n))
-        return fail(c, NB_EINVAL, "non-finite input");
-    for (int64_t i = 0; i < n; ++i)
-        if (m[i] < 0.0) return fail(c, NB_EINVAL, "negative mass at %lld", (long long)i);
+    if (!dev) {
+        if (!finite_all(m, n) || !finite_all(x, 3 * n) || !finite_all(v, 3 * n))
+            return fail(c, NB_EINVAL, "non-finite input");
+        for (int64_t i = 0; i < n; ++i)
+            if (m[i] < 0.0) return fail(c, NB_EINVAL, "negative mass at %lld", (long long)i);
+    }
 
     c->n = (int)n;
     c->eps = eps;
@@ -543,9 +548,9 @@ static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, con
         CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
         c->own_stream = true;
     }
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+    int device = 0;
+    CK(cudaGetDevice(&device));
+    CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device));
     const bool f64 = o.precision == NB_FP64;
     int bi = 0, bj = 0, bs = 0;
     if (occupancy_force(o.precision, kRegIpar, &bi) || occupancy_force(o.precision, kRegJpar, &bj) ||
@@ -628,9 +633,16 @@ static int init_impl(nb_ctx *c, int64_t n, const double *m, const double *x, con
     CK(cudaMemsetAsync(c->d_k, 0, sizeof(double) * 3 * N, c->st));
     CK(cudaMemsetAsync(c->d_t, 0, sizeof(long long) * N, c->st));
     CK(cudaMemsetAsync(c->d_jcnt, 0, sizeof(int) * N, c->st));
-    CK(cudaMemcpyAsync(c->d_m, m, sizeof(double) * N, cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(c->d_stage, x, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(c->d_stage + 3 * N, v, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));
+    const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(c->d_m, m, sizeof(double) * N, kind, c->st));
+    CK(cudaMemcpyAsync(c->d_stage, x, sizeof(double) * 3 * N, kind, c->st));
+    CK(cudaMemcpyAsync(c->d_stage + 3 * N, v, sizeof(double) * 3 * N, kind, c->st));
+    if (dev) {
+        // the host checks of nb_init, on the device; reported by the final sync
+        launch_check_input(c->d_m, N, true, &c->d_ctrl->err, c->st);
+        launch_check_input(c->d_stage, 6 * N, false, &c->d_ctrl->err, c->st);
+        c->launches += 2;
+    }
     launch_scatter_state(c->S, c->d_stage, c->d_stage + 3 * N, nullptr, nullptr, c->st);
     launch_iota(c->d_all, c->n, c->st);
     launch_predict(c->S, 0, nullptr, nullptr, o.precision, c->jds, c->jf, c->st);
@@ -662,9 +674,34 @@ int nb_init(nb_ctx **ctx, int64_t n, const double *m, const double *x, const dou
         g_init_err = "out of host memory";
         return NB_ENOMEM;
     }
-    const int rc = init_impl(c, n, m, x, v, eps, opts);
+    const int rc = init_impl(c, n, m, x, v, eps, opts, false);
     if (rc != NB_OK) {
         g_init_err = c->err;  // readable through nb_last_error(NULL)
+        nb_free(c);
+        return rc;
+    }
+    *ctx = c;
+    return NB_OK;
+}
+
+int nb_init_dev(nb_ctx **ctx, int64_t n, const double *d_m, const double *d_x, const double *d_v,
+                double eps, const nb_opts *opts)
+{
+    const Range range_("nb_init_dev");
+    g_init_err.clear();
+    if (!ctx) {
+        g_init_err = "ctx is NULL";
+        return NB_EINVAL;
+    }
+    *ctx = nullptr;
+    nb_ctx *c = new (std::nothrow) nb_ctx();
+    if (!c) {
+        g_init_err = "out of host memory";
+        return NB_ENOMEM;
+    }
+    const int rc = init_impl(c, n, d_m, d_x, d_v, eps, opts, true);
+    if (rc != NB_OK) {
+        g_init_err = c->err;
         nb_free(c);
         return rc;
     }
@@ -713,15 +750,17 @@ int nb_force_dev(nb_ctx *c, const int32_t *d_idx, int32_t na, double *d_acc, dou
     if (na < 0 || na > c->n) return fail(c, NB_EINVAL, "n_active=%d outside [0, %d]", na, c->n);
     if (na > 0 && !d_idx) return fail(c, NB_EINVAL, "active_idx is NULL");
     if (na > 0) {
+        // Validation and force (on the caller's indices) go out together, and
+        // the one synchronisation follows the force: the force kernels clamp every
+        // index into [0, n), so a bad index costs only wasted work, and the
+        // caller's outputs are written only once the indices proved valid.
         CK(cudaMemsetAsync(c->d_bitmap, 0, sizeof(unsigned) * (size_t)((c->n + 31) / 32), c->st));
         launch_validate(d_idx, na, c->n, c->d_bitmap, &c->d_ctrl->err, c->st);
         c->launches += 1;
+        enqueue_force(c, d_idx, na, nullptr, res_out(c));
+        CK(cudaGetLastError());
         int rc = sync_ctrl(c);
         if (rc) return rc;
-        CK(cudaMemcpyAsync(c->d_idx, d_idx, sizeof(int) * (size_t)na, cudaMemcpyDeviceToDevice,
-                           c->st));
-        enqueue_force(c, c->d_idx, na, nullptr, res_out(c));
-        CK(cudaGetLastError());
         if ((rc = copy_results_out(c, na, d_acc, d_jerk, d_pot, cudaMemcpyDeviceToDevice))) return rc;
     }
     c->force_valid = true;
@@ -758,7 +797,7 @@ int nb_correct(nb_ctx *c, const int32_t *idx, int32_t na, double t, const double
     }
     CK(cudaMemcpyAsync(c->d_idx, idx, sizeof(int) * (size_t)na, cudaMemcpyHostToDevice, c->st));
     launch_correct(c->S, c->d_idx, na, nullptr, ticks, nullptr, an, kn, c->o.eta, c->o.level_min,
-                   c->o.level_fixed, &c->d_ctrl->err, c->st);
+                   c->o.level_fixed, &c->d_ctrl->err, c->sms, c->st);
     CK(cudaGetLastError());
     c->launches += 1;
     c->force_valid = false;
@@ -818,9 +857,9 @@ int nb_run(nb_ctx *c, double t_end, int64_t max_steps, int64_t *steps_out, int64
         c->capturing = false;
         c->step_nodes = c->launches - l0;
         c->launches = l0;
-        cudaError_t e = cudaStreamEndCapture(c->st, &g);
-        if (e != cudaSuccess) return fail(c, NB_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&c->step_exec, g, 0);
+        cudaError_t ce = cudaStreamEndCapture(c->st, &g);
+        if (ce != cudaSuccess) return fail(c, NB_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+        const cudaError_t e = cudaGraphInstantiate(&c->step_exec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
             c->step_exec = nullptr;
@@ -904,6 +943,22 @@ int nb_get_state(nb_ctx *c, double *x, double *v, double *a, double *k, int64_t 
     if (t) CK(cudaMemcpyAsync(t, c->d_t, sizeof(long long) * N, cudaMemcpyDeviceToHost, c->st));
     if (lev) CK(cudaMemcpyAsync(lev, c->d_lev, sizeof(int) * N, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
+    return NB_OK;
+}
+
+int nb_get_state_dev(nb_ctx *c, double *d_x, double *d_v, double *d_a, double *d_k, int64_t *d_t,
+                     int32_t *d_lev)
+{
+    const Range range_("nb_get_state_dev");
+    if (!c) return NB_EINVAL;
+    const long long N = c->n;
+    if (d_x || d_v || d_a || d_k) {
+        launch_gather_state(c->S, d_x, d_v, d_a, d_k, c->st);
+        c->launches += 1;
+    }
+    if (d_t) CK(cudaMemcpyAsync(d_t, c->d_t, sizeof(long long) * N, cudaMemcpyDeviceToDevice, c->st));
+    if (d_lev) CK(cudaMemcpyAsync(d_lev, c->d_lev, sizeof(int) * N, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaGetLastError());
     return NB_OK;
 }
 
@@ -1038,25 +1093,31 @@ int nb_traj_forward(nb_ctx *c, int64_t steps, int64_t checkpoint_every)
     return NB_OK;
 }
 
-int nb_traj_backward(nb_ctx *c, const double *xbar_T, const double *vbar_T, double *xbar0,
-                     double *vbar0, double *mbar)
+// dev: the cotangents and the gradients are device arrays.
+static int traj_backward_impl(nb_ctx *c, const double *xbar_T, const double *vbar_T, double *xbar0,
+                              double *vbar0, double *mbar, bool dev)
 {
-    const Range range_("nb_traj_backward");
     if (!c) return NB_EINVAL;
     if (!c->traj_valid) return fail(c, NB_ESTATE, "nb_traj_backward needs nb_traj_forward first");
     if (!xbar_T) return fail(c, NB_EINVAL, "xbar_T is required");
     const long long N = c->n, per = 12 * N;
-    if (!finite_all(xbar_T, 3 * N) || (vbar_T && !finite_all(vbar_T, 3 * N)))
+    if (!dev && (!finite_all(xbar_T, 3 * N) || (vbar_T && !finite_all(vbar_T, 3 * N))))
         return fail(c, NB_EINVAL, "non-finite cotangent");
     int rc = sync_ctrl(c);
     if (rc) return rc;
     const Ctrl saved = *c->h_ctrl;
     const double dt = ldexp(1.0, -c->o.level_fixed);
-    CK(cudaMemcpyAsync(cot(c, 0), xbar_T, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));
+    const cudaMemcpyKind kin = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kout = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(cot(c, 0), xbar_T, sizeof(double) * 3 * N, kin, c->st));
     if (vbar_T)
-        CK(cudaMemcpyAsync(cot(c, 1), vbar_T, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));
+        CK(cudaMemcpyAsync(cot(c, 1), vbar_T, sizeof(double) * 3 * N, kin, c->st));
     else
         CK(cudaMemsetAsync(cot(c, 1), 0, sizeof(double) * 3 * N, c->st));
+    if (dev) {
+        launch_check_input(cot(c, 0), 6 * N, false, &c->d_ctrl->err, c->st);
+        c->launches += 1;
+    }
     CK(cudaMemsetAsync(cot(c, 2), 0, sizeof(double) * (6 * N + N), c->st));  // ab, kb, mb
     const long long steps = c->traj_steps, ck = c->traj_ckpt;
     const long long nseg = (steps + ck - 1) / ck;
@@ -1086,9 +1147,9 @@ int nb_traj_backward(nb_ctx *c, const double *xbar_T, const double *vbar_T, doub
     launch_add3(c->n, cot(c, 0), cot(c, 5), cot(c, 1), cot(c, 6), cot(c, 4), cot(c, 7), c->st);
     c->launches += 2;
     CK(cudaGetLastError());
-    if (xbar0) CK(cudaMemcpyAsync(xbar0, cot(c, 0), sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->st));
-    if (vbar0) CK(cudaMemcpyAsync(vbar0, cot(c, 1), sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->st));
-    if (mbar) CK(cudaMemcpyAsync(mbar, cot(c, 4), sizeof(double) * N, cudaMemcpyDeviceToHost, c->st));
+    if (xbar0) CK(cudaMemcpyAsync(xbar0, cot(c, 0), sizeof(double) * 3 * N, kout, c->st));
+    if (vbar0) CK(cudaMemcpyAsync(vbar0, cot(c, 1), sizeof(double) * 3 * N, kout, c->st));
+    if (mbar) CK(cudaMemcpyAsync(mbar, cot(c, 4), sizeof(double) * N, kout, c->st));
     // leave the context at the end of the trajectory, as after nb_traj_forward
     launch_copy_state(c->S, state_view(c, c->d_fin), c->st);
     CK(cudaMemcpyAsync(c->d_t, c->d_tfin, sizeof(long long) * N, cudaMemcpyDeviceToDevice, c->st));
@@ -1100,6 +1161,20 @@ int nb_traj_backward(nb_ctx *c, const double *xbar_T, const double *vbar_T, doub
     CK(cudaMemcpyAsync(c->d_ctrl, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->st));
     c->force_valid = false;
     return sync_ctrl(c);
+}
+
+int nb_traj_backward(nb_ctx *c, const double *xbar_T, const double *vbar_T, double *xbar0,
+                     double *vbar0, double *mbar)
+{
+    const Range range_("nb_traj_backward");
+    return traj_backward_impl(c, xbar_T, vbar_T, xbar0, vbar0, mbar, false);
+}
+
+int nb_traj_backward_dev(nb_ctx *c, const double *d_xbar_T, const double *d_vbar_T, double *d_xbar0,
+                         double *d_vbar0, double *d_mbar)
+{
+    const Range range_("nb_traj_backward_dev");
+    return traj_backward_impl(c, d_xbar_T, d_vbar_T, d_xbar0, d_vbar0, d_mbar, true);
 }
 
 int nb_set_profiling(nb_ctx *c, int enable)

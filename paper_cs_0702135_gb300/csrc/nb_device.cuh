@@ -50,6 +50,28 @@ __device__ __forceinline__ void ds_add(float &h, float &l, float h2, float l2)
     l = (l + l2) + e;
 }
 
+// a / C rounded to nearest, for the constants C = 3, 12, 20 of the predictor
+// and corrector, without an FP64 division (a long sequence on the GB300's
+// narrow FP64 pipe): q0 = RN(a y) with y = RN(1/C) is within one ulp of a/C
+// (1/C is rounded with relative error 2^-54 for these C), the residual
+// r = a - C q0 is exact in one FMA, and RN(q0 + r y) is then RN(a/C) by
+// Markstein's theorem (IBM J. Res. Dev. 34, 1990).  Operands outside
+// 2^-900 < |a| < 2^1000 (zero with its sign, huge, not finite) take the plain
+// division; the range test reads the exponent bits on the integer pipe.
+template <int C>
+__device__ __forceinline__ double div_by(double a)
+{
+    static_assert(C == 3 || C == 12 || C == 20, "reciprocal error checked for 3, 12, 20 only");
+    const unsigned hi = (unsigned)__double2hiint(a) & 0x7FFFFFFFu;
+    if (hi >= (123u << 20) && hi < (2023u << 20)) {
+        constexpr double y = 1.0 / C;
+        const double q0 = __dmul_rn(a, y);
+        const double r = __fma_rn(-q0, (double)C, a);
+        return __fma_rn(r, y, q0);
+    }
+    return __ddiv_rn(a, (double)C);
+}
+
 // Hermite predictor (Section 2), round-to-nearest in the formula's order:
 //   x_p = x + (v + (dt/2)(a + (dt/3) k)) dt,   v_p = v + (a + (dt/2) k) dt.
 // dt/2 is taken as dt * 0.5, the same number (halving is exact for every dt on
@@ -65,7 +87,7 @@ __device__ __forceinline__ void predict1hq(double x, double v, double a, double 
 __device__ __forceinline__ void predict1(double x, double v, double a, double k, double dt,
                                          double &xp, double &vp)
 {
-    predict1hq(x, v, a, k, dt, __dmul_rn(dt, 0.5), __ddiv_rn(dt, 3.0), xp, vp);
+    predict1hq(x, v, a, k, dt, __dmul_rn(dt, 0.5), div_by<3>(dt), xp, vp);
 }
 
 // State loads: plain, or past L1 (CG) for state that other SMs may have
@@ -82,7 +104,7 @@ template <bool CG = false>
 __device__ __forceinline__ void predict3(const State &s, long long i, long long n, double dt,
                                          double xp[3], double vp[3])
 {
-    const double h = __dmul_rn(dt, 0.5), q = __ddiv_rn(dt, 3.0);
+    const double h = __dmul_rn(dt, 0.5), q = div_by<3>(dt);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
         predict1hq(ldst<CG>(&s.x[c * n + i]), ldst<CG>(&s.v[c * n + i]), ldst<CG>(&s.a[c * n + i]),
@@ -153,7 +175,7 @@ __device__ __forceinline__ bool correct_particle(const State &s, long long i, lo
                                                  double eta, int level_min, int level_fixed)
 {
     const double dt = ticks_to_time(tn - ldst<CG>(&s.t[i]));
-    const double h = __dmul_rn(dt, 0.5), q = __ddiv_rn(dt, 3.0);
+    const double h = __dmul_rn(dt, 0.5), q = div_by<3>(dt);
     double a2[3], a3[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -165,10 +187,10 @@ __device__ __forceinline__ bool correct_particle(const State &s, long long i, lo
         const double d = __dsub_rn(a, ap[c]);
         a3[c] = __dadd_rn(__dmul_rn(2.0, d), __dmul_rn(__dadd_rn(k, kp[c]), dt));
         a2[c] = __dsub_rn(__dmul_rn(-3.0, d), __dmul_rn(__dadd_rn(__dmul_rn(2.0, k), kp[c]), dt));
-        s.x[e] = __dadd_rn(xp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[c], 12.0), __ddiv_rn(a3[c], 20.0)),
+        s.x[e] = __dadd_rn(xp, __dmul_rn(__dadd_rn(div_by<12>(a2[c]), div_by<20>(a3[c])),
                                          __dmul_rn(dt, dt)));
         // a3 / 4 as a3 * 0.25: the same real number, so the same rounded result
-        s.v[e] = __dadd_rn(vp, __dmul_rn(__dadd_rn(__ddiv_rn(a2[c], 3.0), __dmul_rn(a3[c], 0.25)), dt));
+        s.v[e] = __dadd_rn(vp, __dmul_rn(__dadd_rn(div_by<3>(a2[c]), __dmul_rn(a3[c], 0.25)), dt));
         s.a[e] = ap[c];
         s.k[e] = kp[c];
     }
@@ -189,8 +211,14 @@ __device__ __forceinline__ bool correct_particle(const State &s, long long i, lo
     double s1[3], cr[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double s0 = pow2 ? __dmul_rn(__dmul_rn(2.0, a2[c]), r2) : __ddiv_rn(__dmul_rn(2.0, a2[c]), dt2);
-        cr[c] = pow2 ? __dmul_rn(__dmul_rn(6.0, a3[c]), r3) : __ddiv_rn(__dmul_rn(6.0, a3[c]), dt3);
+        double s0;
+        if (pow2) {
+            s0 = __dmul_rn(__dmul_rn(2.0, a2[c]), r2);
+            cr[c] = __dmul_rn(__dmul_rn(6.0, a3[c]), r3);
+        } else {
+            s0 = __ddiv_rn(__dmul_rn(2.0, a2[c]), dt2);
+            cr[c] = __ddiv_rn(__dmul_rn(6.0, a3[c]), dt3);
+        }
         s1[c] = __dadd_rn(s0, __dmul_rn(cr[c], dt));
     }
     const double na = norm3(ap[0], ap[1], ap[2]);
@@ -204,6 +232,103 @@ __device__ __forceinline__ bool correct_particle(const State &s, long long i, lo
     const bool ok = level_of(dt_raw, level_min, kq);
     if (!ok) kq = kTickBits;
     s.lev[i] = next_level(ldst<CG>(&s.lev[i]), kq, tn, level_min);
+    return ok;
+}
+
+// correct_particle spread over the four lanes of a quad (lanes 4u .. 4u+3 of
+// a warp), for blocks too small to fill the GPU: the corrector is a chain of
+// FP64 operations, and on the GB300 an FP64 warp instruction occupies the SM's
+// narrow FP64 pipe for many cycles however few of its lanes are active, so
+// one particle's three axes on three lanes (and its four norms on four)
+// issue about half the FP64 instructions of the one-thread form.  Each lane
+// evaluates exactly the operations of correct_particle for its axis, in the
+// same order, so the results are the same bits.
+//
+// Every lane of the warp must call this together (it shuffles over the whole
+// warp).  Lane q = lane & 3 of a quad passes component q of the new
+// acceleration and jerk (lane 3: any finite value, e.g. that of axis 2) and
+// the same particle i as its quad; `active` false (the whole quad) computes
+// on a valid i without storing.  Returns false (on every lane of an active
+// quad) when the new step fell below 2^-40.
+template <bool CG = false>
+__device__ __forceinline__ bool correct_particle_quad(const State &s, long long i, long long stride,
+                                                      long long tn, double apc, double kpc,
+                                                      double eta, int level_min, int level_fixed,
+                                                      bool active)
+{
+    const int lane = threadIdx.x & 31, q = lane & 3, base = lane & ~3;
+    const int c = q < 3 ? q : 2;          // lane 3 shadows axis 2 without storing
+    const bool own = active && q < 3;
+    const double dt = ticks_to_time(tn - ldst<CG>(&s.t[i]));
+    const double h = __dmul_rn(dt, 0.5), q3 = div_by<3>(dt);
+    const long long e = c * stride + i;
+    const double x = ldst<CG>(&s.x[e]), v = ldst<CG>(&s.v[e]), a = ldst<CG>(&s.a[e]),
+                 k = ldst<CG>(&s.k[e]);
+    const int lev_old = ldst<CG>(&s.lev[i]);
+    double xp, vp;
+    predict1hq(x, v, a, k, dt, h, q3, xp, vp);
+    const double d = __dsub_rn(a, apc);
+    const double a3 = __dadd_rn(__dmul_rn(2.0, d), __dmul_rn(__dadd_rn(k, kpc), dt));
+    const double a2 = __dsub_rn(__dmul_rn(-3.0, d), __dmul_rn(__dadd_rn(__dmul_rn(2.0, k), kpc), dt));
+    const double xn = __dadd_rn(xp, __dmul_rn(__dadd_rn(div_by<12>(a2), div_by<20>(a3)),
+                                            __dmul_rn(dt, dt)));
+    const double vn = __dadd_rn(vp, __dmul_rn(__dadd_rn(div_by<3>(a2), __dmul_rn(a3, 0.25)), dt));
+    // every lane of the quad has read the old state before any lane stores
+    __syncwarp();
+    if (own) {
+        s.x[e] = xn;
+        s.v[e] = vn;
+        s.a[e] = apc;
+        s.k[e] = kpc;
+    }
+    if (level_fixed > 0) {
+        if (active && q == 0) {
+            s.t[i] = tn;
+            s.lev[i] = level_fixed;
+        }
+        return true;
+    }
+    const double dt2 = __dmul_rn(dt, dt);
+    const double dt3 = __dmul_rn(dt2, dt);
+    const bool pow2 = (__double_as_longlong(dt) & 0x000FFFFFFFFFFFFFLL) == 0 && dt > 0x1p-100;
+    const double r2 = pow2 ? __longlong_as_double((2046LL << 52) - (__double_as_longlong(dt2) & 0x7FF0000000000000LL)) : 0.0;
+    const double r3 = pow2 ? __longlong_as_double((2046LL << 52) - (__double_as_longlong(dt3) & 0x7FF0000000000000LL)) : 0.0;
+    double s0, cr;
+    if (pow2) {
+        s0 = __dmul_rn(__dmul_rn(2.0, a2), r2);
+        cr = __dmul_rn(__dmul_rn(6.0, a3), r3);
+    } else {
+        s0 = __ddiv_rn(__dmul_rn(2.0, a2), dt2);
+        cr = __ddiv_rn(__dmul_rn(6.0, a3), dt3);
+    }
+    const double s1 = __dadd_rn(s0, __dmul_rn(cr, dt));
+    // |a_p|, |k_p|, |s1|, |c| on lanes 0..3 of the quad, each as norm3 forms it
+    const double sq0 = __dmul_rn(apc, apc), sq1 = __dmul_rn(kpc, kpc);
+    const double sq2 = __dmul_rn(s1, s1), sq3 = __dmul_rn(cr, cr);
+    double w[3];
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+        const double t0 = __shfl_sync(0xffffffffu, sq0, base + cc);
+        const double t1 = __shfl_sync(0xffffffffu, sq1, base + cc);
+        const double t2 = __shfl_sync(0xffffffffu, sq2, base + cc);
+        const double t3 = __shfl_sync(0xffffffffu, sq3, base + cc);
+        w[cc] = q == 0 ? t0 : (q == 1 ? t1 : (q == 2 ? t2 : t3));
+    }
+    const double nrm = __dsqrt_rn(__dadd_rn(__dadd_rn(w[0], w[1]), w[2]));
+    const double na = __shfl_sync(0xffffffffu, nrm, base + 0);
+    const double nk = __shfl_sync(0xffffffffu, nrm, base + 1);
+    const double ns = __shfl_sync(0xffffffffu, nrm, base + 2);
+    const double nc = __shfl_sync(0xffffffffu, nrm, base + 3);
+    const double num = __dadd_rn(__dmul_rn(na, ns), __dmul_rn(nk, nk));
+    const double den = __dadd_rn(__dmul_rn(nk, nc), __dmul_rn(ns, ns));
+    const double dt_raw = den == 0.0 ? (double)INFINITY : __dsqrt_rn(__ddiv_rn(__dmul_rn(eta, num), den));
+    int kq;
+    const bool ok = level_of(dt_raw, level_min, kq);
+    if (!ok) kq = kTickBits;
+    if (active && q == 0) {
+        s.t[i] = tn;
+        s.lev[i] = next_level(lev_old, kq, tn, level_min);
+    }
     return ok;
 }
 

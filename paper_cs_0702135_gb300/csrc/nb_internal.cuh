@@ -275,6 +275,7 @@ constexpr int kFixUnroll = NB_FIX_UNROLL;  // fixed point: j unrolling of the in
 constexpr int kSeqNT = 128;         // FP32 index order: threads per CTA, one i each
 constexpr int kSortNT = 1024;       // FP32 sorted: one CTA per i
 constexpr int kErrFixedScale = 64;  // device error word: fixed-point scales out of range
+constexpr int kErrInput = 65;       // device error word: a non-finite value or a negative mass
 
 __host__ __device__ inline ForcePlan make_force_plan(const ForceArgs &fa, int na)
 {
@@ -315,6 +316,8 @@ __device__ __forceinline__ ForcePlan load_plan(const ForceArgs &fa)
 // systems of up to kRunMaxN particles, kRunNT threads per CTA, one CTA per
 // `per` particles.
 constexpr int kRunNT = 256;
+// a CTA corrects up to this many particles of a step with four lanes each
+constexpr int kRunQuadMax = 16;
 constexpr int kRunMaxN = 16384;   // above it the per-stage graph, using every SM for the force, is faster
 struct RunArgs {
     State s;
@@ -385,10 +388,13 @@ cudaError_t launch_check_wait(const unsigned long long *counter, long long limit
 // k_step.cu
 void launch_predict(const State &s, long long t_val, const long long *t_ptr, const int *gate,
                     int precision, JDS jds, JF64 jf, cudaStream_t st);
+// Blocks of at most kCorrectQuadPerSM x SMs particles are corrected with four
+// lanes per particle (correct_particle_quad), larger ones one thread each.
+constexpr int kCorrectQuadPerSM = 16;
 void launch_correct(const State &s, const int *act, int na_host, const int *na_dev,
                     long long t_val, const long long *t_ptr, const double *acc_new,
                     const double *jerk_new, double eta, int level_min, int level_fixed,
-                    int *err, cudaStream_t st);
+                    int *err, int sms, cudaStream_t st);
 void launch_initial_steps(const State &s, const double *acc, const double *jerk, double eta_init,
                           int level_min, int level_fixed, int *err, cudaStream_t st);
 // Also writes the plan of the force on the new block (make_force_plan(fa, n_active)).
@@ -405,6 +411,9 @@ void launch_gather_state(const State &s, double *x, double *v, double *a, double
 void launch_scatter_state(const State &s, const double *x, const double *v, const double *a,
                           const double *k, cudaStream_t st);
 void launch_iota(int *p, int n, cudaStream_t st);
+// Raises kErrInput unless every value of p[cnt] is finite (and, with
+// nonneg, >= 0).
+void launch_check_input(const double *p, long long cnt, bool nonneg, int *err, cudaStream_t st);
 
 // k_adjoint.cu
 int vjp_slots(int precision, int sms);

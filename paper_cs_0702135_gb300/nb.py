@@ -65,6 +65,10 @@ SIGNATURES = [
     ("nb_default_opts", None, [ctypes.POINTER(nb_opts)]),
     ("nb_init", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int64, _vp, _vp, _vp, ctypes.c_double,
                                ctypes.POINTER(nb_opts)]),
+    ("nb_init_dev", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int64, _vp, _vp, _vp,
+                                   ctypes.c_double, ctypes.POINTER(nb_opts)]),
+    ("nb_get_state_dev", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("nb_traj_backward_dev", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("nb_predict", ctypes.c_int, [_vp, ctypes.c_double]),
     ("nb_force", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, _vp]),
     ("nb_force_dev", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, _vp]),
@@ -191,6 +195,21 @@ def nb_init(m, x, v, eps, opts=None):
     return ctx
 
 
+def nb_init_dev(n, d_m, d_x, d_v, eps, opts=None):
+    """nb_init from device arrays (torch CUDA float64 tensors m[n], x[n,3],
+    v[n,3], or raw device addresses); returns a context handle."""
+    n = int(n)
+    nn = max(n, 0)
+    args = (_dev(d_m, "float64", nn, "d_m"), _dev(d_x, "float64", 3 * nn, "d_x"),
+            _dev(d_v, "float64", 3 * nn, "d_v"))
+    ctx = ctypes.c_void_p()
+    rc = lib().nb_init_dev(ctypes.byref(ctx), n, *args, float(eps),
+                           None if opts is None else ctypes.byref(opts))
+    if rc != NB_OK:
+        raise NbError(rc, lib().nb_last_error(None).decode())
+    return ctx
+
+
 def nb_predict(ctx, t):
     _check(ctx, lib().nb_predict(ctx, float(t)))
 
@@ -272,6 +291,18 @@ def nb_get_state(ctx):
     return st
 
 
+def nb_get_state_dev(ctx, d_x=None, d_v=None, d_a=None, d_k=None, d_t=None, d_level=None):
+    """nb_get_state into device tensors (float64 [n,3]; int64 / int32 [n]),
+    enqueued on the context's stream."""
+    n = int(lib().nb_num_particles(ctx))
+    _check(ctx, lib().nb_get_state_dev(ctx, _dev(d_x, "float64", 3 * n, "d_x", False),
+                                       _dev(d_v, "float64", 3 * n, "d_v", False),
+                                       _dev(d_a, "float64", 3 * n, "d_a", False),
+                                       _dev(d_k, "float64", 3 * n, "d_k", False),
+                                       _dev(d_t, "int64", n, "d_t", False),
+                                       _dev(d_level, "int32", n, "d_level", False)))
+
+
 def nb_set_state(ctx, x, v, a, k, t, level):
     n = int(lib().nb_num_particles(ctx))
     arrs = [_f64(x, (n, 3)), _f64(v, (n, 3)), _f64(a, (n, 3)), _f64(k, (n, 3)),
@@ -311,6 +342,17 @@ def nb_traj_backward(ctx, xbar_T, vbar_T=None):
     xb, vb, mb = np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
     _check(ctx, lib().nb_traj_backward(ctx, _ptr(xt), _ptr(vt), _ptr(xb), _ptr(vb), _ptr(mb)))
     return xb, vb, mb
+
+
+def nb_traj_backward_dev(ctx, d_xbar_T, d_vbar_T=None, d_xbar0=None, d_vbar0=None, d_mbar=None):
+    """nb_traj_backward with device tensors (float64): cotangents of the final
+    x, v in, gradients with respect to the initial x, v and the masses out."""
+    n = int(lib().nb_num_particles(ctx))
+    _check(ctx, lib().nb_traj_backward_dev(ctx, _dev(d_xbar_T, "float64", 3 * n, "d_xbar_T"),
+                                           _dev(d_vbar_T, "float64", 3 * n, "d_vbar_T", False),
+                                           _dev(d_xbar0, "float64", 3 * n, "d_xbar0", False),
+                                           _dev(d_vbar0, "float64", 3 * n, "d_vbar0", False),
+                                           _dev(d_mbar, "float64", n, "d_mbar", False)))
 
 
 def nb_set_profiling(ctx, enable=True):
@@ -487,6 +529,23 @@ class Context:
         self.ctx = nb_init(m, x, v, eps, o)
         self.n = nb_num_particles(self.ctx)
 
+    @classmethod
+    def from_device(cls, d_m, d_x, d_v, eps, n=None, **opts):
+        """A context made by nb_init_dev from device tensors (float64 m[n],
+        x[n,3], v[n,3]); n is needed only for raw addresses."""
+        self = cls.__new__(cls)
+        n = d_m.numel() if n is None else int(n)
+        o = nb_default_opts(**opts) if opts else None
+        self.ctx = nb_init_dev(n, d_m, d_x, d_v, eps, o)
+        self.n = nb_num_particles(self.ctx)
+        return self
+
+    def nb_get_state_dev(self, d_x=None, d_v=None, d_a=None, d_k=None, d_t=None, d_level=None):
+        return nb_get_state_dev(self.ctx, d_x, d_v, d_a, d_k, d_t, d_level)
+
+    def nb_traj_backward_dev(self, d_xbar_T, d_vbar_T=None, d_xbar0=None, d_vbar0=None, d_mbar=None):
+        return nb_traj_backward_dev(self.ctx, d_xbar_T, d_vbar_T, d_xbar0, d_vbar0, d_mbar)
+
     def nb_predict(self, t):
         return nb_predict(self.ctx, t)
 
@@ -537,6 +596,12 @@ class Context:
 
     def nb_free(self):
         nb_free(self.ctx)
+
+    def __del__(self):
+        try:
+            self.nb_free()
+        except Exception:
+            pass
 
     def __enter__(self):
         return self

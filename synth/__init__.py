@@ -3,4 +3,4 @@
 Input generation only: no force, integrator or energy arithmetic of the method
 lives here.
 """
-from .plummer import plummer, sample_active, ensemble, salpeter_masses  # noqa: F401
+from .plummer import plummer, sample_active, ensemble, ensemble_member, salpeter_masses  # noqa: F401

@@ -175,6 +175,22 @@ def _ensemble_cluster(job):
     return plummer(nc, sub, masses=m, virial_ratio=q, exact_virial_max=1024, sample_pairs=200000)
 
 
+def _ensemble_jobs(n_clusters, seed, n_lo, n_hi, q_lo, q_hi):
+    c = np.arange(n_clusters, dtype=np.int64)
+    un = rng.uniform(seed, _S_ENS_N, c)
+    sizes = np.floor(np.exp(math.log(n_lo) + un * (math.log(n_hi + 1) - math.log(n_lo)))).astype(np.int64)
+    sizes = np.clip(sizes, n_lo, n_hi)
+    uq = rng.uniform(seed, _S_ENS_Q, c)
+    return [(int(sizes[ci]), (seed * 1000003 + ci) & 0x7FFFFFFFFFFFFFFF,
+             float(q_lo + uq[ci] * (q_hi - q_lo))) for ci in range(n_clusters)]
+
+
+def ensemble_member(n_clusters: int, seed: int, index: int, n_lo: int = 32, n_hi: int = 4096,
+                    q_lo: float = 0.3, q_hi: float = 0.7):
+    """Cluster ``index`` of ``ensemble(n_clusters, seed, ...)`` alone, bit for bit."""
+    return _ensemble_cluster(_ensemble_jobs(n_clusters, seed, n_lo, n_hi, q_lo, q_hi)[index])
+
+
 def ensemble(n_clusters: int, seed: int, n_lo: int = 32, n_hi: int = 4096,
              q_lo: float = 0.3, q_hi: float = 0.7, workers: int = 1):
     """Independent clusters: N log-uniform in [n_lo, n_hi], Salpeter masses,
@@ -182,13 +198,7 @@ def ensemble(n_clusters: int, seed: int, n_lo: int = 32, n_hi: int = 4096,
     above 1024 bodies are scaled with W estimated from 2e5 sampled pairs.
     Every cluster draws from its own counter-based streams, so ``workers`` > 1
     (processes started by spawn) gives the same clusters."""
-    c = np.arange(n_clusters, dtype=np.int64)
-    un = rng.uniform(seed, _S_ENS_N, c)
-    sizes = np.floor(np.exp(math.log(n_lo) + un * (math.log(n_hi + 1) - math.log(n_lo)))).astype(np.int64)
-    sizes = np.clip(sizes, n_lo, n_hi)
-    uq = rng.uniform(seed, _S_ENS_Q, c)
-    jobs = [(int(sizes[ci]), (seed * 1000003 + ci) & 0x7FFFFFFFFFFFFFFF,
-             float(q_lo + uq[ci] * (q_hi - q_lo))) for ci in range(n_clusters)]
+    jobs = _ensemble_jobs(n_clusters, seed, n_lo, n_hi, q_lo, q_hi)
     if workers > 1 and n_clusters > 1:
         import multiprocessing
         with multiprocessing.get_context("spawn").Pool(workers) as pool:

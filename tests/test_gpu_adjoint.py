@@ -131,7 +131,7 @@ def test_gradient_matches_gpu_fp64_finite_differences(nb):
         assert an == pytest.approx(fd, rel=1e-6, abs=1e-8)
 
 
-def test_autograd_function_loss_backward(nb):
+def test_autograd_function_loss_backward(nb, monkeypatch):
     torch = pytest.importorskip("torch")
     from paper_cs_0702135_gb300.autograd import hermite_trajectory
     n, eps, level, steps = 128, 1 / 256, 8, 16
@@ -140,12 +140,88 @@ def test_autograd_function_loss_backward(nb):
     x0 = torch.from_numpy(x).cuda().requires_grad_(True)
     v0 = torch.from_numpy(v).cuda().requires_grad_(True)
     mm = torch.from_numpy(m).cuda().requires_grad_(True)
-    xT, vT = hermite_trajectory(x0, v0, mm, eps, level, steps, 4, nb.NB_FP64)
-    loss = ((xT - tgt) ** 2).sum()
-    loss.backward()
+    # the Function must stay on the device: the host-array entry points and
+    # host copies of CUDA tensors are unavailable while it runs
+    def host_path(*a, **k):
+        raise AssertionError("host round trip inside hermite_trajectory")
+    with monkeypatch.context() as mp:
+        for name in ("nb_init", "nb_get_state", "nb_traj_backward", "nb_set_state"):
+            mp.setattr(nb.nb, name, host_path)
+        mp.setattr(torch.Tensor, "cpu", host_path)
+        mp.setattr(torch.Tensor, "numpy", host_path)
+        xT, vT = hermite_trajectory(x0, v0, mm, eps, level, steps, 4, nb.NB_FP64)
+        assert xT.is_cuda and vT.is_cuda
+        loss = ((xT - tgt) ** 2).sum()
+        loss.backward()
+    assert x0.grad.is_cuda and mm.grad.is_cuda
     xt, _ = oracle.traj_final(m, x, v, eps, 2.0 ** -level, steps)
     _, _, oxb, ovb, omb = oracle.traj_vjp(m, x, v, eps, 2.0 ** -level, steps,
                                           2 * (xt - tgt.cpu().numpy()), np.zeros((n, 3)))
     assert _rel(x0.grad.cpu().numpy(), oxb) < 1e-9
     assert _rel(v0.grad.cpu().numpy(), ovb) < 1e-9
     assert _rel(mm.grad.cpu().numpy(), omb) < 1e-9
+    # the library context is released after the first backward: a second
+    # backward through the same trajectory is refused
+    x1 = torch.from_numpy(x).cuda().requires_grad_(True)
+    xT2, _ = hermite_trajectory(x1, v0.detach(), mm.detach(), eps, level, steps, 4, nb.NB_FP64)
+    l2 = (xT2 ** 2).sum()
+    l2.backward(retain_graph=True)
+    with pytest.raises(RuntimeError):
+        l2.backward()
+
+
+def test_device_init_and_state_match_the_host_entry_points(nb):
+    torch = pytest.importorskip("torch")
+    n, eps = 700, 1 / 256
+    m, x, v = plummer(n, 99)
+    a = nb.Context(m, x, v, eps)
+    b = nb.Context.from_device(torch.from_numpy(m).cuda(), torch.from_numpy(x).cuda(),
+                               torch.from_numpy(v).cuda(), eps)
+    try:
+        for c in (a, b):
+            c.nb_run(1.0 / 16)
+        sa = a.nb_get_state()
+        d = {k: torch.empty((n, 3), dtype=torch.float64, device="cuda") for k in "xvak"}
+        dt = torch.empty(n, dtype=torch.int64, device="cuda")
+        dl = torch.empty(n, dtype=torch.int32, device="cuda")
+        b.nb_get_state_dev(d["x"], d["v"], d["a"], d["k"], dt, dl)
+        torch.cuda.synchronize()
+        for k in "xvak":
+            assert np.array_equal(d[k].cpu().numpy(), sa[k]), k
+        assert np.array_equal(dt.cpu().numpy(), sa["t"]) and np.array_equal(dl.cpu().numpy(), sa["level"])
+    finally:
+        a.nb_free()
+        b.nb_free()
+    bad = torch.from_numpy(x).cuda()
+    bad[5, 1] = float("nan")
+    with pytest.raises(nb.NbError) as ei:
+        nb.Context.from_device(torch.from_numpy(m).cuda(), bad, torch.from_numpy(v).cuda(), eps)
+    assert ei.value.code == nb.NB_EINVAL
+    neg = torch.from_numpy(m).cuda()
+    neg[3] = -1.0
+    with pytest.raises(nb.NbError):
+        nb.Context.from_device(neg, torch.from_numpy(x).cuda(), torch.from_numpy(v).cuda(), eps)
+
+
+def test_traj_backward_dev_matches_host(nb):
+    torch = pytest.importorskip("torch")
+    n, eps = 200, 1 / 256
+    m, x, v = plummer(n, 101)
+    r = np.random.default_rng(5)
+    xb, vb = r.normal(size=(n, 3)), r.normal(size=(n, 3))
+    c = _ctx(nb, m, x, v, eps, nb.NB_DS, level=9)
+    try:
+        c.nb_traj_forward(24, 8)
+        host = c.nb_traj_backward(xb, vb)
+        out = [torch.empty((n, 3), dtype=torch.float64, device="cuda") for _ in range(2)]
+        out.append(torch.empty(n, dtype=torch.float64, device="cuda"))
+        c.nb_traj_backward_dev(torch.from_numpy(xb).cuda(), torch.from_numpy(vb).cuda(), *out)
+        for g, h in zip(out, host):
+            assert np.array_equal(g.cpu().numpy(), h)
+        bad = torch.from_numpy(xb).cuda()
+        bad[0, 0] = float("inf")
+        with pytest.raises(nb.NbError) as ei:
+            c.nb_traj_backward_dev(bad, None, *out)
+        assert ei.value.code == nb.NB_EINVAL
+    finally:
+        c.nb_free()

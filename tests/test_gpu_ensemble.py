@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
-from synth import ensemble, plummer
+from synth import ensemble, ensemble_member, plummer
 from nbtest import TOL_DS, assert_force_close, nb, pair_magnitudes  # noqa: F401
 
 pytestmark = pytest.mark.gpu
@@ -135,6 +135,34 @@ def test_energy_over_one_time_unit_vs_oracle_runs(nb):
         assert abs(st["steps"][c] - steps) <= 0.05 * steps + 5
     # launches go out in batches of 32 between completion checks
     assert st["steps"].max() + 1 <= launches < st["steps"].max() + 1 + 32
+
+
+def test_energy_outliers_match_the_oracle(nb):
+    # The clusters of the 4096-cluster benchmark ensemble (seed 5) whose energy
+    # the GPU conserves worst (358 and 114 bodies; close pairs of massive
+    # stars, the encounters Section 2 leaves out), next to two ordinary ones.
+    # The oracle's FP64 integrator must show the same error on the same
+    # cluster: the outliers are the method's, not the GPU's.
+    picks = (2923, 1231, 7, 100)
+    cl = [ensemble_member(4096, 5, ci) for ci in picks]
+    off, m, x, v = _flatten(cl)
+    e = nb.Ensemble(off, m, x, v, EPS)
+    try:
+        k0, p0 = e.nb_ens_energy()
+        e.nb_ens_run(1.0)
+        k1, p1 = e.nb_ens_energy()
+    finally:
+        e.nb_ens_free()
+    for c, (mc, xc, vc) in enumerate(cl):
+        it = oracle.Integrator(mc, xc, vc, EPS, nthreads=8)
+        E0 = it.energy()
+        it.run(1.0)
+        d_orc = abs(it.energy() - E0) / abs(E0)
+        d_gpu = abs(k1[c] + p1[c] - (k0[c] + p0[c])) / abs(k0[c] + p0[c])
+        assert d_gpu <= max(1e-6, 3 * d_orc), (picks[c], d_gpu, d_orc)
+        if c < 2:
+            # a real outlier of the integrator, reproduced within a factor 3
+            assert d_orc > 1e-5 and d_gpu >= d_orc / 3, (picks[c], d_gpu, d_orc)
 
 
 def test_matches_single_system_path(nb):

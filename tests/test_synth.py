@@ -4,7 +4,7 @@ import math
 import numpy as np
 import pytest
 
-from synth import plummer, rng, sample_active, salpeter_masses, ensemble
+from synth import plummer, rng, sample_active, salpeter_masses, ensemble, ensemble_member
 from synth.plummer import LENGTH_UNIT, kinetic_energy, unsoftened_potential_energy
 
 
@@ -104,4 +104,12 @@ def test_ensemble_workers_give_the_same_clusters():
     assert len(seq) == len(par)
     for a, b in zip(seq, par):
         for p, q in zip(a, b):
+            assert np.array_equal(p, q)
+
+
+def test_ensemble_member_is_the_same_cluster():
+    full = ensemble(9, 6, n_lo=32, n_hi=700)
+    for ci in (0, 4, 8):
+        one = ensemble_member(9, 6, ci, n_lo=32, n_hi=700)
+        for p, q in zip(full[ci], one):
             assert np.array_equal(p, q)
