@@ -78,6 +78,9 @@ def parse_args():
     p.add_argument("--n-max", type=int, default=524288, help="replay: largest N of the ladder")
     p.add_argument("--baseline-sample", type=int, default=32,
                    help="ensemble: clusters timed one by one through the single-system path")
+    p.add_argument("--ens-config", default="",
+                   help="ensemble: 'threads,gmax' instead of the autotuner (e.g. for a profiler run, "
+                        "under which the tuner's timings are distorted)")
     p.add_argument("--oracle-outliers", type=int, default=0,
                    help="ensemble: re-run this many worst clusters (<= 512 bodies) with the oracle")
     p.add_argument("--oracle-n", type=int, default=1024, help="adjoint: size of the CPU FP64 comparison")
@@ -887,11 +890,12 @@ def run_ensemble(args):
     import torch
     import paper_cs_0702135_gb300 as nb
     torch.cuda.set_device(0)
+    fixed = tuple(int(q) for q in args.ens_config.split(",")) if args.ens_config else None
     print(json.dumps(ensemble_config(nb, torch, args.clusters, args.baseline_sample,
-                                     oracle_outliers=args.oracle_outliers)), flush=True)
+                                     oracle_outliers=args.oracle_outliers, fixed=fixed)), flush=True)
 
 
-def ensemble_config(nb, torch, C, baseline_sample, oracle_outliers=0, oracle_n_max=512):
+def ensemble_config(nb, torch, C, baseline_sample, oracle_outliers=0, oracle_n_max=512, fixed=None):
     from synth import ensemble
     t0 = time.perf_counter()
     cl = ensemble(C, 5, workers=min(16, os.cpu_count() or 1))
@@ -904,7 +908,12 @@ def ensemble_config(nb, torch, C, baseline_sample, oracle_outliers=0, oracle_n_m
     v = np.concatenate([c[2] for c in cl])
     eps = 1.0 / 256
     e = nb.Ensemble(off, m, x, v, eps)
-    th, gm, ms_tuned = e.nb_ens_tune(10)
+    if fixed:
+        th, gm = fixed
+        e.nb_ens_configure(th, gm)
+        ms_tuned = None
+    else:
+        th, gm, ms_tuned = e.nb_ens_tune(10)
     k0, p0 = e.nb_ens_energy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
