@@ -395,3 +395,41 @@ def test_block_steps_at_65536_bodies(nb):
                            "after 160 block steps")
     finally:
         nb.nb_free(ctx)
+
+
+def test_corrector_bit_exact_around_the_quad_threshold(nb):
+    # Blocks of up to 16 x SMs particles are corrected by four lanes per
+    # particle, larger ones by one thread each; on both sides of the switch
+    # (and well above it) the corrector and the new levels must equal the
+    # oracle's bit for bit, given the same new acceleration and jerk.
+    torch = pytest.importorskip("torch")
+    qmax = 16 * torch.cuda.get_device_properties(0).multi_processor_count
+    n = qmax + 700
+    m, x, v = plummer(n, 31)
+    it = oracle.Integrator(m, x, v, EPS)
+    lev = np.full(n, 10, dtype=np.int32)
+    t0 = np.zeros(n, dtype=np.int64)
+    tn = 1 << 30                       # one step of 2^-10
+    rng = np.random.default_rng(41)
+    for na in (qmax - 1, qmax, qmax + 1, qmax + 600):
+        act = np.sort(rng.choice(n, na, replace=False)).astype(np.int32)
+        anew = it.a[act] * (1.0 + 1e-3 * rng.normal(size=(na, 3)))
+        knew = it.k[act] * (1.0 + 1e-2 * rng.normal(size=(na, 3)))
+        ctx = nb.nb_init(m, x, v, EPS, nb.nb_default_opts(flags=nb.NB_INIT_NO_FORCE))
+        try:
+            nb.nb_set_state(ctx, it.x, it.v, it.a, it.k, t0, lev)
+            nb.nb_correct(ctx, act, tn / T, acc=anew, jerk=knew)
+            st = nb.nb_get_state(ctx)
+        finally:
+            nb.nb_free(ctx)
+        dt = tn / T
+        for q in range(0, na, max(1, na // 300)):
+            i = act[q]
+            xp, vp = oracle.predict_one(it.x[i], it.v[i], it.a[i], it.k[i], dt)
+            xc, vc, a2, a3 = oracle.correct_one(xp, vp, it.a[i], it.k[i], anew[q], knew[q], dt)
+            assert np.array_equal(st["x"][i], xc) and np.array_equal(st["v"][i], vc), (na, i)
+            assert np.array_equal(st["a"][i], anew[q]) and st["t"][i] == tn
+            rc, kq = oracle.level_of(oracle.aarseth_dt(anew[q], knew[q], a2, a3, dt, 0.01), 3)
+            assert rc == 0 and st["level"][i] == oracle.next_level(10, kq, tn, 3), (na, i)
+        rest = np.setdiff1d(np.arange(n), act)
+        assert np.array_equal(st["x"][rest], it.x[rest]) and np.all(st["level"][rest] == 10)
