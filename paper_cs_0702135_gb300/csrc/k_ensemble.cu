@@ -70,9 +70,7 @@ struct EnsArgs {
     int qcap;                 // queue capacity: P + C (at most n_c + 1 items per cluster)
     int *pred_left;           // [C] prediction chunks of the cluster not yet done
     float4 *jph, *jpl, *jv;   // [P] predicted double-single records
-    // [P] single-precision mirror of the FP64 state for the j predictor:
-    // position as double-single (x_hi + mass, x_lo), velocity, acceleration, jerk
-    float4 *mh, *ml, *mv, *ma, *mk;
+    Mirror mir;               // [P] single-precision mirror of the FP64 state for the j predictor
     int *act;                 // [P] active particles of each cluster (local indices)
     int *na;                  // [C] block sizes
     long long *tnext;         // [C] block times
@@ -104,58 +102,21 @@ struct MinLL {
 
 enum EnsMode { kEnsStep = 0, kEnsForce = 1, kEnsInit = 2 };
 
-// (hi, lo) += d in double-single: TwoSum of hi and d, then renormalised.
-__device__ __forceinline__ void ds_add_f(float hi, float lo, float d, float &ho, float &lout)
-{
-    const float s = hi + d;
-    const float bb = s - hi;
-    const float e = (hi - (s - bb)) + (d - bb);
-    const float l2 = lo + e;
-    ho = s + l2;
-    lout = l2 - (ho - s);
-}
-
-// j record of particle gi at block time tn from the single-precision mirror:
-// the predictor's Taylor increments (Section 2) in FP32,
-//   dx = (v + (dt/2)(a + (dt/3) k)) dt,   v_p = v + (a + (dt/2) k) dt,
-// and the position accumulated in double-single, x_p = (x_hi + x_lo) + dx.
-// The FP64 state itself is predicted in FP64 by the corrector.
+// j record of particle gi at block time tn from the single-precision mirror
+// (predict_j32: FP32 Taylor increments, double-single position add).  The FP64
+// state itself is predicted in FP64 by the corrector.
 __device__ __forceinline__ void ens_predict_j32(const EnsArgs &ea, long long gi, long long tn)
 {
-    const float dt = (float)(tn - ea.s.t[gi]) * 0x1p-40f;
-    const float h = 0.5f * dt, q = dt * (1.0f / 3.0f);
-    const float4 xh = ea.mh[gi], xl = ea.ml[gi], v = ea.mv[gi], a = ea.ma[gi], k = ea.mk[gi];
     float4 ph, pl, pv;
-    ds_add_f(xh.x, xl.x, fmaf(h, fmaf(q, k.x, a.x), v.x) * dt, ph.x, pl.x);
-    ds_add_f(xh.y, xl.y, fmaf(h, fmaf(q, k.y, a.y), v.y) * dt, ph.y, pl.y);
-    ds_add_f(xh.z, xl.z, fmaf(h, fmaf(q, k.z, a.z), v.z) * dt, ph.z, pl.z);
-    pv.x = fmaf(fmaf(h, k.x, a.x), dt, v.x);
-    pv.y = fmaf(fmaf(h, k.y, a.y), dt, v.y);
-    pv.z = fmaf(fmaf(h, k.z, a.z), dt, v.z);
-    ph.w = xh.w;
-    pl.w = 0.0f;
-    pv.w = 0.0f;
+    predict_j32(ea.mir, gi, tn - ea.s.t[gi], ph, pl, pv);
     ea.jph[gi] = ph;
     ea.jpl[gi] = pl;
     ea.jv[gi] = pv;
 }
 
-// The single-precision mirror of particle gi from its FP64 state.
 __device__ __forceinline__ void ens_write_mirror(const EnsArgs &ea, long long gi)
 {
-    const State &S = ea.s;
-    const long long P = S.n;
-    float hi[3], lo[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) split_ds(S.x[c * P + gi], hi[c], lo[c]);
-    ea.mh[gi] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(S.m[gi]));
-    ea.ml[gi] = make_float4(lo[0], lo[1], lo[2], 0.0f);
-    ea.mv[gi] = make_float4(__double2float_rn(S.v[gi]), __double2float_rn(S.v[P + gi]),
-                            __double2float_rn(S.v[2 * P + gi]), 0.0f);
-    ea.ma[gi] = make_float4(__double2float_rn(S.a[gi]), __double2float_rn(S.a[P + gi]),
-                            __double2float_rn(S.a[2 * P + gi]), 0.0f);
-    ea.mk[gi] = make_float4(__double2float_rn(S.k[gi]), __double2float_rn(S.k[P + gi]),
-                            __double2float_rn(S.k[2 * P + gi]), 0.0f);
+    write_mirror(ea.s, ea.mir, gi, ea.s.n);
 }
 
 __global__ void k_ens_mirror(EnsArgs ea)
@@ -636,11 +597,11 @@ EnsArgs ens_args(nb_ens *e)
     a.jph = e->d_jph;
     a.jpl = e->d_jpl;
     a.jv = e->d_jv;
-    a.mh = e->d_mirror;
-    a.ml = e->d_mirror + e->P;
-    a.mv = e->d_mirror + 2 * e->P;
-    a.ma = e->d_mirror + 3 * e->P;
-    a.mk = e->d_mirror + 4 * e->P;
+    a.mir.h = e->d_mirror;
+    a.mir.l = e->d_mirror + e->P;
+    a.mir.v = e->d_mirror + 2 * e->P;
+    a.mir.a = e->d_mirror + 3 * e->P;
+    a.mir.k = e->d_mirror + 4 * e->P;
     a.act = e->d_act;
     a.na = e->d_na;
     a.tnext = e->d_tnext;

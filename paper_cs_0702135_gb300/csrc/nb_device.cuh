@@ -235,6 +235,65 @@ __device__ __forceinline__ bool correct_particle(const State &s, long long i, lo
     return ok;
 }
 
+// ---------------------------------------------------------------------------
+// Single-precision mirror of the FP64 state, for j records predicted with FP32
+// Taylor increments: position as double-single (x_hi + mass, x_lo), velocity,
+// acceleration and jerk in FP32, as five float4 arrays of the particle count.
+struct Mirror {
+    float4 *h, *l, *v, *a, *k;
+};
+
+// The mirror of particle i from its FP64 state (component-major, stride n).
+template <bool CG = false>
+__device__ __forceinline__ void write_mirror(const State &s, const Mirror &mr, long long i, long long n)
+{
+    float hi[3], lo[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) split_ds(ldst<CG>(&s.x[c * n + i]), hi[c], lo[c]);
+    mr.h[i] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(ldst<CG>(&s.m[i])));
+    mr.l[i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+    mr.v[i] = make_float4(__double2float_rn(ldst<CG>(&s.v[i])), __double2float_rn(ldst<CG>(&s.v[n + i])),
+                          __double2float_rn(ldst<CG>(&s.v[2 * n + i])), 0.0f);
+    mr.a[i] = make_float4(__double2float_rn(ldst<CG>(&s.a[i])), __double2float_rn(ldst<CG>(&s.a[n + i])),
+                          __double2float_rn(ldst<CG>(&s.a[2 * n + i])), 0.0f);
+    mr.k[i] = make_float4(__double2float_rn(ldst<CG>(&s.k[i])), __double2float_rn(ldst<CG>(&s.k[n + i])),
+                          __double2float_rn(ldst<CG>(&s.k[2 * n + i])), 0.0f);
+}
+
+// (hi, lo) + d in double-single: TwoSum of hi and d, then renormalised.
+__device__ __forceinline__ void ds_add_f(float hi, float lo, float d, float &ho, float &lout)
+{
+    const float s = hi + d;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (d - bb);
+    const float l2 = lo + e;
+    ho = s + l2;
+    lout = l2 - (ho - s);
+}
+
+// j record of particle i, dt ticks after its own time, from the mirror: the
+// predictor's Taylor increments (Section 2) in FP32,
+//   dx = (v + (dt/2)(a + (dt/3) k)) dt,   v_p = v + (a + (dt/2) k) dt,
+// and the position accumulated in double-single, x_p = (x_hi + x_lo) + dx.
+template <bool CG = false>
+__device__ __forceinline__ void predict_j32(const Mirror &mr, long long i, long long dt_ticks,
+                                            float4 &ph, float4 &pl, float4 &pv)
+{
+    const float dt = (float)dt_ticks * 0x1p-40f;
+    const float h = 0.5f * dt, q = dt * (1.0f / 3.0f);
+    const float4 xh = ldst<CG>(&mr.h[i]), xl = ldst<CG>(&mr.l[i]), v = ldst<CG>(&mr.v[i]),
+                 a = ldst<CG>(&mr.a[i]), k = ldst<CG>(&mr.k[i]);
+    ds_add_f(xh.x, xl.x, fmaf(h, fmaf(q, k.x, a.x), v.x) * dt, ph.x, pl.x);
+    ds_add_f(xh.y, xl.y, fmaf(h, fmaf(q, k.y, a.y), v.y) * dt, ph.y, pl.y);
+    ds_add_f(xh.z, xl.z, fmaf(h, fmaf(q, k.z, a.z), v.z) * dt, ph.z, pl.z);
+    pv.x = fmaf(fmaf(h, k.x, a.x), dt, v.x);
+    pv.y = fmaf(fmaf(h, k.y, a.y), dt, v.y);
+    pv.z = fmaf(fmaf(h, k.z, a.z), dt, v.z);
+    ph.w = xh.w;
+    pl.w = 0.0f;
+    pv.w = 0.0f;
+}
+
 // correct_particle spread over the four lanes of a quad (lanes 4u .. 4u+3 of
 // a warp), for blocks too small to fill the GPU: the corrector is a chain of
 // FP64 operations, and on the GB300 an FP64 warp instruction occupies the SM's
