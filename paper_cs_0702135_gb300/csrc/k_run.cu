@@ -364,39 +364,59 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
             const int kn = (int)min((long long)kRunNT, cnt_r - k0);
             for (int k = warp; k < kn; k += kRunNT / 32) {
                 const long long a = r + (long long)ra.ncta * (k0 + k);
+                // a CTA's seven partials of a particle are contiguous: a lane
+                // loads all seven of each of its CTAs at once, so the loads
+                // of every component are in flight together
                 if (MODE == NB_SUM_FIXED) {
                     const long long *part = reinterpret_cast<const long long *>(ra.part);
+                    long long hi[7];
+                    unsigned long long lo[7];
+#pragma unroll
+                    for (int c = 0; c < 7; ++c) hi[c] = 0, lo[c] = 0;
+                    for (int q = lane; q < ra.ncta; q += 32) {
+                        const long long *pp = part + 2 * (((long long)q * n + a) * kComp);
+                        long long ph[7], pl[7];
+#pragma unroll
+                        for (int c = 0; c < 7; ++c) ph[c] = __ldcg(&pp[2 * c]), pl[c] = __ldcg(&pp[2 * c + 1]);
+#pragma unroll
+                        for (int c = 0; c < 7; ++c) {
+                            const unsigned long long l2 = lo[c] + (unsigned long long)pl[c];
+                            hi[c] += ph[c] + (l2 < lo[c] ? 1 : 0);
+                            lo[c] = l2;
+                        }
+                    }
 #pragma unroll
                     for (int c = 0; c < 7; ++c) {
-                        long long hi = 0;
-                        unsigned long long lo = 0;
-                        for (int q = lane; q < ra.ncta; q += 32) {
-                            const long long *pp = part + 2 * (((long long)q * n + a) * kComp + c);
-                            const unsigned long long l2 = lo + (unsigned long long)__ldcg(&pp[1]);
-                            hi += __ldcg(&pp[0]) + (l2 < lo ? 1 : 0);
-                            lo = l2;
-                        }
 #pragma unroll
                         for (int o = 16; o >= 1; o >>= 1) {
-                            const long long h2 = __shfl_xor_sync(kFullR, hi, o);
-                            const unsigned long long l2 = __shfl_xor_sync(kFullR, lo, o);
-                            const unsigned long long ls = lo + l2;
-                            hi += h2 + (ls < lo ? 1 : 0);
-                            lo = ls;
+                            const long long h2 = __shfl_xor_sync(kFullR, hi[c], o);
+                            const unsigned long long l2 = __shfl_xor_sync(kFullR, lo[c], o);
+                            const unsigned long long ls = lo[c] + l2;
+                            hi[c] += h2 + (ls < lo[c] ? 1 : 0);
+                            lo[c] = ls;
                         }
                         if (lane == 0)
-                            s_res[k][c] = __dmul_rn(i128_to_double(hi, lo),
+                            s_res[k][c] = __dmul_rn(i128_to_double(hi[c], lo[c]),
                                                     c < 3 ? Sc.inv[0] : (c < 6 ? Sc.inv[1] : Sc.inv[2]));
                     }
                 } else {
+                    // per component the same order as before: CTAs lane,
+                    // lane + 32, ... in turn, then the fixed xor tree
+                    double sum[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                    for (int q = lane; q < ra.ncta; q += 32) {
+                        const double *pp = ra.part + ((long long)q * n + a) * kComp;
+                        double v[7];
+#pragma unroll
+                        for (int c = 0; c < 7; ++c) v[c] = __ldcg(&pp[c]);
+#pragma unroll
+                        for (int c = 0; c < 7; ++c) sum[c] += v[c];
+                    }
 #pragma unroll
                     for (int c = 0; c < 7; ++c) {
-                        double sum = 0.0;
-                        for (int q = lane; q < ra.ncta; q += 32)
-                            sum += __ldcg(&ra.part[((long long)q * n + a) * kComp + c]);
+                        double t = sum[c];
 #pragma unroll
-                        for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(kFullR, sum, o);
-                        if (lane == 0) s_res[k][c] = sum;
+                        for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(kFullR, t, o);
+                        if (lane == 0) s_res[k][c] = t;
                     }
                 }
             }
