@@ -234,6 +234,7 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
     __shared__ int s_wtot[kRunNT / 32];
     __shared__ int s_ok, s_err;
     __shared__ double s_res[kRunNT][kComp];   // phase 5: combined force of this CTA's block particles
+    __shared__ int s_idx[kRunNT];              // phase 5: their particle indices
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, r = blockIdx.x;
     const State &S = ra.s;
     const int n = ra.n;
@@ -261,9 +262,29 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
         }
         if (!grid_barrier(ra, target, &s_ok)) return;
 
-        // 2. block time, stop decision, offsets, block list, prediction
-        long long tn = LLONG_MAX;
-        for (int q = tid; q < ra.ncta; q += kRunNT) tn = min(tn, __ldcg(&ra.mins[q]));
+        // 2. block time, stop decision, offsets, block list, prediction.  The
+        // state the prediction reads does not depend on the block time, and
+        // each CTA's minimum and count are read once: all go out first.
+        long long p_t = 0;
+        double p_x[3], p_v[3], p_a[3], p_k[3];
+        if (tid < m) {
+            const int i = i0 + tid;
+            p_t = __ldcg(&S.t[i]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                p_x[c] = __ldcg(&S.x[c * n + i]);
+                p_v[c] = __ldcg(&S.v[c * n + i]);
+                p_a[c] = __ldcg(&S.a[c * n + i]);
+                p_k[c] = __ldcg(&S.k[c * n + i]);
+            }
+        }
+        long long m_own = LLONG_MAX, c_own = 0;  // CTA tid's minimum and count
+        if (tid < ra.ncta) {
+            m_own = __ldcg(&ra.mins[tid]);
+            c_own = __ldcg(&ra.counts[tid]);
+        }
+        long long tn = m_own;
+        for (int q = tid + kRunNT; q < ra.ncta; q += kRunNT) tn = min(tn, __ldcg(&ra.mins[q]));
         tn = cta_reduce_r(tn, MinR(), s_red);
         if (tid == 0) s_err = *(volatile int *)&ra.ctrl->err;
         __syncthreads();
@@ -274,8 +295,9 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
             }
             return;
         }
-        long long off = 0, na = 0;
-        for (int q = tid; q < ra.ncta; q += kRunNT) {
+        long long na = m_own == tn ? c_own : 0;
+        long long off = tid < r ? na : 0;
+        for (int q = tid + kRunNT; q < ra.ncta; q += kRunNT) {
             const long long cq = __ldcg(&ra.mins[q]) == tn ? (long long)__ldcg(&ra.counts[q]) : 0;
             na += cq;
             off += q < r ? cq : 0;
@@ -286,8 +308,13 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
         unsigned mb = 0, vb = 0;
         if (tid < m) {
             const int i = i0 + tid;
+            // predict3's arithmetic on the state loaded above
+            const double dt = ticks_to_time(tn - p_t);
+            const double dt_h = __dmul_rn(dt, 0.5), dt_q = div_by<3>(dt);
             double xp[3], vp[3];
-            predict3<true>(S, i, n, ticks_to_time(tn - __ldcg(&S.t[i])), xp, vp);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                predict1hq(p_x[c], p_v[c], p_a[c], p_k[c], dt, dt_h, dt_q, xp[c], vp[c]);
             float h[3], l[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) split_ds(xp[c], h[c], l[c]);
@@ -364,6 +391,7 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
             const int kn = (int)min((long long)kRunNT, cnt_r - k0);
             for (int k = warp; k < kn; k += kRunNT / 32) {
                 const long long a = r + (long long)ra.ncta * (k0 + k);
+                if (lane == 0) s_idx[k] = __ldcg(&ra.act[a]);
                 // a CTA's seven partials of a particle are contiguous: a lane
                 // loads all seven of each of its CTAs at once, so the loads
                 // of every component are in flight together
@@ -429,7 +457,7 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
                     const bool active = kq < kn;
                     const int kk = active ? kq : kn - 1;
                     const int c = qd < 3 ? qd : 2;
-                    const int i = (int)__ldcg(&ra.act[r + (long long)ra.ncta * (k0 + kk)]);
+                    const int i = s_idx[kk];
                     const bool ok = correct_particle_quad<true>(S, i, n, tn, s_res[kk][c],
                                                                 s_res[kk][3 + c], ra.eta,
                                                                 ra.level_min, ra.level_fixed, active);
@@ -438,7 +466,7 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
             } else if (tid < kn) {
                 const double ap[3] = {s_res[tid][0], s_res[tid][1], s_res[tid][2]};
                 const double kp[3] = {s_res[tid][3], s_res[tid][4], s_res[tid][5]};
-                const int i = (int)__ldcg(&ra.act[r + (long long)ra.ncta * (k0 + tid)]);
+                const int i = s_idx[tid];
                 if (!correct_particle<true>(S, i, n, tn, ap, kp, ra.eta, ra.level_min, ra.level_fixed))
                     atomicCAS(&ra.ctrl->err, 0, NB_ESTEP);
             }
