@@ -3,12 +3,16 @@
 // systems small enough that a step is mostly launch latency on the
 // kernel-per-stage path.
 //
-// CTA r owns particles [r P, (r + 1) P).  One block step is four phases
+// CTA r owns particles [r P, (r + 1) P).  One block step is three phases
 // separated by grid barriers (a counter in global memory, added to with
 // release and read with acquire semantics; each wait ends after about 2 s
 // with NB_ETIMEOUT, and the cooperative launch keeps every CTA resident):
-//   1. each CTA's minimum end time t_i + 2^-lev_i over its particles and how
-//      many of them end then;
+//   1. the CTA corrects its own particles of the previous block: a warp adds a
+//      particle's partials over the CTAs (lanes over CTAs, then a fixed
+//      shuffle tree), then the FP64 corrector and Aarseth step run (four
+//      lanes per particle for up to 16 particles); the new end times
+//      t_i + 2^-lev_i of its particles, kept in shared memory, give its
+//      minimum and how many of its particles end then;
 //   2. the block time t_next = min over the CTAs (the same in every CTA, so
 //      every CTA takes the same decision to stop); a CTA has block particles
 //      exactly when its own minimum is t_next, and writes them, in ascending
@@ -16,18 +20,14 @@
 //      into the double-single j records (fixed point: its largest mass and
 //      |vx|+|vy|+|vz|);
 //   3. force partials: every CTA sums every block particle's pair terms over
-//      its own particles as j and writes them per (CTA, block particle);
-//   4. block particle a is corrected by CTA a mod (CTAs): a warp adds its
-//      partials over the CTAs (lanes over CTAs, then a fixed shuffle tree),
-//      then one thread runs the FP64 corrector and Aarseth step.  The
-//      corrector's FP64 chain is long, so spreading the block evenly keeps
-//      every CTA's share short.
-// Everything that other CTAs wrote in the same launch (state included, since
-// a particle may be corrected by any CTA) is read past L1 (__ldcg).  Two summations: the
-// compensated double-single sums (TwoSum-promoted FP32 partials, FP64 across
-// CTAs) and the GRAPE-style fixed-point sums of k_sum.cu (exact, so the run is
-// bit-identical to the kernel-per-stage path and to any IEEE evaluation of the
-// same sums).
+//      its own particles as j and writes them per (CTA, block particle).
+// Since a particle is corrected by its owner, no CTA reads another CTA's
+// state, and the correction needs no barrier of its own.
+// Everything that other CTAs wrote in the same launch is read past L1
+// (__ldcg).  Two summations: the compensated double-single sums
+// (TwoSum-promoted FP32 partials, FP64 across CTAs) and the GRAPE-style
+// fixed-point sums of k_sum.cu (exact, so the run is bit-identical to the
+// kernel-per-stage path and to any IEEE evaluation of the same sums).
 #include <climits>
 
 #include "nb_device.cuh"
@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
     __shared__ int s_ok, s_err;
     __shared__ double s_res[kRunNT][kComp];   // phase 5: combined force of this CTA's block particles
     __shared__ int s_idx[kRunNT];              // phase 5: their particle indices
+    __shared__ long long s_et[kRunNT];         // end times t_i + 2^-lev_i of this CTA's particles
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, r = blockIdx.x;
     const State &S = ra.s;
     const int n = ra.n;
@@ -243,9 +244,128 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
     unsigned long long target = 0;
     long long steps = 0;
 
+    // end times of this CTA's particles: read once here, then kept up to date
+    // by this CTA's own corrections (phase 1a)
+    if (tid < m) s_et[tid] = end_time_of(S, i0 + tid);
+    __syncthreads();
+    long long off_b = 0, cnt_b = 0, tn_b = 0;
     for (;;) {
-        // 1. own minimum end time and the particles that end then
-        const long long et = tid < m ? end_time_of(S, i0 + tid) : LLONG_MAX;
+        if (steps > 0) {
+            // 1a. The previous block's particles that this CTA owns (block
+            // positions off_b .. off_b + cnt_b - 1): partials in CTA order,
+            // corrector, new steps, and their new end times into s_et.
+            Scale Sc;
+            bool scale_ok = true;
+            if (MODE == NB_SUM_FIXED) {
+                unsigned bm = 0, bv = 0;
+                for (int q = tid; q < ra.ncta; q += kRunNT) {
+                    bm = max(bm, __ldcg(&ra.maxs[2 * q]));
+                    bv = max(bv, __ldcg(&ra.maxs[2 * q + 1]));
+                }
+                bm = cta_reduce_r(bm, MaxU(), s_redu);
+                bv = cta_reduce_r(bv, MaxU(), s_redu);
+                const unsigned bounds[2] = {bm, bv};
+                scale_ok = fixed_scale(bounds, ra.eps2f, Sc);
+            }
+            // warp w adds the partials of particles k = w, w + 8, ... over the CTAs
+            // (lane l takes CTAs l, l + 32, ... in order, then a fixed xor tree;
+            // exact in fixed point), then the particles are corrected
+            const long long cnt_r = cnt_b;
+            for (long long k0 = 0; scale_ok && k0 < cnt_r; k0 += kRunNT) {
+                const int kn = (int)min((long long)kRunNT, cnt_r - k0);
+                for (int k = warp; k < kn; k += kRunNT / 32) {
+                    const long long a = off_b + k0 + k;
+                    if (lane == 0) s_idx[k] = __ldcg(&ra.act[a]);
+                    // a CTA's seven partials of a particle are contiguous: a lane
+                    // loads all seven of each of its CTAs at once, so the loads
+                    // of every component are in flight together
+                    if (MODE == NB_SUM_FIXED) {
+                        const long long *part = reinterpret_cast<const long long *>(ra.part);
+                        long long hi[7];
+                        unsigned long long lo[7];
+#pragma unroll
+                        for (int c = 0; c < 7; ++c) hi[c] = 0, lo[c] = 0;
+                        for (int q = lane; q < ra.ncta; q += 32) {
+                            const long long *pp = part + 2 * (((long long)q * n + a) * kComp);
+                            long long ph[7], pl[7];
+#pragma unroll
+                            for (int c = 0; c < 7; ++c) ph[c] = __ldcg(&pp[2 * c]), pl[c] = __ldcg(&pp[2 * c + 1]);
+#pragma unroll
+                            for (int c = 0; c < 7; ++c) {
+                                const unsigned long long l2 = lo[c] + (unsigned long long)pl[c];
+                                hi[c] += ph[c] + (l2 < lo[c] ? 1 : 0);
+                                lo[c] = l2;
+                            }
+                        }
+#pragma unroll
+                        for (int c = 0; c < 7; ++c) {
+#pragma unroll
+                            for (int o = 16; o >= 1; o >>= 1) {
+                                const long long h2 = __shfl_xor_sync(kFullR, hi[c], o);
+                                const unsigned long long l2 = __shfl_xor_sync(kFullR, lo[c], o);
+                                const unsigned long long ls = lo[c] + l2;
+                                hi[c] += h2 + (ls < lo[c] ? 1 : 0);
+                                lo[c] = ls;
+                            }
+                            if (lane == 0)
+                                s_res[k][c] = __dmul_rn(i128_to_double(hi[c], lo[c]),
+                                                        c < 3 ? Sc.inv[0] : (c < 6 ? Sc.inv[1] : Sc.inv[2]));
+                        }
+                    } else {
+                        // per component the same order as before: CTAs lane,
+                        // lane + 32, ... in turn, then the fixed xor tree
+                        double sum[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                        for (int q = lane; q < ra.ncta; q += 32) {
+                            const double *pp = ra.part + ((long long)q * n + a) * kComp;
+                            double v[7];
+#pragma unroll
+                            for (int c = 0; c < 7; ++c) v[c] = __ldcg(&pp[c]);
+#pragma unroll
+                            for (int c = 0; c < 7; ++c) sum[c] += v[c];
+                        }
+#pragma unroll
+                        for (int c = 0; c < 7; ++c) {
+                            double t = sum[c];
+#pragma unroll
+                            for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(kFullR, t, o);
+                            if (lane == 0) s_res[k][c] = t;
+                        }
+                    }
+                }
+                __syncthreads();
+                if (kn <= kRunQuadMax) {
+                    // few particles: four lanes each (the same FP64 operations,
+                    // about half the FP64 instructions per particle)
+                    if (warp * 8 < kn) {
+                        const int kq = tid >> 2, qd = tid & 3;
+                        const bool active = kq < kn;
+                        const int kk = active ? kq : kn - 1;
+                        const int c = qd < 3 ? qd : 2;
+                        const int i = s_idx[kk];
+                        const bool ok = correct_particle_quad<true>(S, i, n, tn_b, s_res[kk][c],
+                                                                    s_res[kk][3 + c], ra.eta,
+                                                                    ra.level_min, ra.level_fixed, active);
+                        if (active && qd == 0) {
+                            if (!ok) atomicCAS(&ra.ctrl->err, 0, NB_ESTEP);
+                            // this lane stored the new level: read back in program order
+                            s_et[i - i0] = tn_b + (1LL << (kTickBits - S.lev[i]));
+                        }
+                    }
+                } else if (tid < kn) {
+                    const double ap[3] = {s_res[tid][0], s_res[tid][1], s_res[tid][2]};
+                    const double kp[3] = {s_res[tid][3], s_res[tid][4], s_res[tid][5]};
+                    const int i = s_idx[tid];
+                    if (!correct_particle<true>(S, i, n, tn_b, ap, kp, ra.eta, ra.level_min, ra.level_fixed))
+                        atomicCAS(&ra.ctrl->err, 0, NB_ESTEP);
+                    s_et[i - i0] = tn_b + (1LL << (kTickBits - S.lev[i]));
+                }
+                __syncthreads();
+            }
+            __syncthreads();
+        }
+
+        // 1b. own minimum end time (kept in s_et) and the particles that end then
+        const long long et = tid < m ? s_et[tid] : LLONG_MAX;
         const long long mn = cta_reduce_r(et, MinR(), s_red);
         const bool at_min = tid < m && et == mn;
         const unsigned bal = __ballot_sync(kFullR, at_min);
@@ -305,6 +425,9 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
         na = cta_reduce_r(na, AddR(), s_red);
         off = cta_reduce_r(off, AddR(), s_red);
         if (at_min && mn == tn) ra.act[off + woff + __popc(bal & ((1u << lane) - 1u))] = i0 + tid;
+        off_b = off;                      // this CTA's block particles, corrected next iteration
+        cnt_b = mn == tn ? cnt_min : 0;
+        tn_b = tn;
         unsigned mb = 0, vb = 0;
         if (tid < m) {
             const int i = i0 + tid;
@@ -339,7 +462,7 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
         }
         if (!grid_barrier(ra, target, &s_ok)) return;
 
-        // 4. force partials of every block particle over this CTA's particles
+        // 3. force partials of every block particle over this CTA's particles
         if (tid < m) {
             s_p[tid] = __ldcg(&ra.j.pos_hi[i0 + tid]);
             s_l[tid] = __ldcg(&ra.j.pos_lo[i0 + tid]);
@@ -367,111 +490,6 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
         }
         if (!grid_barrier(ra, target, &s_ok)) return;
 
-        // 5. block particles a = r, r + CTAs, ...: partials in CTA order,
-        // corrector, new steps
-        Scale Sc;
-        bool scale_ok = true;
-        if (MODE == NB_SUM_FIXED) {
-            unsigned bm = 0, bv = 0;
-            for (int q = tid; q < ra.ncta; q += kRunNT) {
-                bm = max(bm, __ldcg(&ra.maxs[2 * q]));
-                bv = max(bv, __ldcg(&ra.maxs[2 * q + 1]));
-            }
-            bm = cta_reduce_r(bm, MaxU(), s_redu);
-            bv = cta_reduce_r(bv, MaxU(), s_redu);
-            const unsigned bounds[2] = {bm, bv};
-            scale_ok = fixed_scale(bounds, ra.eps2f, Sc);
-        }
-        // this CTA's block particles are a = r + CTAs * k, k = 0, 1, ...: first
-        // warp w adds the partials of particles k = w, w + 8, ... over the CTAs
-        // (lane l takes CTAs l, l + 32, ... in order, then a fixed xor tree;
-        // exact in fixed point), then thread k corrects particle k
-        const long long cnt_r = na > r ? (na - 1 - r) / ra.ncta + 1 : 0;
-        for (long long k0 = 0; scale_ok && k0 < cnt_r; k0 += kRunNT) {
-            const int kn = (int)min((long long)kRunNT, cnt_r - k0);
-            for (int k = warp; k < kn; k += kRunNT / 32) {
-                const long long a = r + (long long)ra.ncta * (k0 + k);
-                if (lane == 0) s_idx[k] = __ldcg(&ra.act[a]);
-                // a CTA's seven partials of a particle are contiguous: a lane
-                // loads all seven of each of its CTAs at once, so the loads
-                // of every component are in flight together
-                if (MODE == NB_SUM_FIXED) {
-                    const long long *part = reinterpret_cast<const long long *>(ra.part);
-                    long long hi[7];
-                    unsigned long long lo[7];
-#pragma unroll
-                    for (int c = 0; c < 7; ++c) hi[c] = 0, lo[c] = 0;
-                    for (int q = lane; q < ra.ncta; q += 32) {
-                        const long long *pp = part + 2 * (((long long)q * n + a) * kComp);
-                        long long ph[7], pl[7];
-#pragma unroll
-                        for (int c = 0; c < 7; ++c) ph[c] = __ldcg(&pp[2 * c]), pl[c] = __ldcg(&pp[2 * c + 1]);
-#pragma unroll
-                        for (int c = 0; c < 7; ++c) {
-                            const unsigned long long l2 = lo[c] + (unsigned long long)pl[c];
-                            hi[c] += ph[c] + (l2 < lo[c] ? 1 : 0);
-                            lo[c] = l2;
-                        }
-                    }
-#pragma unroll
-                    for (int c = 0; c < 7; ++c) {
-#pragma unroll
-                        for (int o = 16; o >= 1; o >>= 1) {
-                            const long long h2 = __shfl_xor_sync(kFullR, hi[c], o);
-                            const unsigned long long l2 = __shfl_xor_sync(kFullR, lo[c], o);
-                            const unsigned long long ls = lo[c] + l2;
-                            hi[c] += h2 + (ls < lo[c] ? 1 : 0);
-                            lo[c] = ls;
-                        }
-                        if (lane == 0)
-                            s_res[k][c] = __dmul_rn(i128_to_double(hi[c], lo[c]),
-                                                    c < 3 ? Sc.inv[0] : (c < 6 ? Sc.inv[1] : Sc.inv[2]));
-                    }
-                } else {
-                    // per component the same order as before: CTAs lane,
-                    // lane + 32, ... in turn, then the fixed xor tree
-                    double sum[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-                    for (int q = lane; q < ra.ncta; q += 32) {
-                        const double *pp = ra.part + ((long long)q * n + a) * kComp;
-                        double v[7];
-#pragma unroll
-                        for (int c = 0; c < 7; ++c) v[c] = __ldcg(&pp[c]);
-#pragma unroll
-                        for (int c = 0; c < 7; ++c) sum[c] += v[c];
-                    }
-#pragma unroll
-                    for (int c = 0; c < 7; ++c) {
-                        double t = sum[c];
-#pragma unroll
-                        for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(kFullR, t, o);
-                        if (lane == 0) s_res[k][c] = t;
-                    }
-                }
-            }
-            __syncthreads();
-            if (kn <= kRunQuadMax) {
-                // few particles: four lanes each (the same FP64 operations,
-                // about half the FP64 instructions per particle)
-                if (warp * 8 < kn) {
-                    const int kq = tid >> 2, qd = tid & 3;
-                    const bool active = kq < kn;
-                    const int kk = active ? kq : kn - 1;
-                    const int c = qd < 3 ? qd : 2;
-                    const int i = s_idx[kk];
-                    const bool ok = correct_particle_quad<true>(S, i, n, tn, s_res[kk][c],
-                                                                s_res[kk][3 + c], ra.eta,
-                                                                ra.level_min, ra.level_fixed, active);
-                    if (active && qd == 0 && !ok) atomicCAS(&ra.ctrl->err, 0, NB_ESTEP);
-                }
-            } else if (tid < kn) {
-                const double ap[3] = {s_res[tid][0], s_res[tid][1], s_res[tid][2]};
-                const double kp[3] = {s_res[tid][3], s_res[tid][4], s_res[tid][5]};
-                const int i = s_idx[tid];
-                if (!correct_particle<true>(S, i, n, tn, ap, kp, ra.eta, ra.level_min, ra.level_fixed))
-                    atomicCAS(&ra.ctrl->err, 0, NB_ESTEP);
-            }
-            __syncthreads();
-        }
         ++steps;
         if (r == 0 && tid == 0) {
             ra.ctrl->t_next = tn;
@@ -480,8 +498,6 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
             ra.ctrl->steps += 1;
             ra.ctrl->interactions += na * (long long)(n - 1);
         }
-        // the owners read the corrected state in the next step's phase 1
-        if (!grid_barrier(ra, target, &s_ok)) return;
     }
 }
 
