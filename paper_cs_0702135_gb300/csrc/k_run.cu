@@ -506,12 +506,13 @@ __global__ void __launch_bounds__(kRunNT) k_run(RunArgs ra)
 int run_layout(int n, int sms, int blocks_per_sm, int *ncta, int *per)
 {
     // 32 particles per CTA up to 64 CTAs, then up to 64 particles per CTA
-    // (64 CTAs at n = 4096), then 64 per CTA up to 128 CTAs, then 128 CTAs
-    // (measured on whole runs: more CTAs share the force and the predictor but
-    // add to every barrier and to the partials each block particle sums)
+    // (64 CTAs at n = 4096), then one CTA per SM (measured on whole runs: more
+    // CTAs share the force and the predictor but add to every barrier and to
+    // the partials each block particle sums; above 4096 bodies the force
+    // share wins)
     int p = (n + 63) / 64;
     if (p < 32) p = 32;
-    if (p > 64) p = (n + 127) / 128 > 64 ? (n + 127) / 128 : 64;
+    if (p > 64) p = (n + sms - 1) / sms;
     if (p > kRunNT) return -1;
     const int c = (n + p - 1) / p;
     if (c > sms * blocks_per_sm) return -1;
