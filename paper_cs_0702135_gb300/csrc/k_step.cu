@@ -158,45 +158,49 @@ struct SumOp {
     __device__ T operator()(T a, T b) const { return a + b; }
 };
 
-__global__ void k_sched_min(State s, long long *blockmin)
-{
-    __shared__ long long sm[kSchedNT / 32];
-    const int lo = blockIdx.x * kSchedChunk;
-    const int hi = min(s.n, lo + kSchedChunk);
-    long long m = LLONG_MAX;
-    for (int i = lo + threadIdx.x; i < hi; i += kSchedNT) m = min(m, end_time(s, i));
-    m = block_reduce(m, MinOp(), sm);
-    if (threadIdx.x == 0) blockmin[blockIdx.x] = m;
-}
-
-__global__ void k_sched_count(State s, Ctrl *ctrl, const long long *blockmin, int *blockcnt,
-                              int nblocks)
+// Per chunk its minimum end time and how many of its particles end then (a
+// chunk's count matters only if its minimum is the block time).
+__global__ void k_sched_min(State s, long long *blockmin, int *blockcnt)
 {
     __shared__ long long sm[kSchedNT / 32];
     __shared__ int si[kSchedNT / 32];
+    constexpr int kPer = kSchedChunk / kSchedNT;
+    const int lo = blockIdx.x * kSchedChunk;
+    const int hi = min(s.n, lo + kSchedChunk);
+    long long et[kPer];
+    long long m = LLONG_MAX;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int i = lo + q * kSchedNT + threadIdx.x;
+        et[q] = i < hi ? end_time(s, i) : LLONG_MAX;
+        m = min(m, et[q]);
+    }
+    m = block_reduce(m, MinOp(), sm);
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) cnt += et[q] == m;
+    cnt = block_reduce(cnt, SumOp(), si);
+    if (threadIdx.x == 0) {
+        blockmin[blockIdx.x] = m;
+        blockcnt[blockIdx.x] = cnt;
+    }
+}
+
+__global__ void k_sched_scatter(State s, Ctrl *ctrl, const long long *blockmin, const int *blockcnt,
+                                int *act, int nblocks, ForceArgs fa, ForcePlan *plan_out)
+{
+    __shared__ long long sm[kSchedNT / 32];
+    __shared__ int si[kSchedNT / 32];
+    __shared__ int wtot[kSchedNT / 32];
+    // the block time: the least chunk minimum (every CTA reduces the same values)
     long long tn = LLONG_MAX;
     for (int b = threadIdx.x; b < nblocks; b += kSchedNT) tn = min(tn, blockmin[b]);
     tn = block_reduce(tn, MinOp(), sm);
     if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->t_next = tn;
     const bool done = tn > ctrl->t_end;
-    const int lo = blockIdx.x * kSchedChunk;
-    const int hi = min(s.n, lo + kSchedChunk);
-    int cnt = 0;
+    int pre = 0;   // no block past the end time: nothing counted
     if (!done)
-        for (int i = lo + threadIdx.x; i < hi; i += kSchedNT) cnt += end_time(s, i) == tn;
-    cnt = block_reduce(cnt, SumOp(), si);
-    if (threadIdx.x == 0) blockcnt[blockIdx.x] = cnt;
-}
-
-__global__ void k_sched_scatter(State s, Ctrl *ctrl, const int *blockcnt, int *act, int nblocks,
-                                ForceArgs fa, ForcePlan *plan_out)
-{
-    __shared__ int si[kSchedNT / 32];
-    __shared__ int wtot[kSchedNT / 32];
-    const long long tn = ctrl->t_next;
-    const bool done = tn > ctrl->t_end;
-    int pre = 0;
-    for (int b = threadIdx.x; b < blockIdx.x; b += kSchedNT) pre += blockcnt[b];
+        for (int b = threadIdx.x; b < blockIdx.x; b += kSchedNT) pre += blockmin[b] == tn ? blockcnt[b] : 0;
     pre = block_reduce(pre, SumOp(), si);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lo = blockIdx.x * kSchedChunk;
@@ -375,9 +379,9 @@ int schedule_blocks(int n) { return cdiv(n, kSchedChunk); }
 void launch_schedule(const State &s, Ctrl *ctrl, long long *blockmin, int *blockcnt, int *act,
                      int nblocks, const ForceArgs &fa, ForcePlan *plan_out, cudaStream_t st)
 {
-    k_sched_min<<<nblocks, kSchedNT, 0, st>>>(s, blockmin);
-    k_sched_count<<<nblocks, kSchedNT, 0, st>>>(s, ctrl, blockmin, blockcnt, nblocks);
-    k_sched_scatter<<<nblocks, kSchedNT, 0, st>>>(s, ctrl, blockcnt, act, nblocks, fa, plan_out);
+    k_sched_min<<<nblocks, kSchedNT, 0, st>>>(s, blockmin, blockcnt);
+    k_sched_scatter<<<nblocks, kSchedNT, 0, st>>>(s, ctrl, blockmin, blockcnt, act, nblocks, fa,
+                                                   plan_out);
 }
 
 int energy_blocks(int n)

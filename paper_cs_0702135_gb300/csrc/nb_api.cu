@@ -281,7 +281,7 @@ void enqueue_step(nb_ctx *c)
     launch_correct(c->S, c->d_act, 0, &c->d_ctrl->n_active, 0, &c->d_ctrl->t_next, c->d_res,
                    c->d_res + 3LL * c->n, c->o.eta, c->o.level_min, c->o.level_fixed,
                    &c->d_ctrl->err, c->sms, c->st);
-    c->launches += 3 + 1 + 1;  // scheduler, predictor, corrector (force counted above)
+    c->launches += 2 + 1 + 1;  // scheduler, predictor, corrector (force counted above)
 }
 
 int set_t_end(nb_ctx *c, long long t_end)
