@@ -68,3 +68,23 @@ def test_oracle_blockstep_baseline_whole_run_and_projection():
     m2, x2, v2 = plummer(2048, 3)
     samp = bench.oracle_blockstep_rate(m2, x2, v2, 1.0 / 256, 3, 0.125, gpu, 1e-3)
     assert not samp["whole_run"] and "steps" not in samp and samp["value"] > 0
+
+
+def test_bench_error_metric_matches_the_parity_tests():
+    # The benchmark's accuracy figures use the per-particle metric of the
+    # parity tests: the same pair-magnitude sums, and err = |d| / max(|ref|, S/10)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from nbtest import force_errors, pair_magnitudes
+    import numpy as np
+    m, x, v = plummer(300, 41)
+    idx = np.array([0, 7, 150, 299], dtype=np.int32)
+    eps = 1.0 / 256
+    sa, sk = bench.pair_magnitude_sums(m, x, v, eps, idx, chunk=3)
+    ta, tk = pair_magnitudes(m, x, v, eps, idx)
+    assert np.allclose(sa, ta, rtol=1e-12) and np.allclose(sk, tk, rtol=1e-12)
+    r = np.random.default_rng(3)
+    ref = (r.normal(size=(4, 3)), r.normal(size=(4, 3)), -np.abs(r.normal(size=4)) - 1.0)
+    got = tuple(q * (1 + 1e-7 * r.normal(size=q.shape)) for q in ref)
+    e = bench.force_error_stats(got, ref, sa, sk)
+    ea, ek, ep = force_errors(got, ref, (sa, sk))
+    assert np.isclose(e[0], ea.max()) and np.isclose(e[1], ek.max()) and np.isclose(e[2], ep.max())
