@@ -329,42 +329,39 @@ def test_step_underflow_reports_nb_estep(nb):
         nb.nb_free(ctx)
 
 
-def test_block_steps_at_65536_bodies(nb):
-    # Config: Plummer N = 65536 (seed 2, eps = 1/256), the size of the paper's
-    # largest block-step timing.  At this scale: the start-up forces on
-    # sampled particles against the oracle, every start-up level from the
-    # oracle's initial-step rule applied to the GPU's start-up forces, and for
-    # 160 block steps the block (time and members) recomputed from the GPU's
-    # state before the step, with the corrector and the new level of sampled
-    # block members equal bit for bit to the oracle's given the GPU's new
-    # forces.  Then the force on sampled particles at the latest particle
-    # time against the oracle.
+def _block_steps_against_oracle(nb, n, seed, eps, steps, n_sample, label):
+    """Start-up forces on sampled particles against the oracle, every 97th
+    start-up level from the oracle's initial-step rule applied to the GPU's
+    start-up forces, `steps` device-driven block steps each with its block
+    (time and members) recomputed from the GPU's state before the step and the
+    corrector and new level of up to 16 block members equal bit for bit to the
+    oracle's given the GPU's new forces, then the force on sampled particles
+    at the latest particle time against the oracle."""
     from nbtest import TOL_DS, assert_force_close, pair_magnitudes
     from synth import sample_active
-    n = 65536
-    m, x, v = plummer(n, 2)
-    ctx = nb.nb_init(m, x, v, EPS)
+    m, x, v = plummer(n, seed)
+    ctx = nb.nb_init(m, x, v, eps)
     try:
         st = nb.nb_get_state(ctx)
-        idx = sample_active(n, 128, 77)
-        ref = oracle.force(m, x, v, EPS, idx, nthreads=8)
-        mags = pair_magnitudes(m, x, v, EPS, idx, chunk=16)
+        idx = sample_active(n, n_sample, 77)
+        ref = oracle.force(m, x, v, eps, idx, nthreads=8)
+        mags = pair_magnitudes(m, x, v, eps, idx, chunk=8)
         # the state holds the start-up acceleration and jerk (the potential is
         # checked after the run)
-        assert_force_close((st["a"][idx], st["k"][idx], ref[2]), ref, mags, TOL_DS, "start-up")
+        assert_force_close((st["a"][idx], st["k"][idx], ref[2]), ref, mags, TOL_DS, label + " start-up")
         for i in range(0, n, 97):
             rc, lv = oracle.level_of(oracle.initial_dt(st["a"][i], st["k"][i], 0.01), 3)
             assert rc == 0 and st["level"][i] == lv, i
         rng = np.random.default_rng(5)
         checked = 0
-        for step in range(160):
+        for step in range(steps):
             before = nb.nb_get_state(ctx)
             ends = before["t"] + (np.int64(1) << (40 - before["level"].astype(np.int64)))
             tn = ends.min()
             want = np.nonzero(ends == tn)[0]
             tb, na = nb.nb_step(ctx)
             act, tt = nb.nb_get_active(ctx)
-            assert tt == tn and na == len(want) and np.array_equal(act, want), step
+            assert tt == tn and na == len(want) and np.array_equal(act, want), (label, step)
             g = nb.nb_get_state(ctx)
             pick = want if len(want) <= 16 else rng.choice(want, 16, replace=False)
             for i in pick:
@@ -380,7 +377,7 @@ def test_block_steps_at_65536_bodies(nb):
                 checked += 1
             rest = np.setdiff1d(np.arange(n), want)[::257]
             assert np.array_equal(g["x"][rest], before["x"][rest]), step
-        assert checked >= 160
+        assert checked >= steps
         # force at the latest particle time on sampled particles
         st = nb.nb_get_state(ctx)
         t_now = int(st["t"].max())
@@ -388,13 +385,26 @@ def test_block_steps_at_65536_bodies(nb):
         xp = st["x"] + (st["v"] + (dt / 2)[:, None] * (st["a"] + (dt / 3)[:, None] * st["k"])) * dt[:, None]
         vp = st["v"] + (st["a"] + (dt / 2)[:, None] * st["k"]) * dt[:, None]
         nb.nb_predict(ctx, t_now / T)
-        idx = sample_active(n, 128, 78)
+        idx = sample_active(n, n_sample, 78)
         got = nb.nb_force(ctx, idx)
-        ref = oracle.force(m, xp, vp, EPS, idx, nthreads=8)
-        assert_force_close(got, ref, pair_magnitudes(m, xp, vp, EPS, idx, chunk=16), TOL_DS,
-                           "after 160 block steps")
+        ref = oracle.force(m, xp, vp, eps, idx, nthreads=8)
+        assert_force_close(got, ref, pair_magnitudes(m, xp, vp, eps, idx, chunk=8), TOL_DS,
+                           "%s after %d block steps" % (label, steps))
     finally:
         nb.nb_free(ctx)
+
+
+def test_block_steps_at_65536_bodies(nb):
+    # Plummer N = 65536 (seed 2, eps = 1/256), the size of the paper's largest
+    # block-step timing, through 160 device-driven block steps.
+    _block_steps_against_oracle(nb, 65536, 2, EPS, 160, 128, "65536 bodies")
+
+
+def test_block_steps_at_2p20_bodies(nb):
+    # Plummer N = 2^20 (seed 3, eps = 1/1024), the benchmark's system, through
+    # 24 device-driven block steps from t = 0 (the step launches that the
+    # benchmark's block-step configuration times).
+    _block_steps_against_oracle(nb, 1 << 20, 3, 1.0 / 1024, 24, 64, "2^20 bodies")
 
 
 def test_corrector_bit_exact_around_the_quad_threshold(nb):
