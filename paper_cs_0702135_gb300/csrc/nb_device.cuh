@@ -391,29 +391,22 @@ __device__ __forceinline__ bool correct_particle_quad(const State &s, long long 
     return ok;
 }
 
-// One FP32 pair interaction on double-single positions (Eq. 1 with the
-// attractive sign; pair terms of the Appendix A kernel), dx = x_j - x_i formed
-// as (x_j,hi - x_i,hi) + (x_j,lo - x_i,lo).  SOFT = false drops pairs at
-// r = 0; GUARD drops the pair j == i.
+// FP32 pair terms of Eq. 1 (attractive sign; pair terms of the Appendix A
+// kernel) from the separation dx = x_j - x_i and the velocity difference
+// u = v_j - v_i.  SOFT = false drops pairs at r = 0; GUARD drops the pair
+// j == i.
 template <bool SOFT, bool GUARD>
-__device__ __forceinline__ void pair_ds(const float4 &p, const float4 &l, const float4 &w,
-                                        const float xh[3], const float xl[3], const float vi[3],
-                                        float eps2, float acc[3], float jk[3], float &pot,
-                                        int j = 0, int i = 1)
+__device__ __forceinline__ void pair_terms(float dx, float dy, float dz, float ux, float uy, float uz,
+                                           float m, float eps2, float acc[3], float jk[3], float &pot,
+                                           int j, int i)
 {
-    const float dx = (p.x - xh[0]) + (l.x - xl[0]);
-    const float dy = (p.y - xh[1]) + (l.y - xl[1]);
-    const float dz = (p.z - xh[2]) + (l.z - xl[2]);
-    const float ux = w.x - vi[0];
-    const float uy = w.y - vi[1];
-    const float uz = w.z - vi[2];
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
     const float rv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
     float rinv = rsqrt_sfu(r2);
     if (!SOFT) rinv = (r2 > 0.0f) ? rinv : 0.0f;
     if (GUARD) rinv = (j == i) ? 0.0f : rinv;
     const float rinv2 = rinv * rinv;
-    const float mr = p.w * rinv;           // m_j / r
+    const float mr = m * rinv;             // m_j / r
     const float mr3 = mr * rinv2;          // m_j / r^3
     const float b = -3.0f * rv * rinv2;    // -3 (dx . dv) / r^2
     acc[0] = fmaf(mr3, dx, acc[0]);
@@ -426,6 +419,56 @@ __device__ __forceinline__ void pair_ds(const float4 &p, const float4 &l, const 
     jk[1] = fmaf(mr3, qy, jk[1]);
     jk[2] = fmaf(mr3, qz, jk[2]);
     pot -= mr;
+}
+
+// One FP32 pair interaction on double-single positions, dx = x_j - x_i formed
+// as (x_j,hi - x_i,hi) + (x_j,lo - x_i,lo).
+template <bool SOFT, bool GUARD>
+__device__ __forceinline__ void pair_ds(const float4 &p, const float4 &l, const float4 &w,
+                                        const float xh[3], const float xl[3], const float vi[3],
+                                        float eps2, float acc[3], float jk[3], float &pot,
+                                        int j = 0, int i = 1)
+{
+    const float dx = (p.x - xh[0]) + (l.x - xl[0]);
+    const float dy = (p.y - xh[1]) + (l.y - xl[1]);
+    const float dz = (p.z - xh[2]) + (l.z - xl[2]);
+    pair_terms<SOFT, GUARD>(dx, dy, dz, w.x - vi[0], w.y - vi[1], w.z - vi[2], p.w, eps2, acc, jk, pot,
+                            j, i);
+}
+
+// The i side of a pair in the packed form below: the x and y components
+// negated and paired, z kept as it is.
+struct IDS {
+    float2 nh, nl, nv;   // (-x_hi, -y_hi), (-x_lo, -y_lo), (-v_x, -v_y)
+    float zh, zl, vz;
+};
+
+__device__ __forceinline__ IDS make_ids(const float4 &p, const float4 &l, const float4 &v)
+{
+    IDS I;
+    I.nh = make_float2(-p.x, -p.y);
+    I.nl = make_float2(-l.x, -l.y);
+    I.nv = make_float2(-v.x, -v.y);
+    I.zh = p.z; I.zl = l.z; I.vz = v.z;
+    return I;
+}
+
+// pair_ds with the x and y components of the three differences taken by
+// packed two-lane FP32 adds (add.f32x2): four instructions instead of eight,
+// each lane rounded exactly as the scalar subtraction it replaces
+// (RN(a + (-b)) = RN(a - b)), so the result is bit for bit that of pair_ds.
+// The FMA pipe does the same work; the saving is issue slots.
+template <bool SOFT, bool GUARD>
+__device__ __forceinline__ void pair_ds_packed(const float4 &p, const float4 &l, const float4 &w,
+                                               const IDS &I, float eps2, float acc[3], float jk[3],
+                                               float &pot, int j = 0, int i = 1)
+{
+    const float2 dh = __fadd2_rn(make_float2(p.x, p.y), I.nh);
+    const float2 dl = __fadd2_rn(make_float2(l.x, l.y), I.nl);
+    const float2 d = __fadd2_rn(dh, dl);
+    const float2 u = __fadd2_rn(make_float2(w.x, w.y), I.nv);
+    const float dz = (p.z - I.zh) + (l.z - I.zl);
+    pair_terms<SOFT, GUARD>(d.x, d.y, dz, u.x, u.y, w.z - I.vz, p.w, eps2, acc, jk, pot, j, i);
 }
 
 // Block size of a force launch: read on the device when the host does not know it.

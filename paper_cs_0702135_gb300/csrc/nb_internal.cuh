@@ -63,7 +63,7 @@ struct ForceOut {
 #define NB_IPAR_R 4
 #endif
 #ifndef NB_IPAR_UNROLL
-#define NB_IPAR_UNROLL 8
+#define NB_IPAR_UNROLL 4
 #endif
 
 constexpr int kIparNT = NB_IPAR_NT;  // threads per CTA (= j per tile), i-parallel kernels
