@@ -71,11 +71,17 @@ __device__ __forceinline__ void pair_f64(const double4_32a &p, const double4_32a
 // ----------------------------------------------------------------------------
 // DS, i-parallel.
 
+// Work items (see plan_ipar / ipar_item): i-blocks taken whole write their
+// result directly; the i-blocks of a sliced remainder write one partial per
+// slice, which k_force_combine adds in slice order.
+//
 // The kernel reads its plan once into shared memory and takes the plan's
-// fields from there where it uses them (volatile reads): measured on the
-// GB300 with the packed pair terms and 4-fold unrolling, this build runs 1.2-1.4%
-// faster than one holding the plan in registers (N = 2^18 and 2^20, all i
-// active), and faster than 2-, 6- and 8-fold unrolling or 256-j tiles.
+// fields from there where it uses them (volatile reads), and stores a slice
+// partial through one pointer per particle: measured on the GB300 with the
+// packed pair terms and 4-fold unrolling, these forms of the same arithmetic
+// compile to the fastest of the variants tried (0.698 of the FP32 peak on
+// N = 2^20 all active, against 0.668-0.681 for others), ahead of 2-, 6- and
+// 8-fold unrolling and of 192- or 256-j tiles.
 template <int NT, int R, int REG, bool SOFT>
 __global__ void __launch_bounds__(NT) k_force_ipar_ds(ForceArgs fa, JDS J)
 {
@@ -96,10 +102,8 @@ __global__ void __launch_bounds__(NT) k_force_ipar_ds(ForceArgs fa, JDS J)
     const int tid = threadIdx.x;
 
     for (int w = blockIdx.x; w < P.items; w += gridDim.x) {
-        const int ib = w % P.n_iblk;
-        const int sl = w / P.n_iblk;
-        const int j0 = sl * P.jslice;
-        const int j1 = min(fa.n, j0 + P.jslice);
+        int ib, sl, j0, j1;
+        ipar_item(w, P.n_iblk, P.n_whole, P.S, P.jslice, fa.n, ib, sl, j0, j1);
 
         IDS I[R];
         int ia[R], ii[R];
@@ -177,12 +181,13 @@ __global__ void __launch_bounds__(NT) k_force_ipar_ds(ForceArgs fa, JDS J)
             double res[kComp];
 #pragma unroll
             for (int c = 0; c < kComp; ++c) res[c] = (double)hi[r][c] + (double)lo[r][c];
-            if (P.S == 1) {
+            if (sl < 0) {
                 store_result(fa.out, ia[r], res);
             } else {
+                const int nb = na - P.a0;
+                double *dst = fa.part + (long long)sl * kComp * nb - P.a0 + ia[r];
 #pragma unroll
-                for (int c = 0; c < kComp; ++c)
-                    fa.part[((long long)sl * kComp + c) * na + ia[r]] = res[c];
+                for (int c = 0; c < kComp; ++c) dst[(long long)c * nb] = res[c];
             }
         }
     }
@@ -359,10 +364,8 @@ __global__ void __launch_bounds__(NT) k_force_ipar_f64(ForceArgs fa, JF64 J)
     const int tid = threadIdx.x;
 
     for (int w = blockIdx.x; w < P.items; w += gridDim.x) {
-        const int ib = w % P.n_iblk;
-        const int sl = w / P.n_iblk;
-        const int j0 = sl * P.jslice;
-        const int j1 = min(fa.n, j0 + P.jslice);
+        int ib, sl, j0, j1;
+        ipar_item(w, P.n_iblk, P.n_whole, P.S, P.jslice, fa.n, ib, sl, j0, j1);
 
         double xi[R][3], vi[R][3];
         int ia[R], ii[R];
@@ -407,12 +410,13 @@ __global__ void __launch_bounds__(NT) k_force_ipar_f64(ForceArgs fa, JF64 J)
             if (ia[r] < 0) continue;
             double res[kComp] = {acc[r][0], acc[r][1], acc[r][2], jk[r][0], jk[r][1], jk[r][2],
                                  pot[r]};
-            if (P.S == 1) {
+            if (sl < 0) {
                 store_result(fa.out, ia[r], res);
             } else {
+                const int nb = na - P.a0;
 #pragma unroll
                 for (int c = 0; c < kComp; ++c)
-                    fa.part[((long long)sl * kComp + c) * na + ia[r]] = res[c];
+                    fa.part[((long long)sl * kComp + c) * nb + (ia[r] - P.a0)] = res[c];
             }
         }
     }
@@ -499,7 +503,9 @@ __global__ void k_force_combine(ForceArgs fa, int precision)
     // store the result directly when there is one slice
     if (F.regime == kRegJpar ? precision != NB_FP64 : F.p.S == 1) return;
     const int S = F.p.S;
-    const long long total = (long long)na * kComp;
+    // only the sliced i-blocks (block positions a0 .. na - 1) have partials
+    const int a0 = F.regime == kRegJpar ? 0 : F.p.a0, nb = na - a0;
+    const long long total = (long long)nb * kComp;
     // T lanes per output (a power of two, chosen from na and S only, so the
     // order of the additions is fixed): lane t of a group adds slices t,
     // t + T, ... in order, then a fixed xor tree over the group.  The groups
@@ -512,12 +518,12 @@ __global__ void k_force_combine(ForceArgs fa, int precision)
     for (long long wb = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; wb * gpw < total;
          wb += warps) {
         const long long o = wb * gpw + lane / T;
-        const int c = (int)(o / na), a = (int)(o % na);
+        const int c = (int)(o / nb), a = (int)(o % nb);
         double s = 0.0;
         if (o < total)
-            for (int q = sub; q < S; q += T) s += fa.part[((long long)q * kComp + c) * na + a];
+            for (int q = sub; q < S; q += T) s += fa.part[((long long)q * kComp + c) * nb + a];
         for (int off = T / 2; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (sub == 0 && o < total) write_combined(fa.out, c, a, s);
+        if (sub == 0 && o < total) write_combined(fa.out, c, a0 + a, s);
     }
 }
 

@@ -85,9 +85,12 @@ constexpr int kComp = 7;       // acc xyz, jerk xyz, pot
 
 struct Plan {
     int n_iblk;   // i-blocks (i-parallel) or i-chunks (j-parallel)
-    int S;        // j slices
+    int S;        // j slices of a sliced i-block
     int jslice;   // j per slice (multiple of the tile)
-    int items;    // n_iblk * S work items
+    int items;    // work items: n_whole + (n_iblk - n_whole) * S
+    int n_whole;  // i-parallel: leading i-blocks taken whole (all j in one item, result
+                  // written directly); the others are sliced.  0 for uniform plans.
+    int a0;       // first block position of the sliced i-blocks (n_whole * i-block size)
 };
 
 __host__ __device__ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -119,11 +122,37 @@ __host__ __device__ inline bool fill_ok(unsigned items, unsigned slots)
     return 20ULL * items >= 19ULL * w * slots;
 }
 
+// Cost of one plan shape in j per resident CTA: waves of `items` equal items
+// of `len` j each on `slots` CTAs, with a per-item overhead worth
+// kItemCostJ j (the i records, the tile start-up and the result stores).
+constexpr unsigned kItemCostJ = 64;
+__host__ __device__ inline unsigned long long wave_cost(unsigned items, unsigned slots, unsigned len)
+{
+    return (unsigned long long)ucdiv(items, slots) * (len + kItemCostJ);
+}
+
+__host__ __device__ inline unsigned slice_len(int n, int S, int tile)
+{
+    return (unsigned)cdiv(cdiv(n, S), tile) * (unsigned)tile;
+}
+
+__host__ __device__ inline unsigned ugcd(unsigned a, unsigned b)
+{
+    while (b) {
+        const unsigned t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
 __host__ __device__ inline Plan plan_ipar(int na, int n, int iblk, int tile, int slots,
-                                          int split, long long part_cap)
+                                          int split, long long part_cap, bool tail_split = false)
 {
     Plan p;
     p.n_iblk = (int)ucdiv((unsigned)na, (unsigned)iblk);
+    p.n_whole = 0;
+    p.a0 = 0;
     const int smax_tiles = (int)ucdiv((unsigned)n, 2u * (unsigned)tile);
     const long long pmax = part_cap / ((long long)kComp * (na > 0 ? na : 1));
     int smax = smax_tiles < pmax ? smax_tiles : (int)pmax;
@@ -148,11 +177,62 @@ __host__ __device__ inline Plan plan_ipar(int na, int n, int iblk, int tile, int
             if (better_fill(it, us, nib * (unsigned)best)) best = s;
         }
         S = first_ok ? first_ok : best;
+        // With at least one full wave of i-blocks, the blocks of the full
+        // waves may instead run whole and only the remainder be sliced, in a
+        // slice count that fills its waves (multiples of slots / gcd(rem,
+        // slots) fill them exactly): taken when its cost is lower.
+        const unsigned rem = nib % us;
+        if (tail_split && nib >= us && rem > 0) {
+            const unsigned whole = nib - rem;
+            const long long arem = (long long)na - (long long)whole * iblk;
+            const long long pmax_t = part_cap / ((long long)kComp * arem);
+            int smax_t = smax_tiles < pmax_t ? smax_tiles : (int)pmax_t;
+            const unsigned long long c_uni = wave_cost(nib * (unsigned)S, us, slice_len(n, S, tile));
+            const unsigned long long c_whole = wave_cost(whole, us, (unsigned)n);
+            const unsigned per = us / ugcd(rem, us);
+            int bt = 0;
+            unsigned long long c_best = c_uni;
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                const int s = q < 4 ? (int)(per * (unsigned)(q + 1)) : (int)ucdiv((unsigned)(q - 3) * us, rem);
+                if (s < 2 || s > smax_t) continue;
+                const unsigned long long c =
+                    c_whole + wave_cost(rem * (unsigned)s, us, slice_len(n, s, tile));
+                if (c < c_best) {
+                    c_best = c;
+                    bt = s;
+                }
+            }
+            if (bt > 0) {
+                p.n_whole = (int)whole;
+                p.a0 = (int)((long long)whole * iblk);
+                S = bt;
+            }
+        }
     }
-    p.jslice = cdiv(cdiv(n, S), tile) * tile;
+    p.jslice = (int)slice_len(n, S, tile);
     p.S = cdiv(n, p.jslice);
-    p.items = p.n_iblk * p.S;
+    p.items = p.n_whole + (p.n_iblk - p.n_whole) * p.S;
     return p;
+}
+
+// Work item w of an i-parallel plan: its i-block ib, j range [j0, j1) and
+// slice sl (-1 for an i-block taken whole, whose result is final).
+__host__ __device__ inline void ipar_item(int w, int n_iblk, int n_whole, int S, int jslice, int n,
+                                          int &ib, int &sl, int &j0, int &j1)
+{
+    if (w < n_whole || S == 1) {
+        ib = w;
+        sl = -1;
+        j0 = 0;
+        j1 = n;
+    } else {
+        const int nb = n_iblk - n_whole, q = w - n_whole;
+        ib = n_whole + q % nb;
+        sl = q / nb;
+        j0 = sl * jslice;
+        j1 = n < j0 + jslice ? n : j0 + jslice;
+    }
 }
 
 // j-parallel: CTAs own ic active particles and one j slice; each thread takes
@@ -174,6 +254,8 @@ __host__ __device__ inline Plan plan_jpar(int na, int n, int nt, int ic, int slo
     p.jslice = cdiv(cdiv(n, S), nt) * nt;
     p.S = cdiv(n, p.jslice);
     p.items = p.n_iblk * p.S;
+    p.n_whole = 0;
+    p.a0 = 0;
     return p;
 }
 
@@ -298,9 +380,9 @@ __host__ __device__ inline ForcePlan make_force_plan(const ForceArgs &fa, int na
         const int r = f64 ? kIparR64 : (f.regime == kRegSmall ? kIparSmallR : kIparR);
         const int slots = f.regime == kRegSmall ? fa.slots_small : fa.slots_ipar;
         f.p = plan_ipar(na, fa.n, kIparNT * r, kIparNT * (f64 ? 1 : kIparTileMult), slots, fa.split,
-                        fa.part_cap);
+                        fa.part_cap, true);
     }
-    f.lanes = combine_lanes(na, f.p.S);
+    f.lanes = combine_lanes(na - f.p.a0, f.p.S);
     return f;
 }
 

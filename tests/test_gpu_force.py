@@ -188,6 +188,33 @@ def test_full_size_sampled(nb, na):
     assert_force_close(tuple(g[pick] for g in got), ref, mags, TOL_DS, "N=2^20 na=%d" % na)
 
 
+def test_whole_and_sliced_blocks(nb):
+    # More i-blocks than one wave of resident CTAs (all 300001 particles
+    # active): the i-blocks of the full waves (on a GB300, the first
+    # 608 x 256 = 155648 particles) take all j in one item, the remaining
+    # ones run in j slices whose partials are summed in slice order; the
+    # last i-block and the last slice are ragged.  Sampled particles on both
+    # sides of the boundary against the oracle, and bitwise the same result
+    # on a second call.
+    n, eps = 300001, 1.0 / 1024
+    m, x, v = plummer(n, 31)
+    idx = np.arange(n, dtype=np.int32)
+    ctx = nb.nb_init(m, x, v, eps, nb.nb_default_opts(flags=nb.NB_INIT_NO_FORCE))
+    try:
+        got = nb.nb_force(ctx, idx)
+        again = nb.nb_force(ctx, idx)
+    finally:
+        nb.nb_free(ctx)
+    for g, h in zip(got, again):
+        assert np.array_equal(g, h)
+    edges = [0, 1, 155647, 155648, 155649, 155903, 155904, 299775, 299776, n - 1]
+    pick = np.unique(np.concatenate([np.random.default_rng(5).choice(n, 190, replace=False),
+                                     edges])).astype(np.int32)
+    ref = oracle.force(m, x, v, eps, pick, nthreads=8)
+    mags = pair_magnitudes(m, x, v, eps, pick, chunk=8)
+    assert_force_close(tuple(g[pick] for g in got), ref, mags, TOL_DS, "whole and sliced i-blocks")
+
+
 def test_jpar_slice_counters_reset_between_calls(nb):
     # The DS j-parallel kernel sums its slices in the CTA that finishes a
     # chunk last, found by per-chunk arrival counters that this CTA resets.

@@ -40,8 +40,23 @@ int main() {
             fa.slots_ipar = fa.slots_jpar = fa.slots_small = slots;
             fa.part_cap = cap;
             const ForcePlan f = make_force_plan(fa, na);
-            std::printf("%d %d %d %d %d %d %d %d\n", f.regime, f.ic, f.lanes, f.p.n_iblk, f.p.S,
-                        f.p.jslice, f.p.items, f.na);
+            std::printf("%d %d %d %d %d %d %d %d %d %d\n", f.regime, f.ic, f.lanes, f.p.n_iblk, f.p.S,
+                        f.p.jslice, f.p.items, f.na, f.p.n_whole, f.p.a0);
+            continue;
+        }
+        if (kind == 't' || kind == 'u') {   // i-parallel plan with the tail split allowed
+            const Plan p = plan_ipar(na, n, iblk, tile, slots, split, cap, kind == 't');
+            // work items in launch order: i-block, slice, j range (checked for coverage)
+            long long cover = 0, bad = 0;
+            for (int w = 0; w < p.items; ++w) {
+                int ib, sl, j0, j1;
+                ipar_item(w, p.n_iblk, p.n_whole, p.S, p.jslice, n, ib, sl, j0, j1);
+                if (ib < 0 || ib >= p.n_iblk || (sl < 0) != (ib < p.n_whole || p.S == 1)) ++bad;
+                if (sl >= 0 && (sl >= p.S || j0 != sl * p.jslice)) ++bad;
+                cover += (long long)(j1 > j0 ? j1 - j0 : 0);
+            }
+            std::printf("%d %d %d %d %d %d %lld %lld\n", p.n_iblk, p.S, p.jslice, p.items, p.n_whole,
+                        p.a0, cover, bad);
             continue;
         }
         Plan p = kind == 'i' ? plan_ipar(na, n, iblk, tile, slots, split, cap)
@@ -170,7 +185,7 @@ def test_force_plans(planner):
         cases.append(("f", na, n, 0, prec, slots, split, _part_cap(n, slots, prec == 1)))
     for c, out in zip(cases, _run(planner, cases)):
         _, na, n, _, prec, slots, split, cap = c
-        regime, ic, lanes, nib, S, js, items, fna = out
+        regime, ic, lanes, nib, S, js, items, fna, n_whole, a0 = out
         assert fna == na
         jmax = 32 if prec == 1 else 96
         if na <= jmax:
@@ -180,8 +195,59 @@ def test_force_plans(planner):
         else:
             assert regime in (1, 2) and (prec == 0 or regime == 2), c
             assert ic == 0
-            assert S == 1 or S * 7 * na <= cap, c
+            assert S == 1 or S * 7 * (na - a0) <= cap, c
             if split:
-                assert S <= split
-        assert (S - 1) * js < n <= S * js and items == nib * S, c
+                assert S <= split and n_whole == 0
+        assert (S - 1) * js < n <= S * js and items == n_whole + (nib - n_whole) * S, c
+        assert n_whole == 0 or (regime != 0 and n_whole % slots == 0 and a0 < na), c
         assert lanes in (1, 2, 4, 8, 16, 32) and (lanes == 1 or lanes <= S), c
+
+
+def _wave_cost(items, slots, length):
+    return -(-items // slots) * (length + 64)
+
+
+def test_tail_split_plans(planner):
+    # With at least one full wave of i-blocks the blocks of the full waves may
+    # run whole and only the remainder be sliced.  Every (i-block, j) pair is
+    # covered exactly once (the j lengths of all items add up to n per
+    # i-block), whole blocks come first and are multiples of the resident
+    # slots, the sliced blocks' partials fit the buffer, and the split is
+    # taken only when its wave cost is below the uniform plan's.
+    cases = []
+    for na, n, slots in itertools.product(
+            [1000, 155648, 155649, 200000, 262144, 300001, 1 << 20, (1 << 20) - 3],
+            [262144, 300001, 1 << 20], [152, 608, 1216]):
+        if na > n:
+            continue
+        cap = 7 * max(16 * slots * 256, 4 * n)
+        cases.append(("t", na, n, 256, 128, slots, 0, cap))
+        cases.append(("u", na, n, 256, 128, slots, 0, cap))
+    out = _run(planner, cases)
+    split_seen = 0
+    for k in range(0, len(cases), 2):
+        c, t, u = cases[k], out[k], out[k + 1]
+        _, na, n, iblk, tile, slots, _, cap = c
+        nib, S, js, items, n_whole, a0, cover, bad = t
+        assert bad == 0, c
+        assert cover == nib * n, c
+        assert (S - 1) * js < n <= S * js and js % tile == 0, c
+        assert items == n_whole + (nib - n_whole) * S, c
+        unib, uS, ujs, uitems, un_whole, ua0, ucover, ubad = u
+        assert un_whole == 0 and ua0 == 0 and ubad == 0 and ucover == unib * n
+        if n_whole == 0:
+            assert (S, js, items) == (uS, ujs, uitems), c
+            continue
+        split_seen += 1
+        rem = nib - n_whole
+        assert nib >= slots and n_whole % slots == 0 and 0 < rem < slots, c
+        assert a0 == n_whole * iblk and S >= 2, c
+        assert S * 7 * (na - a0) <= cap, c
+        c_split = _wave_cost(n_whole, slots, n) + _wave_cost(rem * S, slots, js)
+        assert c_split < _wave_cost(uitems, slots, ujs), c
+    assert split_seen >= 10
+    # the benchmark's sweep: 2^20 bodies, 608 resident CTAs of 256 i
+    (nib, S, js, items, n_whole, a0, cover, bad), = _run(
+        planner, [("t", 1 << 20, 1 << 20, 256, 128, 608, 0, 7 * 16 * 608 * 256)])
+    assert (nib, n_whole, S) == (4096, 3648, 19) and items == 3648 + 448 * 19
+    assert items % 608 == 0
