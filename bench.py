@@ -45,6 +45,8 @@ EPS = 1.0 / 1024
 SEED = 3
 LEVEL = 10                         # shared step 2^-10
 SWEEP_LADDER = [1, 256, 4096, 65536]
+ABOVE_L2_N = 1 << 22               # small-block sweeps with j records larger than the L2
+ABOVE_L2_LADDER = [1, 4, 32]
 FP64_SAMPLE = 4096
 ACCURACY_SAMPLE_FULL = 128         # sampled i of the headline accuracy check
 L2_FLUSH_BYTES = 256 << 20
@@ -427,6 +429,42 @@ def time_sweeps(ctx, n, nas, dev, torch, sample_active, flush):
     return ladder
 
 
+def time_sweeps_above_l2(nb, torch, stream, dev, sample_active, n=ABOVE_L2_N):
+    """Small-block sweeps whose j records do not fit the L2: Plummer N = 2^22
+    (seed 3), eps = 1/1024, 48 B x N = 201 MB of records against the 129 MB
+    L2, so no flush is needed (and none leaves dirty lines behind); 5 warm-ups,
+    then the median of 20 launches timed with CUDA events around the force
+    kernels."""
+    from synth import plummer
+    m, x, v = plummer(n, SEED)
+    c = nb.Context(m, x, v, EPS, flags=nb.NB_INIT_NO_FORCE, stream=stream.cuda_stream)
+    out = {}
+    try:
+        for na in ABOVE_L2_LADDER:
+            idx = torch.from_numpy(sample_active(n, na, SEED + na)).to(dev)
+            acc = torch.empty((na, 3), dtype=torch.float64, device=dev)
+            jerk, pot = torch.empty_like(acc), torch.empty(na, dtype=torch.float64, device=dev)
+            for _ in range(5):
+                c.nb_force_dev(idx, na, acc, jerk, pot)
+            c.nb_set_profiling(True)
+            c.nb_get_stats(reset=True)
+            times = []
+            for _ in range(20):
+                c.nb_force_dev(idx, na, acc, jerk, pot)
+                st = c.nb_get_stats(reset=True)
+                times.append(st["force_ms"] / 1e3 / max(1, st["force_launches"]))
+            c.nb_set_profiling(False)
+            fs = float(np.median(times))
+            jbytes = J_RECORD_BYTES * n
+            out[str(na)] = {"force_us": fs * 1e6, "j_record_gbs": jbytes / fs / 1e9,
+                            "j_record_hbm_frac": jbytes / fs / 1e9 / hbm_peak_gbs(),
+                            "interactions_per_s": na * (n - 1) / fs}
+    finally:
+        c.nb_free()
+    return {"N": n, "records_mb": J_RECORD_BYTES * n / 1e6, "flush": "none (records exceed L2)",
+            "sweeps": out}
+
+
 def run_extras(args, nb, ctx, m, x, v, stream, dev, torch, sample_active):
     n = args.n
     out = {}
@@ -435,6 +473,7 @@ def run_extras(args, nb, ctx, m, x, v, stream, dev, torch, sample_active):
     ladder = time_sweeps(ctx, n, [na for na in SWEEP_LADDER + [n] if na <= n], dev, torch,
                          sample_active, flush)
     out["sweeps"] = ladder
+    out["sweeps_above_l2"] = time_sweeps_above_l2(nb, torch, stream, dev, sample_active)
 
     # The all-FP64 kernel on the same sweep (FP64_SAMPLE active i against all N).
     na = min(FP64_SAMPLE, n)
