@@ -216,15 +216,19 @@ def force_traffic_per_launch(n, profile="k_force_ipar_ds.md", sources=FORCE_SOUR
         return None
     text = open(path).read()
     mh = re.search(r"force sources sha256[^:]*:\s*([0-9a-f]{64})", text)
-    mb = re.search(r"dram bytes per launch at N=(\d+):\s*([0-9.eE+]+)", text)
-    if not mh or not mb:
+    caps = {int(a): float(b) for a, b in
+            re.findall(r"dram bytes per launch at N=(\d+):\s*([0-9.eE+]+)", text)}
+    if not mh or not caps:
         return None
     if force_sources_sha256(sources) != mh.group(1):
         return None
-    # With the j records resident in L2 the kernel's DRAM traffic is O(N)
-    # (records, block outputs), so a smaller capture scales linearly.
-    n_cap, b = int(mb.group(1)), float(mb.group(2))
-    return b * n / n_cap
+    if n in caps:
+        return caps[n]
+    # Otherwise the largest capture, scaled linearly: with the j records
+    # resident in L2 and a uniform slice plan the traffic is O(N) (records,
+    # block outputs).
+    n_cap = max(caps)
+    return caps[n_cap] * n / n_cap
 
 
 def cpu_oracle_rate(m, x, v, eps, budget_s=10.0, seed=SEED, summation=0):
