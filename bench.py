@@ -504,6 +504,24 @@ def run_extras(args, nb, ctx, m, x, v, stream, dev, torch, sample_active):
         e = force_error_stats(c.nb_force(ia), ref, sa, sk)
         acc_rows[name] = {"max_err_acc": e[0], "max_err_jerk": e[1], "max_err_pot": e[2],
                           "p99_raw_rel_acc": e[3]}
+    # The timed sweep itself (all n i active): sampled outputs of one full-n
+    # force against the oracle, half of them from the last eighth of the
+    # particles, where the plan's sliced remainder lies (its first i-blocks
+    # run whole).
+    rng = np.random.default_rng(SEED + 31)
+    cut = n - n // 8
+    half = min(ACCURACY_SAMPLE_FULL // 2, cut, n - cut)
+    pick = np.sort(np.concatenate([rng.choice(cut, half, replace=False),
+                                   cut + rng.choice(n - cut, half, replace=False)])).astype(np.int32)
+    full = cds.nb_force(np.arange(n, dtype=np.int32))
+    ref_f = oracle.force(m, x, v, EPS, pick, nthreads=os.cpu_count() or 1)
+    fa_, fk_ = pair_magnitude_sums(m, x, v, EPS, pick, chunk=8)
+    e = force_error_stats(tuple(g[pick] for g in full), ref_f, fa_, fk_)
+    acc_rows["ds_full_sweep"] = {"max_err_acc": e[0], "max_err_jerk": e[1], "max_err_pot": e[2],
+                                 "p99_raw_rel_acc": e[3],
+                                 "sample": "%d of the %d outputs of one all-active sweep, %d of them "
+                                           "from the last eighth" % (len(pick), n, half)}
+    del full
     cds.nb_free()
     c64.nb_free()
     acc_rows["sample"] = ("%d i drawn uniformly (seed %d) against all %d j at t = 0; err = |d| / "
