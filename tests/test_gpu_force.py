@@ -188,18 +188,19 @@ def test_full_size_sampled(nb, na):
     assert_force_close(tuple(g[pick] for g in got), ref, mags, TOL_DS, "N=2^20 na=%d" % na)
 
 
-def test_whole_and_sliced_blocks(nb):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_whole_and_sliced_blocks(nb, precision):
     # More i-blocks than one wave of resident CTAs (all 300001 particles
     # active): the i-blocks of the full waves (on a GB300, the first
-    # 608 x 256 = 155648 particles) take all j in one item, the remaining
-    # ones run in j slices whose partials are summed in slice order; the
-    # last i-block and the last slice are ragged.  Sampled particles on both
-    # sides of the boundary against the oracle, and bitwise the same result
-    # on a second call.
+    # 608 x 256 = 155648 particles for DS, 2432 x 64 for FP64) take all j
+    # in one item, the remaining ones run in j slices whose partials are
+    # summed in slice order; the last i-block and the last slice are ragged.
+    # Sampled particles on both sides of the boundary against the oracle,
+    # and bitwise the same result on a second call.
     n, eps = 300001, 1.0 / 1024
     m, x, v = plummer(n, 31)
     idx = np.arange(n, dtype=np.int32)
-    ctx = nb.nb_init(m, x, v, eps, nb.nb_default_opts(flags=nb.NB_INIT_NO_FORCE))
+    ctx = nb.nb_init(m, x, v, eps, nb.nb_default_opts(precision=precision, flags=nb.NB_INIT_NO_FORCE))
     try:
         got = nb.nb_force(ctx, idx)
         again = nb.nb_force(ctx, idx)
@@ -212,7 +213,8 @@ def test_whole_and_sliced_blocks(nb):
                                      edges])).astype(np.int32)
     ref = oracle.force(m, x, v, eps, pick, nthreads=8)
     mags = pair_magnitudes(m, x, v, eps, pick, chunk=8)
-    assert_force_close(tuple(g[pick] for g in got), ref, mags, TOL_DS, "whole and sliced i-blocks")
+    assert_force_close(tuple(g[pick] for g in got), ref, mags, TOL_F64 if precision else TOL_DS,
+                       "whole and sliced i-blocks, precision %d" % precision)
 
 
 def test_jpar_slice_counters_reset_between_calls(nb):
