@@ -25,30 +25,35 @@ __device__ __forceinline__ void raise_err(int *err, int code)
 
 // ---------------------------------------------------------------------------
 
+// Particle i predicted to tn, written as its j record of the force kernels.
+__device__ __forceinline__ void predict_record(const State &s, int i, long long tn, int precision,
+                                               const JDS &jds, const JF64 &jf)
+{
+    const double dt = ticks_to_time(tn - s.t[i]);
+    double xp[3], vp[3];
+    predict3(s, i, s.n, dt, xp, vp);
+    const double m = s.m[i];
+    if (precision == NB_FP64) {
+        jf.pos[i] = make_double4_32a(xp[0], xp[1], xp[2], m);
+        jf.vel[i] = make_double4_32a(vp[0], vp[1], vp[2], 0.0);
+    } else {
+        float hi[3], lo[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) split_ds(xp[c], hi[c], lo[c]);
+        jds.pos_hi[i] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(m));
+        jds.pos_lo[i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+        jds.vel[i] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
+                                 __double2float_rn(vp[2]), 0.0f);
+    }
+}
+
 __global__ void k_predict(State s, long long t_val, const long long *t_ptr, const int *gate,
                           int precision, JDS jds, JF64 jf)
 {
     if (gate && *gate <= 0) return;
     const long long tn = t_ptr ? *t_ptr : t_val;
-    const int n = s.n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double dt = ticks_to_time(tn - s.t[i]);
-        double xp[3], vp[3];
-        predict3(s, i, n, dt, xp, vp);
-        const double m = s.m[i];
-        if (precision == NB_FP64) {
-            jf.pos[i] = make_double4_32a(xp[0], xp[1], xp[2], m);
-            jf.vel[i] = make_double4_32a(vp[0], vp[1], vp[2], 0.0);
-        } else {
-            float hi[3], lo[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) split_ds(xp[c], hi[c], lo[c]);
-            jds.pos_hi[i] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(m));
-            jds.pos_lo[i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
-            jds.vel[i] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
-                                     __double2float_rn(vp[2]), 0.0f);
-        }
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x)
+        predict_record(s, i, tn, precision, jds, jf);
 }
 
 // Hermite corrector and Aarseth step for the block (Section 2); the
@@ -124,8 +129,10 @@ __global__ void k_initial(State s, const double *acc, const double *jerk, double
 // ---------------------------------------------------------------------------
 // Block scheduler: t_next = min_i (t_i + 2^-lev_i) in ticks, then the block
 // {i : t_i + 2^-lev_i = t_next} compacted in ascending order by warp ballot
-// and prefix sums.  Three launches: per-chunk minimum; global minimum and
-// per-chunk counts; per-chunk exclusive offsets and scatter.
+// and prefix sums.  Two launches: per-chunk minimum and the count at it; then
+// the global minimum, per-chunk offsets and scatter, in the same launch as the
+// prediction of every particle to the new block time (Section 2's predictor
+// step, which needs nothing but that time).
 
 constexpr int kSchedNT = 256;
 constexpr int kSchedChunk = kSchedNT * 8;
@@ -186,8 +193,13 @@ __global__ void k_sched_min(State s, long long *blockmin, int *blockcnt)
     }
 }
 
+// Every CTA reduces the chunk minima to the block time; CTAs below nblocks
+// scatter their chunk's block members into act (the last of them also writes
+// n_active and the force plan), then every CTA predicts its share of the
+// particles.
 __global__ void k_sched_scatter(State s, Ctrl *ctrl, const long long *blockmin, const int *blockcnt,
-                                int *act, int nblocks, ForceArgs fa, ForcePlan *plan_out)
+                                int *act, int nblocks, ForceArgs fa, ForcePlan *plan_out,
+                                int precision, JDS jds, JF64 jf)
 {
     __shared__ long long sm[kSchedNT / 32];
     __shared__ int si[kSchedNT / 32];
@@ -198,15 +210,16 @@ __global__ void k_sched_scatter(State s, Ctrl *ctrl, const long long *blockmin, 
     tn = block_reduce(tn, MinOp(), sm);
     if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->t_next = tn;
     const bool done = tn > ctrl->t_end;
+    const bool chunk = blockIdx.x < nblocks;   // CTAs past the chunks only predict
     int pre = 0;   // no block past the end time: nothing counted
-    if (!done)
+    if (!done && chunk)
         for (int b = threadIdx.x; b < blockIdx.x; b += kSchedNT) pre += blockmin[b] == tn ? blockcnt[b] : 0;
     pre = block_reduce(pre, SumOp(), si);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lo = blockIdx.x * kSchedChunk;
     const int hi = min(s.n, lo + kSchedChunk);
     int running = 0;
-    if (!done) {
+    if (!done && chunk) {
         for (int base = lo; base < hi; base += kSchedNT) {
             const int i = base + threadIdx.x;
             const bool f = i < hi && end_time(s, i) == tn;
@@ -234,6 +247,11 @@ __global__ void k_sched_scatter(State s, Ctrl *ctrl, const long long *blockmin, 
             ctrl->interactions += (long long)total * (long long)(s.n - 1);
         }
     }
+    // every particle predicted to the block time (a block exists whenever tn
+    // is not past the end time)
+    if (!done)
+        for (int i = blockIdx.x * kSchedNT + threadIdx.x; i < s.n; i += gridDim.x * kSchedNT)
+            predict_record(s, i, tn, precision, jds, jf);
 }
 
 // ---------------------------------------------------------------------------
@@ -377,11 +395,13 @@ void launch_initial_steps(const State &s, const double *acc, const double *jerk,
 int schedule_blocks(int n) { return cdiv(n, kSchedChunk); }
 
 void launch_schedule(const State &s, Ctrl *ctrl, long long *blockmin, int *blockcnt, int *act,
-                     int nblocks, const ForceArgs &fa, ForcePlan *plan_out, cudaStream_t st)
+                     int nblocks, const ForceArgs &fa, ForcePlan *plan_out, int precision,
+                     const JDS &jds, const JF64 &jf, cudaStream_t st)
 {
     k_sched_min<<<nblocks, kSchedNT, 0, st>>>(s, blockmin, blockcnt);
-    k_sched_scatter<<<nblocks, kSchedNT, 0, st>>>(s, ctrl, blockmin, blockcnt, act, nblocks, fa,
-                                                   plan_out);
+    const int g = std::max(nblocks, grid_for(s.n, kSchedNT));
+    k_sched_scatter<<<g, kSchedNT, 0, st>>>(s, ctrl, blockmin, blockcnt, act, nblocks, fa, plan_out,
+                                            precision, jds, jf);
 }
 
 int energy_blocks(int n)

@@ -274,14 +274,13 @@ void enqueue_force(nb_ctx *c, const int *act, int na_host, const int *na_dev, Fo
 void enqueue_step(nb_ctx *c)
 {
     launch_schedule(c->S, c->d_ctrl, c->d_blockmin, c->d_blockcnt, c->d_act, c->nsched,
-                    force_args(c, c->d_act, 0, &c->d_ctrl->n_active, res_out(c)), c->d_plan, c->st);
-    launch_predict(c->S, 0, &c->d_ctrl->t_next, &c->d_ctrl->n_active, c->o.precision, c->jds,
-                   c->jf, c->st);
+                    force_args(c, c->d_act, 0, &c->d_ctrl->n_active, res_out(c)), c->d_plan,
+                    c->o.precision, c->jds, c->jf, c->st);
     enqueue_force(c, c->d_act, 0, &c->d_ctrl->n_active, res_out(c));
     launch_correct(c->S, c->d_act, 0, &c->d_ctrl->n_active, 0, &c->d_ctrl->t_next, c->d_res,
                    c->d_res + 3LL * c->n, c->o.eta, c->o.level_min, c->o.level_fixed,
                    &c->d_ctrl->err, c->sms, c->st);
-    c->launches += 2 + 1 + 1;  // scheduler, predictor, corrector (force counted above)
+    c->launches += 2 + 1;  // scheduler with the predictor, corrector (force counted above)
 }
 
 int set_t_end(nb_ctx *c, long long t_end)

@@ -479,9 +479,12 @@ void launch_correct(const State &s, const int *act, int na_host, const int *na_d
                     int *err, int sms, cudaStream_t st);
 void launch_initial_steps(const State &s, const double *acc, const double *jerk, double eta_init,
                           int level_min, int level_fixed, int *err, cudaStream_t st);
-// Also writes the plan of the force on the new block (make_force_plan(fa, n_active)).
+// Also writes the plan of the force on the new block (make_force_plan(fa, n_active))
+// and predicts every particle to the block time into the j records (as
+// launch_predict), unless no block is left before the end time.
 void launch_schedule(const State &s, Ctrl *ctrl, long long *blockmin, int *blockcnt, int *act,
-                     int nblocks, const ForceArgs &fa, ForcePlan *plan_out, cudaStream_t st);
+                     int nblocks, const ForceArgs &fa, ForcePlan *plan_out, int precision,
+                     const JDS &jds, const JF64 &jf, cudaStream_t st);
 int schedule_blocks(int n);
 void launch_energy(const State &s, const long long *t_ptr, const double *pot, double *part,
                    Ctrl *ctrl, cudaStream_t st);
