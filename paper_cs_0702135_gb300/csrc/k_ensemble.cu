@@ -317,7 +317,7 @@ __device__ __forceinline__ void ens_b_item(const EnsArgs &ea, int c, int k, floa
     const bool valid = grp < cnt;
     const int i = __ldcg(&ea.act[o + s0 + (valid ? grp : 0)]);
     const float4 ip = __ldcg(&ea.jph[o + i]), il = __ldcg(&ea.jpl[o + i]), iv = __ldcg(&ea.jv[o + i]);
-    const float xh[3] = {ip.x, ip.y, ip.z}, xl[3] = {il.x, il.y, il.z}, vi[3] = {iv.x, iv.y, iv.z};
+    const IDS I = make_ids(ip, il, iv);
     float hi[7] = {0, 0, 0, 0, 0, 0, 0}, lo[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int jt = 0; jt < n; jt += NT) {
         __syncthreads();
@@ -333,8 +333,8 @@ __device__ __forceinline__ void ens_b_item(const EnsArgs &ea, int c, int k, floa
             const int je = min(jc, jb + 64 * g);
             float ta[3] = {0, 0, 0}, tk[3] = {0, 0, 0}, tp = 0.0f;
             for (int jj = jb + lig; jj < je; jj += g)
-                pair_ds<false, true>(s_ph[jj], s_pl[jj], s_v[jj], xh, xl, vi, ea.eps2, ta, tk, tp,
-                                     jt + jj, i);
+                pair_ds_packed<false, true>(s_ph[jj], s_pl[jj], s_v[jj], I, ea.eps2, ta, tk, tp,
+                                            jt + jj, i);
             const float t7[7] = {ta[0], ta[1], ta[2], tk[0], tk[1], tk[2], tp};
 #pragma unroll
             for (int cc = 0; cc < 7; ++cc) two_sum_acc(hi[cc], lo[cc], t7[cc]);
