@@ -137,14 +137,14 @@ __device__ __forceinline__ void force_ds(const RunArgs &ra, int r, int na, int j
         const bool valid = a < na;
         const int i = __ldcg(&ra.act[valid ? a : 0]);
         const float4 ip = __ldcg(&ra.j.pos_hi[i]), il = __ldcg(&ra.j.pos_lo[i]), iv = __ldcg(&ra.j.vel[i]);
-        const float xh[3] = {ip.x, ip.y, ip.z}, xl[3] = {il.x, il.y, il.z}, vi[3] = {iv.x, iv.y, iv.z};
+        const IDS I = make_ids(ip, il, iv);
         float hi[7] = {0, 0, 0, 0, 0, 0, 0}, lo[7] = {0, 0, 0, 0, 0, 0, 0};
         for (int jb = 0; jb < m; jb += 64 * g) {
             const int je = min(m, jb + 64 * g);
             float ta[3] = {0, 0, 0}, tk[3] = {0, 0, 0}, tp = 0.0f;
             for (int jj = jb + lig; jj < je; jj += g)
-                pair_ds<false, true>(s_p[jj], s_l[jj], s_v[jj], xh, xl, vi, ra.eps2f, ta, tk, tp,
-                                     j0 + jj, i);
+                pair_ds_packed<false, true>(s_p[jj], s_l[jj], s_v[jj], I, ra.eps2f, ta, tk, tp,
+                                            j0 + jj, i);
             const float t7[7] = {ta[0], ta[1], ta[2], tk[0], tk[1], tk[2], tp};
 #pragma unroll
             for (int c = 0; c < 7; ++c) two_sum_acc(hi[c], lo[c], t7[c]);
