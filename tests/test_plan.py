@@ -251,3 +251,35 @@ def test_tail_split_plans(planner):
         planner, [("t", 1 << 20, 1 << 20, 256, 128, 608, 0, 7 * 16 * 608 * 256)])
     assert (nib, n_whole, S) == (4096, 3648, 19) and items == 3648 + 448 * 19
     assert items % 608 == 0
+
+
+def test_tail_split_plans_random(planner):
+    # Seeded random block sizes, body counts and resident slots around and
+    # above one full wave of i-blocks, for both i-block sizes (four i per
+    # thread, one i per thread): the same invariants as above on every case.
+    import random
+    r = random.Random(23)
+    cases = []
+    for _ in range(3000):
+        iblk = r.choice([256, 64])
+        slots = r.choice([152, 304, 608, 1216, 2432])
+        n = r.randint(iblk * slots // 2, 3 << 20)
+        lo = min(n, max(1, iblk * slots - 5000))
+        na = r.randint(lo, n) if r.random() < 0.7 else r.randint(1, n)
+        cap = 7 * max(16 * slots * iblk, 4 * n)
+        cases.append(("t", na, n, iblk, 128, slots, 0, cap))
+    out = _run(planner, cases)
+    seen = 0
+    for c, (nib, S, js, items, n_whole, a0, cover, bad) in zip(cases, out):
+        _, na, n, iblk, tile, slots, _, cap = c
+        assert bad == 0 and cover == nib * n, c
+        assert (S - 1) * js < n <= S * js and js % tile == 0, c
+        assert items == n_whole + (nib - n_whole) * S, c
+        if n_whole:
+            seen += 1
+            rem = nib - n_whole
+            assert n_whole % slots == 0 and 0 < rem < slots and a0 == n_whole * iblk, c
+            assert S >= 2 and S * 7 * (na - a0) <= cap, c
+        elif S > 1:
+            assert S * 7 * na <= cap, c
+    assert seen > 500
