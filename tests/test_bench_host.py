@@ -43,6 +43,26 @@ def test_traffic_is_reported_only_for_the_profiled_sources(monkeypatch):
     assert bench.force_traffic_per_launch(1 << 20) is None
 
 
+def test_traffic_lookup_prefers_an_exact_capture(tmp_path):
+    # A summary may carry captures at several N: the launch size's own capture
+    # is taken as it is (the whole/sliced plan's partials do not scale with
+    # N); any other N scales the largest capture linearly.
+    h = bench.force_sources_sha256()
+    prof = tmp_path / "k.md"
+    prof.write_text("force sources sha256 (k_force.cu, ...): %s\n"
+                    "dram bytes per launch at N=262144: 7.8e7\n"
+                    "dram bytes per launch at N=1048576: 2.4e8\n" % h)
+    assert bench.force_traffic_per_launch(1 << 20, str(prof)) == 2.4e8
+    assert bench.force_traffic_per_launch(1 << 18, str(prof)) == 7.8e7
+    assert bench.force_traffic_per_launch(1 << 21, str(prof)) == pytest.approx(4.8e8)
+    assert bench.force_traffic_per_launch(1 << 19, str(prof)) == pytest.approx(1.2e8)
+    prof.write_text("force sources sha256: %s\n" % ("f" * 64) +
+                    "dram bytes per launch at N=1048576: 2.4e8\n")
+    assert bench.force_traffic_per_launch(1 << 20, str(prof)) is None
+    prof.write_text("force sources sha256: %s\n" % h)       # no capture at all
+    assert bench.force_traffic_per_launch(1 << 20, str(prof)) is None
+
+
 def test_measured_hbm_peak(tmp_path, monkeypatch):
     peak = bench.hbm_peak_gbs()
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
